@@ -1,0 +1,337 @@
+"""Benchmark of the MRG32k3a multi-stream hot path on GB300.
+
+Step = one pass of the materialised-generation workload: create 65536 streams
+from the paper's default seed (12345 x 6) by successive 2^127 jumps, then
+generate 16384 draws per stream (2^30 outputs) of each of fp64 uniform, fp32
+uniform, fp64 normal, fp32 normal and fp32 exponential(1), each stream's state
+written back after every call.  Outputs (4-8 GiB per variant) are larger than
+L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on the
+host cores over a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MRG32k3a draws/s & GB/s vs HBM peak; batched/plain speedup; p99 latency"
+VARIANTS = (("uniform", "f64"), ("uniform", "f32"), ("normal", "f64"), ("normal", "f32"),
+            ("exponential", "f32"))
+ES = {"f64": 8, "f32": 4}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(streams: int, draws: int, nthreads: int):
+    """Times the oracle on `streams` streams x `draws` draws of every variant
+    (same seed, same transforms).  Returns (draws/s, seconds, draws done)."""
+    import oracle as O
+    st, _ = O.create_streams((12345,) * 6, streams)
+    codes = {"uniform": O.UNIFORM, "normal": O.NORMAL, "exponential": O.EXPONENTIAL}
+    t0 = time.perf_counter()
+    total = 0
+    for dist, dt in VARIANTS:
+        _, st = O.generate_streams(st, draws, codes[dist], f32=(dt == "f32"), nthreads=nthreads)
+        total += streams * draws
+    sec = time.perf_counter() - t0
+    return total / sec, sec, total
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    streams, draws = 4096, 16384   # bounded sample of the 65536 x 16384 workload
+    for _ in range(args.warmup):
+        cpu_oracle_sample(streams, draws, cores)
+    times, total = [], 0
+    for _ in range(args.steps):
+        v, sec, total = cpu_oracle_sample(streams, draws, cores)
+        times.append(sec)
+    value = total / float(np.mean(times))
+    sample = (f"{streams} of 65536 streams x {draws} draws x {len(VARIANTS)} variants per step "
+              f"({total} draws), OpenMP over streams")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "draws/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "materialised generation, 65536 streams x 16384 draws x 5 "
+                                   "variants (fp64/fp32 uniform, fp64/fp32 normal, fp32 Exp(1))",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "draws/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "draws/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_2201_06604_gb300 import mrg
+    from paper_2201_06604_gb300 import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    ns, n = W.MATERIALISED["streams"], W.MATERIALISED["draws"]
+    if args.quick:
+        ns, n = 4096, 4096
+    total_out = ns * n
+    # Replicas: rank r owns streams [r ns, (r+1) ns) of the creator sequence.
+    seed = tuple(W.PAPER_SEED)
+    for _ in range(rank):
+        seed = mrg.create_streams(ns, device=dev, seed=seed).next_seed
+    s = mrg.Streams(ns, dev)
+    buf = torch.empty(total_out * 8, dtype=torch.uint8, device=dev)
+    outs = {"f64": buf.view(torch.float64).view(ns, n),
+            "f32": buf[: total_out * 4].view(torch.float32).view(ns, n)}
+    tdt = {"f64": torch.float64, "f32": torch.float32}
+    stream = torch.cuda.current_stream()
+
+    def create():
+        nxt = (mrg.ctypes.c_uint32 * 6)()
+        mrg._check(mrg.lib.mrg_create_streams(mrg._u32_array(seed), ns, s.ptr(), nxt,
+                                              stream.cuda_stream))
+
+    def step(events=None):
+        create()
+        for i, (d, dt) in enumerate(VARIANTS):
+            if events is not None:
+                events[i][0].record(stream)
+            mrg.generate(s, n, d, tdt[dt], out=outs[dt])
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in VARIANTS]
+          for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = mrg.launch_count()
+    with ClockSampler(local_rank) as clk:
+        t_start.record(stream)
+        for k in range(K):
+            step(ev[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = mrg.launch_count() - launches0
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step_ms = ms / K
+
+    # advance kernel cost (mrg_skip runs the same jump kernel the generate
+    # call uses to write states back), to isolate generate_kernel
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        mrg.skip(s, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adv_ms = e0.elapsed_time(e1) / 20
+
+    variants = []
+    for i, (d, dt) in enumerate(VARIANTS):
+        t_call = float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
+        t_kern = max(t_call - adv_ms, 1e-6)
+        algo = total_out * ES[dt] + ns * 24  # outputs written + states read
+        variants.append({"dist": d, "dtype": dt, "ms": t_kern, "draws_per_s": total_out / t_kern * 1e3,
+                         "algo_bytes": algo, "gbs": algo / t_kern / 1e6})
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    dom = max(variants, key=lambda v: v["ms"])
+    for v in variants:
+        v["hbm_frac"] = v["gbs"] / hbm
+
+    draws_step = total_out * len(VARIANTS)
+    bytes_step = sum(total_out * ES[dt] for _, dt in VARIANTS)
+    value = draws_step * world / (per_step_ms / 1e3)
+
+    # e2e through the public API with host buffers: seed from pinned host
+    # memory in, every variant's output copied back to pinned host memory.
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty(total_out * 8, dtype=torch.uint8, pin_memory=True)
+        seed_host = torch.tensor(list(seed), dtype=torch.int64).pin_memory()
+        seed_dev = torch.empty_like(seed_host, device=dev)
+
+        def e2e_step():
+            seed_dev.copy_(seed_host, non_blocking=True)
+            create()
+            for d, dt in VARIANTS:
+                mrg.generate(s, n, d, tdt[dt], out=outs[dt])
+                nb = total_out * ES[dt]
+                host[:nb].copy_(buf[:nb], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        KE = max(1, min(K, 3))
+        a.record(stream)
+        for _ in range(KE):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / KE
+        e2e = {"value": draws_step * world / (e2e_ms / 1e3), "unit": "draws/s",
+               "h2d_bytes_per_step": 48, "d2h_bytes_per_step": bytes_step, "ms_per_step": e2e_ms}
+        del host
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle
+        oracle.build()
+        cores = len(os.sched_getaffinity(0))
+        v, sec, tot = cpu_oracle_sample(16384, 16384, cores)
+        cpu = {"value": v, "unit": "draws/s", "cores": cores, "kind": "oracle",
+               "sample": f"16384 of 65536 streams x 16384 draws x 5 variants ({tot} draws) in "
+                         f"{sec:.2f} s, OpenMP over streams"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (paper default seed 12345x6)",
+        "config": {"workload": f"materialised generation: {ns} streams x {n} draws x 5 variants "
+                               "(fp64/fp32 uniform, fp64/fp32 normal, fp32 Exp(1)) + stream creation",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "outputs (4-8 GiB per variant) larger than L2; no flush"},
+        "gbs": bytes_step * world / (per_step_ms / 1e3) / 1e9,
+        "roofline": {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>",
+                     "bound": "hbm", "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": dom["gbs"] / hbm, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "variants": variants,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="small shapes (development only)")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * mrg32k3a.h -- C ABI of libmrg32k3a: many independent MRG32k3a streams
+ * generated by hand-written CUDA kernels for GB300 (sm_103a).
+ *
+ * The method (arXiv 2201.06604, "clrng: A tool set for parallel random number
+ * generation on GPUs in R"):
+ *   - Sec. 2.1 (Creating streams): the period of a long-period generator is cut
+ *     into disjoint streams of equal length Z; a new stream starts Z steps after
+ *     the previous one, a stream keeps its current and its initial state, and
+ *     streams may be split into equally spaced substreams.  Here the generator
+ *     is MRG32k3a (named in Sec. 1 and 2; constants of L'Ecuyer 1999, the
+ *     generator of RngStreams), Z = 2^127 and the substream spacing is 2^76.
+ *   - Sec. 2.2 (Generating uniform random numbers): each work item keeps its
+ *     stream's state privately, draws an integer in [1, m1] per step, scales it
+ *     by a constant factor and writes the state back at the end, so that the
+ *     next call continues the stream.
+ *   - Sec. 3.1 (Algorithm 1, Box-Muller) and Sec. 3.2 (inverse transform): the
+ *     normal and exponential transforms of those uniforms.
+ *   - Sec. 2.2 (saving streams with saveRDS / reloading): state checkpoint.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MRG_OK (0) or a negative MRG_E* code; no exception crosses
+ *     the ABI.  mrg_last_error() returns a text for the calling thread's last
+ *     error.
+ *   - Device pointers are owned by the caller (allocate them with any CUDA
+ *     allocator, e.g. torch).  Host pointers are only read or written during
+ *     the call unless stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Kernels are enqueued on it and are ordered with the caller's
+ *     other work on it; calls return before the GPU work finishes unless the
+ *     entry point says it synchronises.
+ *   - State order inside a stream: six 32-bit words, newest first,
+ *     (x1[n-1], x1[n-2], x1[n-3], x2[n-1], x2[n-2], x2[n-3]); this is the
+ *     order of the paper's stream printout (Sec. 2.1, current.g1.1 .. g2.3).
+ *     Valid states have x1 words < m1 = 4294967087, x2 words < m2 = 4294944443
+ *     and neither triple all zero.
+ */
+#ifndef MRG32K3A_H
+#define MRG32K3A_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MRG_OK 0
+#define MRG_EINVAL (-1)   /* bad argument: invalid seed/state, null pointer, bad dist/dtype */
+#define MRG_ERANGE (-2)   /* a size, index or offset beyond what the generator supports */
+#define MRG_ECUDA (-3)    /* a CUDA runtime error; see mrg_last_error() */
+#define MRG_EBUSY (-4)    /* admission refused (serving queue full / over budget) */
+#define MRG_ETIMEOUT (-5) /* a bounded device or host wait gave up */
+
+/* ---- distributions and output types ----------------------------------- */
+#define MRG_RAW 0         /* z in [1, m1] as uint32 (runifGpu type "integer", Sec. 2.2) */
+#define MRG_UNIFORM 1     /* u = RN64(z * norm), norm = RN64(1/(m1+1)); fp32 = RN32(u) */
+#define MRG_NORMAL 2      /* Box-Muller on consecutive pairs of one stream (Sec. 3.1) */
+#define MRG_EXPONENTIAL 3 /* -ln(z/(m1+1)) / rate (Sec. 3.2, printed-values reading) */
+
+#define MRG_U32 0
+#define MRG_F32 1
+#define MRG_F64 2
+
+/* A set of streams in device memory, structure of arrays.  Word k of stream
+ * i lives at ptr[k * stride + i] (k = 0..5), stride >= n.  `cur` is the
+ * current state, `start` the stream's initial state (Sec. 2.1 "initial
+ * state"), `sub` the start of the current substream.  A view of streams
+ * [a, a + m) of a larger set is {cur + a, start + a, sub + a, m, stride}. */
+typedef struct mrg_streams {
+    uint32_t *cur;
+    uint32_t *start;
+    uint32_t *sub;
+    uint64_t n;
+    uint64_t stride;
+} mrg_streams;
+
+/* Text of the calling thread's last error ("" if none). */
+const char *mrg_last_error(void);
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t mrg_launch_count(void);
+
+/* Library version string. */
+const char *mrg_version(void);
+
+/* Checks a seed / state: x1 words < m1, x2 words < m2, neither triple all
+ * zero.  Returns MRG_OK or MRG_EINVAL. */
+int mrg_seed_check(const uint32_t seed[6]);
+
+/* Creates n streams from the creator state `seed` (Sec. 2.1 setBaseCreator /
+ * createStreamsGpu): stream i starts i * 2^127 steps after seed, exactly as if
+ * the streams had been created one after another.  Writes cur = start = sub
+ * for streams 0..n-1 of `s` (s->n must be >= n), computed in parallel on the
+ * device.  next_seed (host, may be NULL) receives the creator state after the
+ * n-th stream, i.e. seed advanced n * 2^127 steps, so the next creation call
+ * continues the sequence.  Errors: MRG_EINVAL (seed invalid, s or its
+ * pointers NULL with n > 0, n > s->n), MRG_ERANGE (n >= 2^64 streams is not
+ * representable; n > 2^63 rejected), MRG_ECUDA. */
+int mrg_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams *s,
+                       uint32_t next_seed[6], void *stream);
+
+/* Generates n_per_stream values from every stream of `s` into the device
+ * array out, stream-major: value i of stream j at out[j * ld + i], ld >= n.
+ * dist / dtype: MRG_RAW with MRG_U32; MRG_UNIFORM, MRG_NORMAL or
+ * MRG_EXPONENTIAL with MRG_F32 or MRG_F64.  rate is the exponential rate
+ * (> 0; ignored otherwise).  Raw and uniform outputs are bit-exact functions
+ * of the state; normals and exponentials are within 1e-12 absolute (fp64) or
+ * 2 ulp (fp32) of the exact transform of the same integers.  Each stream's
+ * `cur` advances by the draws consumed: n for raw, uniform and exponential,
+ * n + (n mod 2) for normals (an odd count discards the last sine output), so
+ * the next call continues each stream exactly (Sec. 2.2).  The output does
+ * not depend on the launch configuration.  out must not overlap the states.
+ * Errors: MRG_EINVAL (bad dist/dtype pair, rate <= 0 for exponentials, ld < n,
+ * NULL pointers), MRG_ECUDA. */
+int mrg_generate(const mrg_streams *s, uint64_t n_per_stream, int dist, int dtype,
+                 double rate, void *out, uint64_t ld, void *stream);
+
+/* Advances every stream's `cur` by k = k_hi * 2^64 + k_lo steps (jump-ahead
+ * by a matrix power, Sec. 2.1).  `start` and `sub` are unchanged.
+ * Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_skip(const mrg_streams *s, uint64_t k_hi, uint64_t k_lo, void *stream);
+
+/* Moves every stream to the start of its next substream: sub += 2^76 steps,
+ * cur = sub (RngStreams' ResetNextSubstream; substreams, Sec. 2.1). */
+int mrg_substream_next(const mrg_streams *s, void *stream);
+
+/* cur = sub (back to the start of the current substream). */
+int mrg_reset_substream(const mrg_streams *s, void *stream);
+
+/* cur = sub = start (back to the stream's initial state, Sec. 2.1). */
+int mrg_reset_stream(const mrg_streams *s, void *stream);
+
+/* Checkpoint (Sec. 2.2, saving streams to a file and reloading them): copies
+ * the three state arrays to host memory laid out as [3][6][n] uint32
+ * (cur, start, sub; word k of stream i at [a][k][i]).  Synchronises
+ * `stream`.  host must hold 18 * n words.  Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_get_state(const mrg_streams *s, uint32_t *host, void *stream);
+
+/* Restores states saved by mrg_get_state.  Every state is validated first
+ * (MRG_EINVAL and nothing is written if one is invalid).  Synchronises
+ * `stream`. */
+int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
+
+/* Fused consumer with no stored draws: for every stream, `draws` draws are
+ * taken as draws/2 pairs (za, zb) (an odd count is rounded up to whole
+ * pairs).  count[i] = number of pairs with (za/M)^2 + (zb/M)^2 < 1,
+ * M = m1 + 1, decided exactly in integers; sum[i] = sum over the pairs of
+ * X + Y, the Box-Muller normals of the same pair (Sec. 3.1).  count and sum
+ * are device arrays of s->n elements.  Each stream's cur advances by the
+ * draws consumed.  Counts are exact; sums are within 1e-9 of the exact sum
+ * relative to the sum of |X| + |Y|.  Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRG32K3A_H */

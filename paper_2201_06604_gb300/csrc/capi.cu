@@ -1,0 +1,223 @@
+// capi.cu -- extern "C" entry points of libmrg32k3a (declared in
+// include/mrg32k3a.h).  Argument checking, per-device table upload, and the
+// host-side creator arithmetic live here; every per-stream step runs in the
+// kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mrg32k3a.h"
+#include "host_jump.h"
+#include "internal.h"
+#include "mrg32k3a_core.cuh"
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const char* msg) {
+  t_err = msg;
+  return code;
+}
+
+int fail_cuda(cudaError_t e, const char* where) {
+  t_err = std::string(where) + ": " + cudaGetErrorName(e) + ": " + cudaGetErrorString(e);
+  return MRG_ECUDA;
+}
+
+// Per-device one-time set-up: the jump tables go to constant memory.
+int ensure_device() {
+  static std::mutex mu;
+  static bool ready[64] = {};
+  static uint32_t tab[2][mrg::host::kJumpBits][9];
+  static bool tab_built = false;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(MRG_ECUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (ready[dev]) return MRG_OK;
+  if (!tab_built) {
+    if (!mrg::host::norm_constant_ok(mrg::NORM_DELTA))
+      return fail(MRG_ECUDA, "RN64(1/(m1+1)) does not match the kernels' constant");
+    mrg::host::jump_table_u32(tab);
+    tab_built = true;
+  }
+  e = mrg::upload_tables(&tab[0][0][0], sizeof(tab));
+  if (e != cudaSuccess) return fail_cuda(e, "uploading jump tables");
+  ready[dev] = true;
+  return MRG_OK;
+}
+
+bool streams_ok(const mrg_streams* s) {
+  return s && s->cur && s->start && s->sub && s->stride >= s->n;
+}
+
+mrg::DevStreams dev(const mrg_streams* s) {
+  return mrg::DevStreams{s->cur, s->start, s->sub, s->n, s->stride};
+}
+
+inline cudaStream_t cs(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+}  // namespace
+
+extern "C" {
+
+const char* mrg_last_error(void) { return t_err.c_str(); }
+
+uint64_t mrg_launch_count(void) { return mrg::g_launches.load(); }
+
+const char* mrg_version(void) { return "libmrg32k3a 0.1 (sm_103a)"; }
+
+int mrg_seed_check(const uint32_t seed[6]) {
+  if (!seed) return fail(MRG_EINVAL, "seed is NULL");
+  if (!mrg::host::state_valid(seed))
+    return fail(MRG_EINVAL, "invalid seed: need x1 words < m1, x2 words < m2, no all-zero triple");
+  return MRG_OK;
+}
+
+int mrg_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams* s,
+                       uint32_t next_seed[6], void* stream) {
+  int rc = mrg_seed_check(seed);
+  if (rc) return rc;
+  if (n > (1ull << 63)) return fail(MRG_ERANGE, "too many streams");
+  if (n > 0 && !streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (n > 0 && n > s->n) return fail(MRG_EINVAL, "n exceeds the stream set");
+  if (n > 0) {
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = mrg::launch_create(seed, n, dev(s), cs(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "create_kernel");
+  }
+  if (next_seed) {
+    uint32_t t[6];
+    std::memcpy(t, seed, sizeof t);
+    mrg::host::jump_pow2_multiple(t, n, mrg::STREAM_LOG2);
+    std::memcpy(next_seed, t, sizeof t);
+  }
+  return MRG_OK;
+}
+
+int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double rate, void* out,
+                 uint64_t ld, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  bool pair_ok = (dist == MRG_RAW && dtype == MRG_U32) ||
+                 ((dist == MRG_UNIFORM || dist == MRG_NORMAL || dist == MRG_EXPONENTIAL) &&
+                  (dtype == MRG_F32 || dtype == MRG_F64));
+  if (!pair_ok) return fail(MRG_EINVAL, "unsupported dist/dtype combination");
+  if (dist == MRG_EXPONENTIAL && !(rate > 0.0 && rate < 1e300))
+    return fail(MRG_EINVAL, "exponential rate must be positive and finite");
+  if (n == 0 || s->n == 0) return MRG_OK;
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  if (ld < n) return fail(MRG_EINVAL, "ld < n");
+  if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
+  int rc = ensure_device();
+  if (rc) return rc;
+  mrg::GenConfig cfg;
+  cudaError_t e = mrg::launch_generate(dev(s), n, dist, dtype, rate, out, ld, cfg, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "generate_kernel");
+  const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
+  e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, consumed, 0, 0, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (advance)");
+  return MRG_OK;
+}
+
+int mrg_skip(const mrg_streams* s, uint64_t k_hi, uint64_t k_lo, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0 || (k_hi == 0 && k_lo == 0)) return MRG_OK;
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, k_lo, k_hi, 0, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (skip)");
+  return MRG_OK;
+}
+
+int mrg_substream_next(const mrg_streams* s, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_jump(s->sub, s->sub, s->cur, s->stride, s->n, 1, 0,
+                                   mrg::SUBSTREAM_LOG2, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (substream)");
+  return MRG_OK;
+}
+
+int mrg_reset_substream(const mrg_streams* s, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_jump(s->sub, s->cur, nullptr, s->stride, s->n, 0, 0, 0, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (reset substream)");
+  return MRG_OK;
+}
+
+int mrg_reset_stream(const mrg_streams* s, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_jump(s->start, s->cur, s->sub, s->stride, s->n, 0, 0, 0, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (reset stream)");
+  return MRG_OK;
+}
+
+int mrg_get_state(const mrg_streams* s, uint32_t* host, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  if (!host) return fail(MRG_EINVAL, "host buffer is NULL");
+  const uint32_t* src[3] = {s->cur, s->start, s->sub};
+  for (int a = 0; a < 3; ++a) {
+    cudaError_t e = cudaMemcpy2DAsync(host + (size_t)a * 6 * s->n, s->n * 4, src[a], s->stride * 4,
+                                      s->n * 4, 6, cudaMemcpyDeviceToHost, cs(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpy2DAsync (get_state)");
+  }
+  cudaError_t e = cudaStreamSynchronize(cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize (get_state)");
+  return MRG_OK;
+}
+
+int mrg_set_state(const mrg_streams* s, const uint32_t* host, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  if (!host) return fail(MRG_EINVAL, "host buffer is NULL");
+  const uint64_t n = s->n;
+  for (int a = 0; a < 3; ++a)
+    for (uint64_t i = 0; i < n; ++i) {
+      uint32_t st[6];
+      for (int k = 0; k < 6; ++k) st[k] = host[((size_t)a * 6 + k) * n + i];
+      if (!mrg::host::state_valid(st)) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "invalid state (array %d, stream %llu)", a,
+                      (unsigned long long)i);
+        return fail(MRG_EINVAL, buf);
+      }
+    }
+  uint32_t* dst[3] = {s->cur, s->start, s->sub};
+  for (int a = 0; a < 3; ++a) {
+    cudaError_t e = cudaMemcpy2DAsync(dst[a], s->stride * 4, host + (size_t)a * 6 * n, n * 4, n * 4,
+                                      6, cudaMemcpyHostToDevice, cs(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpy2DAsync (set_state)");
+  }
+  cudaError_t e = cudaStreamSynchronize(cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize (set_state)");
+  return MRG_OK;
+}
+
+int mrg_fused_pi_normsum(const mrg_streams* s, uint64_t draws, int64_t* count, double* sum,
+                         void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0) return MRG_OK;
+  if (!count || !sum) return fail(MRG_EINVAL, "count/sum is NULL");
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_fused(dev(s), (draws + 1) / 2, count, sum, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "fused_kernel");
+  return MRG_OK;
+}
+
+}  // extern "C"

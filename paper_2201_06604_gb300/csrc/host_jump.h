@@ -1,0 +1,23 @@
+// host_jump.h -- host-side jump-ahead helpers of libmrg32k3a (internal).
+#pragma once
+#include <stdint.h>
+
+namespace mrg {
+namespace host {
+
+constexpr int kJumpBits = 191;  // A^(2^i), i < 191: offsets < 2^128, stream index < 2^64
+
+// A_c^(2^i) mod m_c as uint32 (row-major 3x3), c = 0 (m1) and 1 (m2).
+void jump_table_u32(uint32_t out[2][kJumpBits][9]);
+
+// x1 words < m1, x2 words < m2, neither triple all zero.
+bool state_valid(const uint32_t s[6]);
+
+// s <- A^(e * 2^base) s, for 0 <= base and base + 63 < kJumpBits.
+void jump_pow2_multiple(uint32_t s[6], uint64_t e, int base);
+
+// True when RN64(1/(m1+1)) has exponent -32 and significand 2^52 + delta.
+bool norm_constant_ok(uint64_t delta);
+
+}  // namespace host
+}  // namespace mrg

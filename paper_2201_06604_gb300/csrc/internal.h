@@ -1,0 +1,51 @@
+// internal.h -- launchers shared by the C-ABI layer and the kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace mrg {
+
+struct DevStreams {
+  uint32_t* cur;
+  uint32_t* start;
+  uint32_t* sub;
+  uint64_t n;
+  uint64_t stride;
+};
+
+// Launch shape of the generate kernel.  Outputs never depend on it: every
+// segment starts with a jump to its absolute offset.
+struct GenConfig {
+  uint64_t seg_len = 0;   // draws per segment (multiple of the chunk); 0 = heuristic
+  int block = 256;        // threads per block (multiple of 32)
+  int chunk = 128;        // bytes per row chunk staged in shared memory: 128 or 256
+  int max_blocks = 0;     // 0 = fill every SM
+};
+
+extern std::atomic<uint64_t> g_launches;
+
+// Copies the jump tables into the current device's constant memory.
+cudaError_t upload_tables(const uint32_t* tab, size_t bytes);
+
+cudaError_t launch_create(const uint32_t seed[6], uint64_t n, const DevStreams& s,
+                          cudaStream_t st);
+
+// dst0 (and dst1 if not null) <- A^(e * 2^base) src, e = e_hi * 2^64 + e_lo,
+// for streams [0, ns).  Requires base + bitlen(e) <= JUMP_BITS.
+cudaError_t launch_jump(const uint32_t* src, uint32_t* dst0, uint32_t* dst1, uint64_t stride,
+                        uint64_t ns, uint64_t e_lo, uint64_t e_hi, int base, cudaStream_t st);
+
+// Generates n values per stream into out (stream-major, leading dimension
+// ld elements).  Does not advance the states.
+cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                            void* out, uint64_t ld, const GenConfig& cfg, cudaStream_t st);
+
+cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
+                         cudaStream_t st);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace mrg

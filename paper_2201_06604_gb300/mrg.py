@@ -1,0 +1,261 @@
+"""Python binding of libmrg32k3a (ctypes; argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; torch only
+provides device memory and CUDA streams.  If the compiled library is missing
+this module raises at import: there is no CPU fallback.
+
+Names follow the C ABI in include/mrg32k3a.h.  The module keeps a stream
+creator state like the paper's hidden creator seed (Sec. 2.1,
+setBaseCreator / createStreamsGpu): `set_base_creator(seed)` sets it, and every
+`create_streams(n)` call reads it and advances it past the streams it made.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+RAW, UNIFORM, NORMAL, EXPONENTIAL = 0, 1, 2, 3
+U32, F32, F64 = 0, 1, 2
+OK, EINVAL, ERANGE, ECUDA, EBUSY, ETIMEOUT = 0, -1, -2, -3, -4, -5
+
+DEFAULT_SEED = (12345, 12345, 12345, 12345, 12345, 12345)
+M1, M2 = 4294967087, 4294944443
+
+_DIST = {"raw": RAW, "uniform": UNIFORM, "normal": NORMAL, "exponential": EXPONENTIAL}
+_DTYPE = {torch.float32: F32, torch.float64: F64, torch.int32: U32}
+
+
+class MrgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Streams(ctypes.Structure):
+    _fields_ = [("cur", ctypes.c_void_p), ("start", ctypes.c_void_p), ("sub", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("stride", ctypes.c_uint64)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libmrg32k3a is not built ({path}); run "
+                          "`python -m paper_2201_06604_gb300.build` first")
+    L = ctypes.CDLL(path)
+    vp, u64, i32, u32p = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)
+    sp = ctypes.POINTER(_Streams)
+    sig = {
+        "mrg_last_error": ([], ctypes.c_char_p),
+        "mrg_launch_count": ([], u64),
+        "mrg_version": ([], ctypes.c_char_p),
+        "mrg_seed_check": ([u32p], i32),
+        "mrg_create_streams": ([u32p, u64, sp, u32p, vp], i32),
+        "mrg_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
+        "mrg_skip": ([sp, u64, u64, vp], i32),
+        "mrg_substream_next": ([sp, vp], i32),
+        "mrg_reset_substream": ([sp, vp], i32),
+        "mrg_reset_stream": ([sp, vp], i32),
+        "mrg_get_state": ([sp, u32p, vp], i32),
+        "mrg_set_state": ([sp, u32p, vp], i32),
+        "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise MrgError(rc, lib.mrg_last_error().decode())
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _u32_array(values) -> ctypes.Array:
+    a = (ctypes.c_uint32 * 6)(*[int(v) for v in values])
+    return a
+
+
+def launch_count() -> int:
+    return int(lib.mrg_launch_count())
+
+
+def seed_check(seed) -> bool:
+    return lib.mrg_seed_check(_u32_array(seed)) == OK
+
+
+class Streams:
+    """n streams on one device: three int32 tensors [6, n] holding the uint32
+    words of the current state, the stream start and the substream start."""
+
+    def __init__(self, n: int, device=None, *, _tensors=None):
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if _tensors is None:
+            self.buf = torch.empty((3, 6, max(n, 1)), dtype=torch.int32, device=dev)
+        else:
+            self.buf = _tensors
+        self.n = n
+        self._c = _Streams(self.buf[0].data_ptr(), self.buf[1].data_ptr(), self.buf[2].data_ptr(),
+                           n, self.buf.shape[2])
+
+    @property
+    def cur(self):
+        return self.buf[0, :, : self.n]
+
+    @property
+    def start(self):
+        return self.buf[1, :, : self.n]
+
+    @property
+    def sub(self):
+        return self.buf[2, :, : self.n]
+
+    @property
+    def device(self):
+        return self.buf.device
+
+    def view(self, a: int, m: int) -> "Streams":
+        """Streams [a, a + m) sharing this set's memory."""
+        if a < 0 or m < 0 or a + m > self.n:
+            raise IndexError("stream range out of bounds")
+        v = Streams.__new__(Streams)
+        v.buf, v.n = self.buf, m
+        v._c = _Streams(self.buf[0].data_ptr() + 4 * a, self.buf[1].data_ptr() + 4 * a,
+                        self.buf[2].data_ptr() + 4 * a, m, self.buf.shape[2])
+        v._parent = self
+        return v
+
+    def ptr(self):
+        return ctypes.byref(self._c)
+
+
+class _Creator:
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.seed = list(DEFAULT_SEED)
+
+
+_creator = _Creator()
+
+
+def set_base_creator(seed=DEFAULT_SEED):
+    """Sets the creator state that the next create_streams call starts from."""
+    if not seed_check(seed):
+        raise MrgError(EINVAL, "invalid seed")
+    with _creator.lock:
+        _creator.seed = [int(v) for v in seed]
+
+
+def get_base_creator():
+    with _creator.lock:
+        return tuple(_creator.seed)
+
+
+def create_streams(n: int, device=None, seed=None, stream=None) -> Streams:
+    """Creates n streams on the device.  With seed=None the module's creator
+    state is used and advanced by n streams (Sec. 2.1); an explicit seed
+    leaves the creator untouched."""
+    s = Streams(n, device)
+    nxt = (ctypes.c_uint32 * 6)()
+    with torch.cuda.device(s.device):
+        if seed is None:
+            with _creator.lock:
+                _check(lib.mrg_create_streams(_u32_array(_creator.seed), n, s.ptr(), nxt,
+                                              _stream_handle(stream)))
+                _creator.seed = list(nxt)
+        else:
+            _check(lib.mrg_create_streams(_u32_array(seed), n, s.ptr(), nxt,
+                                          _stream_handle(stream)))
+    s.next_seed = tuple(nxt)
+    return s
+
+
+def _dtype_code(dist: int, dtype) -> int:
+    if dist == RAW:
+        return U32
+    return {torch.float32: F32, torch.float64: F64}[dtype]
+
+
+def generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64, rate: float = 1.0,
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """n values per stream into a [streams.n, n] tensor (stream-major), or
+    into `out` (2-D, row stride = leading dimension, unit column stride).
+    Raw draws come back as int32 holding the uint32 bit patterns."""
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    dt = torch.int32 if d == RAW else dtype
+    code = _dtype_code(d, dt)
+    if out is None:
+        out = torch.empty((streams.n, n), dtype=dt, device=streams.device)
+    if out.dim() != 2 or out.shape[0] < streams.n or out.shape[1] < n or out.stride(1) != 1:
+        raise ValueError("out must be [>= n_streams, >= n] with unit column stride")
+    if out.dtype != dt:
+        raise ValueError(f"out dtype {out.dtype} != {dt}")
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_generate(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
+                                out.stride(0), _stream_handle(stream)))
+    return out
+
+
+def skip(streams: Streams, k: int, stream=None):
+    if k < 0 or k >= 1 << 128:
+        raise ValueError("k must be in [0, 2^128)")
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_skip(streams.ptr(), k >> 64, k & ((1 << 64) - 1), _stream_handle(stream)))
+
+
+def substream_next(streams: Streams, stream=None):
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_substream_next(streams.ptr(), _stream_handle(stream)))
+
+
+def reset_substream(streams: Streams, stream=None):
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_reset_substream(streams.ptr(), _stream_handle(stream)))
+
+
+def reset_stream(streams: Streams, stream=None):
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_reset_stream(streams.ptr(), _stream_handle(stream)))
+
+
+def get_state(streams: Streams, stream=None) -> np.ndarray:
+    """Host checkpoint [3, 6, n] uint32: (cur, start, sub)."""
+    host = np.zeros((3, 6, max(streams.n, 1)), np.uint32)
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_get_state(streams.ptr(), host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                 _stream_handle(stream)))
+    return host[:, :, : streams.n].copy()
+
+
+def set_state(streams: Streams, host, stream=None):
+    host = np.ascontiguousarray(host, dtype=np.uint32)
+    if host.shape != (3, 6, streams.n):
+        raise ValueError("state must be [3, 6, n]")
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_set_state(streams.ptr(), host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                 _stream_handle(stream)))
+
+
+def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream=None):
+    if count is None:
+        count = torch.empty(streams.n, dtype=torch.int64, device=streams.device)
+    if sum_ is None:
+        sum_ = torch.empty(streams.n, dtype=torch.float64, device=streams.device)
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_fused_pi_normsum(streams.ptr(), draws, count.data_ptr(), sum_.data_ptr(),
+                                        _stream_handle(stream)))
+    return count, sum_

@@ -1,0 +1,54 @@
+// Host-side check of the kernels' integer arithmetic, compiled by nvcc for
+// the CPU from the same header the kernels use (test infrastructure).
+//   mode "uniform": for every z in [1, m1], uniform_bits64(z) equals the bits
+//     of the IEEE product (double)z * RN64(1/(m1+1)), and f32_bits_from_f64
+//     equals the bits of (float) of that product.
+//   mode "step" n seed: prints n outputs of mrg::step from a state.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "../../paper_2201_06604_gb300/csrc/mrg32k3a_core.cuh"
+
+static int check_uniform(unsigned lo, unsigned hi) {
+  volatile double norm_v = 1.0 / 4294967088.0;
+  const double norm = norm_v;
+  long long bad = 0;
+#pragma omp parallel for reduction(+ : bad) schedule(static, 1 << 16)
+  for (long long zz = lo; zz <= (long long)hi; ++zz) {
+    uint32_t z = (uint32_t)zz;
+    double d = (double)z * norm;
+    uint64_t want;
+    std::memcpy(&want, &d, 8);
+    float f = (float)d;
+    uint32_t wantf;
+    std::memcpy(&wantf, &f, 4);
+    uint64_t got = mrg::uniform_bits64(z);
+    if (got != want || mrg::f32_bits_from_f64(got) != wantf) {
+      if (bad < 5) std::printf("mismatch z=%u got=%016llx want=%016llx\n", z,
+                               (unsigned long long)got, (unsigned long long)want);
+      ++bad;
+    }
+  }
+  std::printf("checked [%u, %u]: %lld mismatches\n", lo, hi, bad);
+  return bad != 0;
+}
+
+int main(int argc, char** argv) {
+  if (argc >= 2 && !std::strcmp(argv[1], "uniform")) {
+    unsigned lo = argc > 2 ? (unsigned)std::strtoul(argv[2], 0, 10) : 1u;
+    unsigned hi = argc > 3 ? (unsigned)std::strtoul(argv[3], 0, 10) : mrg::M1;
+    return check_uniform(lo, hi);
+  }
+  if (argc >= 9 && !std::strcmp(argv[1], "step")) {
+    long n = std::atol(argv[2]);
+    mrg::State s{(uint32_t)std::strtoul(argv[3], 0, 10), (uint32_t)std::strtoul(argv[4], 0, 10),
+                 (uint32_t)std::strtoul(argv[5], 0, 10), (uint32_t)std::strtoul(argv[6], 0, 10),
+                 (uint32_t)std::strtoul(argv[7], 0, 10), (uint32_t)std::strtoul(argv[8], 0, 10)};
+    for (long i = 0; i < n; ++i) std::printf("%u\n", mrg::step(s));
+    std::printf("%u %u %u %u %u %u\n", s.a0, s.a1, s.a2, s.b0, s.b1, s.b2);
+    return 0;
+  }
+  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5\n");
+  return 2;
+}
