@@ -27,7 +27,7 @@ import numpy as np  # noqa: E402
 METRIC = "MRG32k3a draws/s & GB/s vs HBM peak; batched/plain speedup; p99 latency"
 VARIANTS = (("uniform", "f64"), ("uniform", "f32"), ("normal", "f64"), ("normal", "f32"),
             ("exponential", "f32"))
-ES = {"f64": 8, "f32": 4}
+ES = {"f64": 8, "f32": 4, "u32": 4}
 
 
 def env_rank():
@@ -169,6 +169,13 @@ def run_gpu(args):
     ns, n = W.MATERIALISED["streams"], W.MATERIALISED["draws"]
     if args.quick:
         ns, n = 4096, 4096
+    if args.streams:
+        ns = args.streams
+    if args.draws:
+        n = args.draws
+    variants_run = VARIANTS
+    if args.only:
+        variants_run = tuple(tuple(v.split(":")) for v in args.only.split(","))
     total_out = ns * n
     # Replicas: rank r owns streams [r ns, (r+1) ns) of the creator sequence.
     seed = tuple(W.PAPER_SEED)
@@ -177,8 +184,9 @@ def run_gpu(args):
     s = mrg.Streams(ns, dev)
     buf = torch.empty(total_out * 8, dtype=torch.uint8, device=dev)
     outs = {"f64": buf.view(torch.float64).view(ns, n),
-            "f32": buf[: total_out * 4].view(torch.float32).view(ns, n)}
-    tdt = {"f64": torch.float64, "f32": torch.float32}
+            "f32": buf[: total_out * 4].view(torch.float32).view(ns, n),
+            "u32": buf[: total_out * 4].view(torch.int32).view(ns, n)}
+    tdt = {"f64": torch.float64, "f32": torch.float32, "u32": torch.int32}
     stream = torch.cuda.current_stream()
 
     def create():
@@ -188,7 +196,7 @@ def run_gpu(args):
 
     def step(events=None):
         create()
-        for i, (d, dt) in enumerate(VARIANTS):
+        for i, (d, dt) in enumerate(variants_run):
             if events is not None:
                 events[i][0].record(stream)
             mrg.generate(s, n, d, tdt[dt], out=outs[dt])
@@ -200,7 +208,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in VARIANTS]
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in variants_run]
           for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -235,7 +243,7 @@ def run_gpu(args):
     adv_ms = e0.elapsed_time(e1) / 20
 
     variants = []
-    for i, (d, dt) in enumerate(VARIANTS):
+    for i, (d, dt) in enumerate(variants_run):
         t_call = float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
         t_kern = max(t_call - adv_ms, 1e-6)
         algo = total_out * ES[dt] + ns * 24  # outputs written + states read
@@ -248,8 +256,8 @@ def run_gpu(args):
     for v in variants:
         v["hbm_frac"] = v["gbs"] / hbm
 
-    draws_step = total_out * len(VARIANTS)
-    bytes_step = sum(total_out * ES[dt] for _, dt in VARIANTS)
+    draws_step = total_out * len(variants_run)
+    bytes_step = sum(total_out * ES[dt] for _, dt in variants_run)
     value = draws_step * world / (per_step_ms / 1e3)
 
     # e2e through the public API with host buffers: seed from pinned host
@@ -263,7 +271,7 @@ def run_gpu(args):
         def e2e_step():
             seed_dev.copy_(seed_host, non_blocking=True)
             create()
-            for d, dt in VARIANTS:
+            for d, dt in variants_run:
                 mrg.generate(s, n, d, tdt[dt], out=outs[dt])
                 nb = total_out * ES[dt]
                 host[:nb].copy_(buf[:nb], non_blocking=True)
@@ -326,6 +334,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small shapes (development only)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")
+    ap.add_argument("--draws", type=int, default=0, help="override draws per stream (profiling)")
+    ap.add_argument("--only", default="", help="comma list of dist:dtype variants (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -113,6 +113,8 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   if (n == 0 || s->n == 0) return MRG_OK;
   if (!out) return fail(MRG_EINVAL, "out is NULL");
   if (ld < n) return fail(MRG_EINVAL, "ld < n");
+  if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
+    return fail(MRG_EINVAL, "out is not aligned to its element size");
   if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
   int rc = ensure_device();
   if (rc) return rc;

@@ -18,9 +18,8 @@ struct DevStreams {
 // Launch shape of the generate kernel.  Outputs never depend on it: every
 // segment starts with a jump to its absolute offset.
 struct GenConfig {
-  uint64_t seg_len = 0;   // draws per segment (multiple of the chunk); 0 = heuristic
-  int block = 256;        // threads per block (multiple of 32)
-  int chunk = 128;        // bytes per row chunk staged in shared memory: 128 or 256
+  uint64_t seg_len = 0;   // draws per segment (rounded up to a multiple of 8); 0 = heuristic
+  int block = 256;        // threads per block (multiple of 32, <= 256)
   int max_blocks = 0;     // 0 = fill every SM
 };
 

@@ -12,11 +12,12 @@
 // the recurrence in registers.  Segment q of the flattened index runs stream
 // q mod ns at segment q div ns, so the 32 lanes of a warp share the segment
 // offset whenever ns >= 32 and the jump's table reads are warp-uniform.
-// Outputs go through a per-lane row of shared memory (CHUNK bytes, padded by
-// 16 B so that the 8 lanes of a 128-bit store phase hit distinct banks) and
-// leave with one cp.async.bulk (TMA bulk copy) per row chunk: each lane's
-// destination is contiguous, so the copy engine writes whole 128-byte lines
-// while the SM goes on with the next chunk's arithmetic.
+// Each lane's outputs are contiguous in its row, so a lane stores whole
+// 32-byte sectors with one 256-bit st.global per 32 bytes: the L2 receives
+// full-sector writes and nothing is staged in shared memory.  (A staged
+// variant -- per-lane shared-memory rows drained by cp.async.bulk -- was
+// measured slower: its shared memory capped occupancy at 3 blocks per SM,
+// and the recurrence is bound by integer issue, not by the store path.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -128,84 +129,78 @@ __global__ void __launch_bounds__(256) jump_kernel(const uint32_t* src, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// TMA bulk-copy primitives (shared -> global), per thread
+// Vector stores: each lane writes whole 32-byte sectors of its own row, so
+// the L2 receives full-sector writes without any staging in shared memory.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void fence_proxy_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_s2g(void* gdst, uint32_t ssrc, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-               :: "l"(gdst), "r"(ssrc), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_wait_read0() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-
-// ---------------------------------------------------------------------------
-// Output pieces: 16 bytes of consecutive outputs of one stream
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ uint4 pack64(uint64_t a, uint64_t b) {
-  return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
-}
-
-__device__ __forceinline__ uint4 pack_d(double a, double b) {
-  return pack64((uint64_t)__double_as_longlong(a), (uint64_t)__double_as_longlong(b));
-}
-
-template <int DIST, int DT>
-__device__ __forceinline__ uint4 piece(State& s, double inv_rate) {
-  if constexpr (DIST == MRG_RAW) {
-    uint32_t z0 = step(s), z1 = step(s), z2 = step(s), z3 = step(s);
-    return make_uint4(z0, z1, z2, z3);
-  } else if constexpr (DIST == MRG_UNIFORM && DT == MRG_F64) {
-    uint64_t u0 = uniform_bits64(step(s));
-    uint64_t u1 = uniform_bits64(step(s));
-    return pack64(u0, u1);
-  } else if constexpr (DIST == MRG_UNIFORM) {
-    uint32_t v0 = f32_bits_from_f64(uniform_bits64(step(s)));
-    uint32_t v1 = f32_bits_from_f64(uniform_bits64(step(s)));
-    uint32_t v2 = f32_bits_from_f64(uniform_bits64(step(s)));
-    uint32_t v3 = f32_bits_from_f64(uniform_bits64(step(s)));
-    return make_uint4(v0, v1, v2, v3);
-  } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F64) {
-    uint32_t z1 = step(s);
-    uint32_t z2 = step(s);
-    double x, y;
-    box_muller_f64(z1, z2, x, y);
-    return pack_d(x, y);
-  } else if constexpr (DIST == MRG_NORMAL) {
-    uint32_t z1 = step(s);
-    uint32_t z2 = step(s);
-    uint32_t z3 = step(s);
-    uint32_t z4 = step(s);
-    double x0, y0, x1, y1;
-    box_muller_f64(z1, z2, x0, y0);
-    box_muller_f64(z3, z4, x1, y1);
-    return make_uint4(__float_as_uint(__double2float_rn(x0)), __float_as_uint(__double2float_rn(y0)),
-                      __float_as_uint(__double2float_rn(x1)), __float_as_uint(__double2float_rn(y1)));
-  } else if constexpr (DT == MRG_F64) {  // exponential
-    double e0 = exponential_f64(step(s), inv_rate);
-    double e1 = exponential_f64(step(s), inv_rate);
-    return pack_d(e0, e1);
+template <int VB>
+__device__ __forceinline__ void store_vec(char* p, const uint32_t* w) {
+  if constexpr (VB == 32) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]),
+                    "r"(w[6]), "r"(w[7]) : "memory");
+  } else if constexpr (VB == 16) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
+  } else if constexpr (VB == 8) {
+    asm volatile("st.global.v2.b32 [%0], {%1, %2};" :: "l"(p), "r"(w[0]), "r"(w[1]) : "memory");
   } else {
-    float e0 = __double2float_rn(exponential_f64(step(s), inv_rate));
-    float e1 = __double2float_rn(exponential_f64(step(s), inv_rate));
-    float e2 = __double2float_rn(exponential_f64(step(s), inv_rate));
-    float e3 = __double2float_rn(exponential_f64(step(s), inv_rate));
-    return make_uint4(__float_as_uint(e0), __float_as_uint(e1), __float_as_uint(e2),
-                      __float_as_uint(e3));
+    asm volatile("st.global.b32 [%0], %1;" :: "l"(p), "r"(w[0]) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Output units: UE consecutive outputs of one stream as 32-bit words
+// ---------------------------------------------------------------------------
+
+struct Consts {
+  uint64_t k1, k2;   // the offset-form addends K1, K2 (kept in registers)
+  double inv_rate;
+};
+
+template <int DIST, int DT, int UE>
+__device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c) {
+  if constexpr (DIST == MRG_RAW) {
+#pragma unroll
+    for (int e = 0; e < UE; ++e) w[e] = step_fast(s, c.k1, c.k2);
+  } else if constexpr (DIST == MRG_UNIFORM && DT == MRG_F64) {
+#pragma unroll
+    for (int e = 0; e < UE; ++e) {
+      uint64_t u = uniform_bits64_fast(step_fast(s, c.k1, c.k2));
+      w[2 * e] = (uint32_t)u;
+      w[2 * e + 1] = (uint32_t)(u >> 32);
+    }
+  } else if constexpr (DIST == MRG_UNIFORM) {
+#pragma unroll
+    for (int e = 0; e < UE; ++e)
+      w[e] = f32_bits_from_f64(uniform_bits64_fast(step_fast(s, c.k1, c.k2)));
+  } else if constexpr (DIST == MRG_NORMAL) {
+#pragma unroll 1
+    for (int p = 0; p < UE / 2; ++p) {
+      uint32_t z1 = step_fast(s, c.k1, c.k2);
+      uint32_t z2 = step_fast(s, c.k1, c.k2);
+      double x, y;
+      box_muller_f64(z1, z2, x, y);
+      if constexpr (DT == MRG_F64) {
+        uint64_t bx = (uint64_t)__double_as_longlong(x), by = (uint64_t)__double_as_longlong(y);
+        w[4 * p] = (uint32_t)bx; w[4 * p + 1] = (uint32_t)(bx >> 32);
+        w[4 * p + 2] = (uint32_t)by; w[4 * p + 3] = (uint32_t)(by >> 32);
+      } else {
+        w[2 * p] = __float_as_uint(__double2float_rn(x));
+        w[2 * p + 1] = __float_as_uint(__double2float_rn(y));
+      }
+    }
+  } else {  // exponential
+#pragma unroll 1
+    for (int e = 0; e < UE; ++e) {
+      double v = exponential_f64(step_fast(s, c.k1, c.k2), c.inv_rate);
+      if constexpr (DT == MRG_F64) {
+        uint64_t bv = (uint64_t)__double_as_longlong(v);
+        w[2 * e] = (uint32_t)bv; w[2 * e + 1] = (uint32_t)(bv >> 32);
+      } else {
+        w[e] = __float_as_uint(__double2float_rn(v));
+      }
+    }
   }
 }
 
@@ -217,29 +212,29 @@ struct GenArgs {
   const uint32_t* cur;
   uint64_t stride, ns;
   uint64_t n;      // outputs per stream
-  uint64_t L;      // segment length in outputs (= draws), multiple of the chunk
+  uint64_t L;      // segment length in outputs (= draws), multiple of 8
   uint64_t total;  // ns * ceil(n / L) segments
   char* out;
   uint64_t ld;     // elements
-  double inv_rate;
+  Consts c;
 };
 
-template <int DIST, int DT, int CHUNK, bool BULK>
+// VB: bytes per vector store (32, 16, 8 or 4), the largest width that the
+// output pointer and row pitch allow.
+template <int DIST, int DT, int VB>
 __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int ES = DT == MRG_F64 ? 8 : 4;     // bytes per element
-  constexpr int PIECES = CHUNK / 16;
-  constexpr int CE = CHUNK / ES;                // elements per row chunk
-  constexpr int PE = 16 / ES;                   // elements per piece
-  constexpr int PITCH = CHUNK + 16;
-  constexpr bool CHEAP = DIST == MRG_RAW || DIST == MRG_UNIFORM;
+  constexpr int ES = DT == MRG_F64 ? 8 : 4;
+  constexpr int UB = (DIST == MRG_NORMAL && VB < 2 * ES) ? 2 * ES : (VB < ES ? ES : VB);
+  constexpr int UE = UB / ES;          // outputs per unit
+  constexpr int UW = UB / 4;           // 32-bit words per unit
+  constexpr int VS = VB < ES ? ES : VB;  // store width actually used
+  constexpr int VW = VS / 4;
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  unsigned char* row = smem + (size_t)(warp * 32 + lane) * PITCH;
-  const uint32_t row_s = (uint32_t)__cvta_generic_to_shared(row);
   const uint64_t ntiles = (a.total + 31) >> 5;
+  const Consts c = a.c;
 
   for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < ntiles;
        w += (uint64_t)gridDim.x * wpb) {
@@ -252,61 +247,26 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
     }
     const uint64_t off = g * a.L;
     const uint32_t cnt = valid ? (uint32_t)min(a.L, a.n - off) : 0u;
-    State st = valid ? load_state(a.cur, a.stride, s) : State{1, 1, 1, 1, 1, 1};
-    jump_lanes(st, off, 0);
+    State st0 = valid ? load_state(a.cur, a.stride, s) : State{1, 1, 1, 1, 1, 1};
+    jump_lanes(st0, off, 0);
+    TState st = to_offset(st0);
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
     char* gdst = a.out + (s * a.ld + off) * ES;
 
-    for (uint32_t c0 = 0; c0 < cmax; c0 += CE) {
-      if constexpr (BULK) {
-        bulk_wait_read0();  // the previous chunk's copy has read this row
-        if constexpr (CHEAP) {
+#pragma unroll 2
+    for (uint32_t i = 0; i < cmax; i += UE) {
+      uint32_t wv[UW];
+      produce<DIST, DT, UE>(st, wv, c);
+      if (i + UE <= cnt) {
 #pragma unroll
-          for (int p = 0; p < PIECES; ++p)
-            *reinterpret_cast<uint4*>(row + p * 16) = piece<DIST, DT>(st, a.inv_rate);
-        } else {
-#pragma unroll 1
-          for (int p = 0; p < PIECES; ++p)
-            *reinterpret_cast<uint4*>(row + p * 16) = piece<DIST, DT>(st, a.inv_rate);
-        }
-        if (c0 < cnt) {
-          const uint32_t m = min((uint32_t)CE, cnt - c0);
-          const uint32_t bytes = m * ES;
-          const uint32_t full = bytes & ~15u;
-          if (full) {
-            fence_proxy_async_shared();
-            bulk_s2g(gdst + (size_t)c0 * ES, row_s, full);
-            bulk_commit();
-          }
-          for (uint32_t b = full; b < bytes; b += 4)
-            *reinterpret_cast<uint32_t*>(gdst + (size_t)c0 * ES + b) =
-                *reinterpret_cast<const uint32_t*>(row + b);
-        }
-      } else {
-#pragma unroll 1
-        for (int p = 0; p < PIECES; ++p) {
-          uint4 v = piece<DIST, DT>(st, a.inv_rate);
-          const uint32_t e0 = c0 + p * PE;
-          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-          if constexpr (ES == 8) {
-            if (e0 < cnt) {
-              uint32_t* d = reinterpret_cast<uint32_t*>(gdst + (size_t)e0 * 8);
-              d[0] = w4[0]; d[1] = w4[1];
-            }
-            if (e0 + 1 < cnt) {
-              uint32_t* d = reinterpret_cast<uint32_t*>(gdst + (size_t)(e0 + 1) * 8);
-              d[0] = w4[2]; d[1] = w4[3];
-            }
-          } else {
+        for (int v = 0; v < UB / VS; ++v) store_vec<VS>(gdst + (size_t)i * ES + v * VS, wv + v * VW);
+      } else if (i < cnt) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (e0 + k < cnt) *reinterpret_cast<uint32_t*>(gdst + (size_t)(e0 + k) * 4) = w4[k];
-          }
-        }
+        for (int e = 0; e < UE; ++e)
+          if (i + e < cnt) store_vec<ES>(gdst + (size_t)(i + e) * ES, wv + e * (ES / 4));
       }
     }
   }
-  if constexpr (BULK) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -314,16 +274,17 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) fused_kernel(uint32_t* cur, uint64_t stride, uint64_t ns,
-                                                    uint64_t pairs, int64_t* count, double* sum) {
+                                                    uint64_t pairs, int64_t* count, double* sum,
+                                                    uint64_t k1, uint64_t k2) {
   constexpr uint64_t MSQ = MNORM * MNORM;  // (m1+1)^2 < 2^64
   const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += step_all) {
-    State s = load_state(cur, stride, i);
+    TState s = to_offset(load_state(cur, stride, i));
     int64_t cnt = 0;
     double acc = 0.0;
     for (uint64_t k = 0; k < pairs; ++k) {
-      uint32_t za = step(s);
-      uint32_t zb = step(s);
+      uint32_t za = step_fast(s, k1, k2);
+      uint32_t zb = step_fast(s, k1, k2);
       uint64_t sa = (uint64_t)za * za, sb = (uint64_t)zb * zb;
       uint64_t ss = sa + sb;
       cnt += (ss >= sa) & (ss < MSQ);  // no carry out of 64 bits and below M^2
@@ -332,7 +293,7 @@ __global__ void __launch_bounds__(256) fused_kernel(uint32_t* cur, uint64_t stri
       acc += x;
       acc += y;
     }
-    store_state(cur, stride, i, s);
+    store_state(cur, stride, i, from_offset(s));
     count[i] = cnt;
     sum[i] = acc;
   }
@@ -396,28 +357,24 @@ cudaError_t launch_jump(const uint32_t* src, uint32_t* dst0, uint32_t* dst1, uin
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
-  fused_kernel<<<grid_for(s.n, 256, 8), 256, 0, st>>>(s.cur, s.stride, s.n, pairs, count, sum);
+  fused_kernel<<<grid_for(s.n, 256, 8), 256, 0, st>>>(s.cur, s.stride, s.n, pairs, count, sum,
+                                                      K1, K2);
   return after_launch();
 }
 
 namespace {
 
-template <int DIST, int DT, int CHUNK, bool BULK>
+template <int DIST, int DT, int VB>
 cudaError_t launch_gen_t(const GenArgs& a, const GenConfig& cfg, cudaStream_t st) {
-  auto kern = generate_kernel<DIST, DT, CHUNK, BULK>;
+  auto kern = generate_kernel<DIST, DT, VB>;
   const int block = cfg.block;
-  const size_t smem = BULK ? (size_t)block * (CHUNK + 16) : 0;
-  static thread_local int occ_cache[64][2] = {};
+  static thread_local int occ_cache[64][9] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  int& occ = occ_cache[dev & 63][block == 256 ? 0 : 1];
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  int& occ = occ_cache[dev & 63][block / 32];
   if (occ == 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, block, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, block, 0);
     if (e != cudaSuccess) return e;
     occ = v > 0 ? v : 1;
   }
@@ -427,15 +384,18 @@ cudaError_t launch_gen_t(const GenArgs& a, const GenConfig& cfg, cudaStream_t st
   uint64_t cap = (uint64_t)sm_count() * occ;
   if (cfg.max_blocks > 0) cap = std::min<uint64_t>(cap, (uint64_t)cfg.max_blocks);
   blocks = std::max<uint64_t>(1, std::min(blocks, cap));
-  kern<<<(unsigned)blocks, block, smem, st>>>(a);
+  kern<<<(unsigned)blocks, block, 0, st>>>(a);
   return after_launch();
 }
 
 template <int DIST, int DT>
-cudaError_t launch_gen_dt(const GenArgs& a, bool bulk, const GenConfig& cfg, cudaStream_t st) {
-  if (!bulk) return launch_gen_t<DIST, DT, 128, false>(a, cfg, st);
-  if (cfg.chunk == 256) return launch_gen_t<DIST, DT, 256, true>(a, cfg, st);
-  return launch_gen_t<DIST, DT, 128, true>(a, cfg, st);
+cudaError_t launch_gen_dt(const GenArgs& a, int vb, const GenConfig& cfg, cudaStream_t st) {
+  switch (vb) {
+    case 32: return launch_gen_t<DIST, DT, 32>(a, cfg, st);
+    case 16: return launch_gen_t<DIST, DT, 16>(a, cfg, st);
+    case 8: return launch_gen_t<DIST, DT, 8>(a, cfg, st);
+    default: return launch_gen_t<DIST, DT, 4>(a, cfg, st);
+  }
 }
 
 }  // namespace
@@ -445,19 +405,18 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
   if (s.n == 0 || n == 0) return cudaSuccess;
   GenConfig cfg = cfg_in;
   if (cfg.block <= 0 || cfg.block > 256 || cfg.block % 32) cfg.block = 256;
-  if (cfg.chunk != 256) cfg.chunk = 128;
   const int es = dtype == MRG_F64 ? 8 : 4;
-  const uint64_t ce = (uint64_t)cfg.chunk / es;
+  const uint64_t ce = 8;  // segment lengths are multiples of 8 outputs (32-byte aligned starts)
   uint64_t L = cfg.seg_len;
   if (L == 0) {
-    // Heuristic: about 16 segments per resident lane slot, at least 4 chunks,
-    // at most the whole row.
+    // Heuristic: about 8 segments per resident lane slot, at least 512 draws
+    // (jump cost amortised), at most the whole row.
     const uint64_t lanes = (uint64_t)sm_count() * 2048;
     const uint64_t total = n * s.n;
-    L = total / (lanes * 16);
-    L = std::max<uint64_t>(L, 4 * ce);
+    L = total / (lanes * 8);
+    L = std::max<uint64_t>(L, 512);
   }
-  L = (L + ce - 1) / ce * ce;                 // whole chunks (even: pairs stay aligned)
+  L = (L + ce - 1) / ce * ce;                 // multiple of 8 (even: pairs stay aligned)
   const uint64_t ncap = (n + ce - 1) / ce * ce;
   L = std::min(L, ncap);
   GenArgs a;
@@ -469,16 +428,20 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
   a.total = s.n * ((n + L - 1) / L);
   a.out = reinterpret_cast<char*>(out);
   a.ld = ld;
-  a.inv_rate = 1.0 / rate;
-  const bool bulk = (reinterpret_cast<uintptr_t>(out) % 16 == 0) && ((ld * es) % 16 == 0);
+  a.c.k1 = K1;
+  a.c.k2 = K2;
+  a.c.inv_rate = 1.0 / rate;
+  // widest store the row starts allow: out address and row pitch alignment
+  const uint64_t align = (reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) & ~((reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) - 1);
+  const int vb = (int)std::min<uint64_t>(align, 32);
   switch (dist * 4 + dtype) {
-    case MRG_RAW * 4 + MRG_U32: return launch_gen_dt<MRG_RAW, MRG_U32>(a, bulk, cfg, st);
-    case MRG_UNIFORM * 4 + MRG_F32: return launch_gen_dt<MRG_UNIFORM, MRG_F32>(a, bulk, cfg, st);
-    case MRG_UNIFORM * 4 + MRG_F64: return launch_gen_dt<MRG_UNIFORM, MRG_F64>(a, bulk, cfg, st);
-    case MRG_NORMAL * 4 + MRG_F32: return launch_gen_dt<MRG_NORMAL, MRG_F32>(a, bulk, cfg, st);
-    case MRG_NORMAL * 4 + MRG_F64: return launch_gen_dt<MRG_NORMAL, MRG_F64>(a, bulk, cfg, st);
-    case MRG_EXPONENTIAL * 4 + MRG_F32: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F32>(a, bulk, cfg, st);
-    case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64>(a, bulk, cfg, st);
+    case MRG_RAW * 4 + MRG_U32: return launch_gen_dt<MRG_RAW, MRG_U32>(a, vb, cfg, st);
+    case MRG_UNIFORM * 4 + MRG_F32: return launch_gen_dt<MRG_UNIFORM, MRG_F32>(a, vb, cfg, st);
+    case MRG_UNIFORM * 4 + MRG_F64: return launch_gen_dt<MRG_UNIFORM, MRG_F64>(a, vb, cfg, st);
+    case MRG_NORMAL * 4 + MRG_F32: return launch_gen_dt<MRG_NORMAL, MRG_F32>(a, vb, cfg, st);
+    case MRG_NORMAL * 4 + MRG_F64: return launch_gen_dt<MRG_NORMAL, MRG_F64>(a, vb, cfg, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F32: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F32>(a, vb, cfg, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64>(a, vb, cfg, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -42,11 +42,13 @@ int main(int argc, char** argv) {
   }
   if (argc >= 9 && !std::strcmp(argv[1], "step")) {
     long n = std::atol(argv[2]);
-    mrg::State s{(uint32_t)std::strtoul(argv[3], 0, 10), (uint32_t)std::strtoul(argv[4], 0, 10),
+    mrg::State c{(uint32_t)std::strtoul(argv[3], 0, 10), (uint32_t)std::strtoul(argv[4], 0, 10),
                  (uint32_t)std::strtoul(argv[5], 0, 10), (uint32_t)std::strtoul(argv[6], 0, 10),
                  (uint32_t)std::strtoul(argv[7], 0, 10), (uint32_t)std::strtoul(argv[8], 0, 10)};
+    mrg::TState s = mrg::to_offset(c);
     for (long i = 0; i < n; ++i) std::printf("%u\n", mrg::step(s));
-    std::printf("%u %u %u %u %u %u\n", s.a0, s.a1, s.a2, s.b0, s.b1, s.b2);
+    c = mrg::from_offset(s);
+    std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
     return 0;
   }
   std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5\n");

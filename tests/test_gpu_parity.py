@@ -102,7 +102,7 @@ def test_plain_1024x1024_f64_uniform_bit_exact(M):
     assert np.array_equal(host_states(M, s), after)
 
 
-CASES = [(33, 1000), (1, 4097), (100, 17), (7, 1), (64, 2048), (5, 3333)]
+CASES = [(33, 1000), (1, 4097), (100, 17), (7, 1), (64, 2048), (5, 3333), (9, 1002), (40, 998)]
 DISTS = [("raw", torch.int32), ("uniform", torch.float64), ("uniform", torch.float32),
          ("normal", torch.float64), ("normal", torch.float32),
          ("exponential", torch.float64), ("exponential", torch.float32)]
