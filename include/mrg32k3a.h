@@ -104,17 +104,31 @@ int mrg_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams *s,
  * array out, stream-major: value i of stream j at out[j * ld + i], ld >= n.
  * dist / dtype: MRG_RAW with MRG_U32; MRG_UNIFORM, MRG_NORMAL or
  * MRG_EXPONENTIAL with MRG_F32 or MRG_F64.  rate is the exponential rate
- * (> 0; ignored otherwise).  Raw and uniform outputs are bit-exact functions
- * of the state; normals and exponentials are within 1e-12 absolute (fp64) or
- * 2 ulp (fp32) of the exact transform of the same integers.  Each stream's
+ * (in [2^-64, 2^64]; ignored otherwise).  Raw and uniform outputs are
+ * bit-exact functions of the state; normals and exponentials are within
+ * 1e-12 absolute (fp64; exponentials 1e-12 / min(rate, 1)) or 2 ulp of the
+ * fp32 spacing (fp32) of the exact transform of the same integers, evaluated
+ * in double-float arithmetic on the FP32 pipe.  Each stream's
  * `cur` advances by the draws consumed: n for raw, uniform and exponential,
  * n + (n mod 2) for normals (an odd count discards the last sine output), so
  * the next call continues each stream exactly (Sec. 2.2).  The output does
  * not depend on the launch configuration.  out must not overlap the states.
- * Errors: MRG_EINVAL (bad dist/dtype pair, rate <= 0 for exponentials, ld < n,
- * NULL pointers), MRG_ECUDA. */
+ * Errors: MRG_EINVAL (bad dist/dtype pair, rate outside [2^-64, 2^64] for
+ * exponentials, ld < n, NULL pointers, out not aligned to its element),
+ * MRG_ECUDA. */
 int mrg_generate(const mrg_streams *s, uint64_t n_per_stream, int dist, int dtype,
                  double rate, void *out, uint64_t ld, void *stream);
+
+/* Applies the output transform of mrg_generate to caller-provided raw draws:
+ * z (device, n values in [1, m1], e.g. from MRG_RAW) -> out (device, n values
+ * of dtype).  MRG_UNIFORM, MRG_NORMAL (consecutive pairs (z[2k], z[2k+1]) give
+ * out[2k] = X, out[2k+1] = Y; an odd n computes the last X from (z[n-1], 1)) or
+ * MRG_EXPONENTIAL with MRG_F32 / MRG_F64, same accuracy as mrg_generate.
+ * Values of z outside [1, m1] give unspecified (but memory-safe) outputs.
+ * Errors: MRG_EINVAL (NULL pointers with n > 0, bad dist/dtype or rate),
+ * MRG_ECUDA. */
+int mrg_transform(const uint32_t *z, uint64_t n, int dist, int dtype, double rate, void *out,
+                  void *stream);
 
 /* Advances every stream's `cur` by k = k_hi * 2^64 + k_lo steps (jump-ahead
  * by a matrix power, Sec. 2.1).  `start` and `sub` are unchanged.

@@ -34,6 +34,7 @@ int ensure_device() {
   static std::mutex mu;
   static bool ready[64] = {};
   static uint32_t tab[2][mrg::host::kJumpBits][9];
+  static float ttab[mrg::host::kTransformEntries][4];
   static bool tab_built = false;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -45,10 +46,13 @@ int ensure_device() {
     if (!mrg::host::norm_constant_ok(mrg::NORM_DELTA))
       return fail(MRG_ECUDA, "RN64(1/(m1+1)) does not match the kernels' constant");
     mrg::host::jump_table_u32(tab);
+    mrg::host::transform_table(ttab);
     tab_built = true;
   }
   e = mrg::upload_tables(&tab[0][0][0], sizeof(tab));
   if (e != cudaSuccess) return fail_cuda(e, "uploading jump tables");
+  e = mrg::upload_transform_table(&ttab[0][0], sizeof(ttab));
+  if (e != cudaSuccess) return fail_cuda(e, "uploading transform tables");
   ready[dev] = true;
   return MRG_OK;
 }
@@ -108,8 +112,8 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
                  ((dist == MRG_UNIFORM || dist == MRG_NORMAL || dist == MRG_EXPONENTIAL) &&
                   (dtype == MRG_F32 || dtype == MRG_F64));
   if (!pair_ok) return fail(MRG_EINVAL, "unsupported dist/dtype combination");
-  if (dist == MRG_EXPONENTIAL && !(rate > 0.0 && rate < 1e300))
-    return fail(MRG_EINVAL, "exponential rate must be positive and finite");
+  if (dist == MRG_EXPONENTIAL && !(rate >= 0x1p-64 && rate <= 0x1p64))
+    return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
   if (n == 0 || s->n == 0) return MRG_OK;
   if (!out) return fail(MRG_EINVAL, "out is NULL");
   if (ld < n) return fail(MRG_EINVAL, "ld < n");
@@ -124,6 +128,25 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
   e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, consumed, 0, 0, cs(stream));
   if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (advance)");
+  return MRG_OK;
+}
+
+int mrg_transform(const uint32_t* z, uint64_t n, int dist, int dtype, double rate, void* out,
+                  void* stream) {
+  bool pair_ok = (dist == MRG_UNIFORM || dist == MRG_NORMAL || dist == MRG_EXPONENTIAL) &&
+                 (dtype == MRG_F32 || dtype == MRG_F64);
+  if (!pair_ok) return fail(MRG_EINVAL, "unsupported dist/dtype combination");
+  if (dist == MRG_EXPONENTIAL && !(rate >= 0x1p-64 && rate <= 0x1p64))
+    return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+  if (n == 0) return MRG_OK;
+  if (!z || !out) return fail(MRG_EINVAL, "z/out is NULL");
+  if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4) ||
+      reinterpret_cast<uintptr_t>(z) % 4)
+    return fail(MRG_EINVAL, "misaligned pointer");
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_transform(z, n, dist, dtype, rate, out, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "transform_kernel");
   return MRG_OK;
 }
 

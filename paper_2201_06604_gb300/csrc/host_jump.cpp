@@ -7,6 +7,7 @@
 // (x[n], x[n-1], x[n-2]) = A (x[n-1], x[n-2], x[n-3]).
 #include "host_jump.h"
 
+#include <cmath>
 #include <cstring>
 
 namespace mrg {
@@ -103,6 +104,31 @@ bool norm_constant_ok(uint64_t delta) {
   uint64_t sig = (bits & ((1ull << 52) - 1)) | (1ull << 52);
   int exp = (int)((bits >> 52) & 0x7FF) - 1023;
   return exp == -32 && sig == (1ull << 52) + delta;
+}
+
+namespace {
+void split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+}  // namespace
+
+void transform_table(float out[kTransformEntries][4]) {
+  const double M = 4294967088.0;       // m1 + 1
+  // log buckets: centre C_k of the zn-range [2^31 + k 2^24, 2^31 + (k+1) 2^24),
+  // the top bucket centred at M so that ln(C_127 / M) = 0 exactly.
+  for (int k = 0; k < 128; ++k) {
+    const double C = k == 127 ? M : 2147483648.0 + (2.0 * k + 1.0) * 8388608.0;
+    split(1.0 / C, out[k][0], out[k][1]);
+    split(std::log1p((C - M) / M), out[k][2], out[k][3]);
+  }
+  // trig buckets: a_j = (pi/2) j 2^23 / D, D = M / 4 (a_0 = 0 exactly)
+  const double D = 1073741772.0;
+  for (int j = 0; j < 65; ++j) {
+    const double a = (M_PI / 2) * ((j * 8388608.0) / D);
+    split(std::sin(a), out[128 + j][0], out[128 + j][1]);
+    split(std::cos(a), out[128 + j][2], out[128 + j][3]);
+  }
 }
 
 }  // namespace host

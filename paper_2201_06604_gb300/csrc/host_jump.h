@@ -19,5 +19,11 @@ void jump_pow2_multiple(uint32_t s[6], uint64_t e, int base);
 // True when RN64(1/(m1+1)) has exponent -32 and significand 2^52 + delta.
 bool norm_constant_ok(uint64_t delta);
 
+// Tables of the double-float transforms (layout in transforms_df.cuh):
+// entries [0, 128): 1/C_k and ln(C_k / M) for the log buckets;
+// entries [128, 193): sin and cos of the bucket angles a_j.
+constexpr int kTransformEntries = 193;
+void transform_table(float out[kTransformEntries][4]);
+
 }  // namespace host
 }  // namespace mrg

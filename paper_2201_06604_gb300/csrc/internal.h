@@ -25,8 +25,10 @@ struct GenConfig {
 
 extern std::atomic<uint64_t> g_launches;
 
-// Copies the jump tables into the current device's constant memory.
+// Copies the jump tables into the current device's constant memory and the
+// transform tables into its global memory.
 cudaError_t upload_tables(const uint32_t* tab, size_t bytes);
+cudaError_t upload_transform_table(const float* tab, size_t bytes);
 
 cudaError_t launch_create(const uint32_t seed[6], uint64_t n, const DevStreams& s,
                           cudaStream_t st);
@@ -43,6 +45,11 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
 
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st);
+
+// Applies the output transform to caller-provided raw draws z[i] in [1, m1]
+// (consecutive pairs for normals): out[i] as generate would write it.
+cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype, double rate,
+                             void* out, cudaStream_t st);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

@@ -25,7 +25,7 @@
 
 #include "internal.h"
 #include "mrg32k3a_core.cuh"
-#include "transforms_f64.cuh"
+#include "transforms_df.cuh"
 
 #define MRG_RAW 0
 #define MRG_UNIFORM 1
@@ -40,10 +40,23 @@ namespace mrg {
 std::atomic<uint64_t> g_launches{0};
 
 __constant__ uint32_t c_jump[2][JUMP_BITS][9];
+__device__ float4 g_ttab[TAB_ENTRIES];
 
 cudaError_t upload_tables(const uint32_t* tab, size_t bytes) {
   if (bytes != sizeof(c_jump)) return cudaErrorInvalidValue;
   return cudaMemcpyToSymbol(c_jump, tab, bytes);
+}
+
+cudaError_t upload_transform_table(const float* tab, size_t bytes) {
+  if (bytes != sizeof(g_ttab)) return cudaErrorInvalidValue;
+  return cudaMemcpyToSymbol(g_ttab, tab, bytes);
+}
+
+// Copies the transform tables into shared memory (all threads of the block
+// must call it).
+__device__ __forceinline__ void load_ttab(float4* s_tab) {
+  for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) s_tab[i] = g_ttab[i];
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -155,51 +168,48 @@ __device__ __forceinline__ void store_vec(char* p, const uint32_t* w) {
 
 struct Consts {
   uint64_t k1, k2;   // the offset-form addends K1, K2 (kept in registers)
-  double inv_rate;
+  float ir_hi, ir_lo;  // -1/rate as a float pair (exponentials)
 };
 
+__device__ __forceinline__ void put_f64(uint32_t* w, uint64_t b) {
+  w[0] = (uint32_t)b;
+  w[1] = (uint32_t)(b >> 32);
+}
+
 template <int DIST, int DT, int UE>
-__device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c) {
+__device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
+                                       const float4* __restrict__ tab) {
   if constexpr (DIST == MRG_RAW) {
 #pragma unroll
     for (int e = 0; e < UE; ++e) w[e] = step_fast(s, c.k1, c.k2);
   } else if constexpr (DIST == MRG_UNIFORM && DT == MRG_F64) {
 #pragma unroll
-    for (int e = 0; e < UE; ++e) {
-      uint64_t u = uniform_bits64_fast(step_fast(s, c.k1, c.k2));
-      w[2 * e] = (uint32_t)u;
-      w[2 * e + 1] = (uint32_t)(u >> 32);
-    }
+    for (int e = 0; e < UE; ++e) put_f64(w + 2 * e, uniform_bits64_fast(step_fast(s, c.k1, c.k2)));
   } else if constexpr (DIST == MRG_UNIFORM) {
 #pragma unroll
     for (int e = 0; e < UE; ++e)
       w[e] = f32_bits_from_f64(uniform_bits64_fast(step_fast(s, c.k1, c.k2)));
   } else if constexpr (DIST == MRG_NORMAL) {
-#pragma unroll 1
+#pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
-      uint32_t z1 = step_fast(s, c.k1, c.k2);
-      uint32_t z2 = step_fast(s, c.k1, c.k2);
-      double x, y;
-      box_muller_f64(z1, z2, x, y);
+      const uint32_t z1 = step_fast(s, c.k1, c.k2);
+      const uint32_t z2 = step_fast(s, c.k1, c.k2);
+      df x, y;
+      box_muller_df(z1, z2, tab, x, y);
       if constexpr (DT == MRG_F64) {
-        uint64_t bx = (uint64_t)__double_as_longlong(x), by = (uint64_t)__double_as_longlong(y);
-        w[4 * p] = (uint32_t)bx; w[4 * p + 1] = (uint32_t)(bx >> 32);
-        w[4 * p + 2] = (uint32_t)by; w[4 * p + 3] = (uint32_t)(by >> 32);
+        put_f64(w + 4 * p, df_to_f64_bits(x));
+        put_f64(w + 4 * p + 2, df_to_f64_bits(y));
       } else {
-        w[2 * p] = __float_as_uint(__double2float_rn(x));
-        w[2 * p + 1] = __float_as_uint(__double2float_rn(y));
+        w[2 * p] = __float_as_uint(df_to_f32(x));
+        w[2 * p + 1] = __float_as_uint(df_to_f32(y));
       }
     }
-  } else {  // exponential
-#pragma unroll 1
+  } else {  // exponential: -ln(u) / rate
+#pragma unroll
     for (int e = 0; e < UE; ++e) {
-      double v = exponential_f64(step_fast(s, c.k1, c.k2), c.inv_rate);
-      if constexpr (DT == MRG_F64) {
-        uint64_t bv = (uint64_t)__double_as_longlong(v);
-        w[2 * e] = (uint32_t)bv; w[2 * e + 1] = (uint32_t)(bv >> 32);
-      } else {
-        w[e] = __float_as_uint(__double2float_rn(v));
-      }
+      const df v = df_mul(ln_u_df(step_fast(s, c.k1, c.k2), tab), df{c.ir_hi, c.ir_lo});
+      if constexpr (DT == MRG_F64) put_f64(w + 2 * e, df_to_f64_bits(v));
+      else w[e] = __float_as_uint(df_to_f32(v));
     }
   }
 }
@@ -230,6 +240,10 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
   constexpr int VS = VB < ES ? ES : VB;  // store width actually used
   constexpr int VW = VS / 4;
 
+  constexpr bool TABLES = DIST == MRG_NORMAL || DIST == MRG_EXPONENTIAL;
+  __shared__ float4 s_tab[TABLES ? TAB_ENTRIES : 1];
+  if constexpr (TABLES) load_ttab(s_tab);
+
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
@@ -256,7 +270,7 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
 #pragma unroll 2
     for (uint32_t i = 0; i < cmax; i += UE) {
       uint32_t wv[UW];
-      produce<DIST, DT, UE>(st, wv, c);
+      produce<DIST, DT, UE>(st, wv, c, s_tab);
       if (i + UE <= cnt) {
 #pragma unroll
         for (int v = 0; v < UB / VS; ++v) store_vec<VS>(gdst + (size_t)i * ES + v * VS, wv + v * VW);
@@ -276,26 +290,69 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
 __global__ void __launch_bounds__(256) fused_kernel(uint32_t* cur, uint64_t stride, uint64_t ns,
                                                     uint64_t pairs, int64_t* count, double* sum,
                                                     uint64_t k1, uint64_t k2) {
+  __shared__ float4 s_tab[TAB_ENTRIES];
+  load_ttab(s_tab);
   constexpr uint64_t MSQ = MNORM * MNORM;  // (m1+1)^2 < 2^64
   const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += step_all) {
     TState s = to_offset(load_state(cur, stride, i));
     int64_t cnt = 0;
-    double acc = 0.0;
+    df acc{0.0f, 0.0f};
     for (uint64_t k = 0; k < pairs; ++k) {
-      uint32_t za = step_fast(s, k1, k2);
-      uint32_t zb = step_fast(s, k1, k2);
-      uint64_t sa = (uint64_t)za * za, sb = (uint64_t)zb * zb;
-      uint64_t ss = sa + sb;
+      const uint32_t za = step_fast(s, k1, k2);
+      const uint32_t zb = step_fast(s, k1, k2);
+      const uint64_t sa = (uint64_t)za * za, sb = (uint64_t)zb * zb;
+      const uint64_t ss = sa + sb;
       cnt += (ss >= sa) & (ss < MSQ);  // no carry out of 64 bits and below M^2
-      double x, y;
-      box_muller_f64(za, zb, x, y);
-      acc += x;
-      acc += y;
+      df x, y;
+      box_muller_df(za, zb, s_tab, x, y);
+      acc = df_add(acc, df_add(x, y));
     }
     store_state(cur, stride, i, from_offset(s));
     count[i] = cnt;
-    sum[i] = acc;
+    sum[i] = __longlong_as_double((long long)df_to_f64_bits(acc));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transform of caller-provided raw draws
+// ---------------------------------------------------------------------------
+
+template <int DIST, int DT>
+__global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restrict__ z, uint64_t n,
+                                                        char* out, Consts c) {
+  __shared__ float4 s_tab[TAB_ENTRIES];
+  load_ttab(s_tab);
+  constexpr int ES = DT == MRG_F64 ? 8 : 4;
+  constexpr int PER = DIST == MRG_NORMAL ? 2 : 1;
+  const uint64_t units = (n + PER - 1) / PER;
+  const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += step_all) {
+    uint32_t w[4];
+    if constexpr (DIST == MRG_NORMAL) {
+      const uint32_t z1 = z[2 * u];
+      const uint32_t z2 = 2 * u + 1 < n ? z[2 * u + 1] : 1u;
+      df x, y;
+      box_muller_df(z1, z2, s_tab, x, y);
+      if constexpr (DT == MRG_F64) { put_f64(w, df_to_f64_bits(x)); put_f64(w + 2, df_to_f64_bits(y)); }
+      else { w[0] = __float_as_uint(df_to_f32(x)); w[1] = __float_as_uint(df_to_f32(y)); }
+    } else if constexpr (DIST == MRG_EXPONENTIAL) {
+      const df v = df_mul(ln_u_df(z[u], s_tab), df{c.ir_hi, c.ir_lo});
+      if constexpr (DT == MRG_F64) put_f64(w, df_to_f64_bits(v));
+      else w[0] = __float_as_uint(df_to_f32(v));
+    } else if constexpr (DT == MRG_F64) {
+      put_f64(w, uniform_bits64_fast(z[u]));
+    } else {
+      w[0] = f32_bits_from_f64(uniform_bits64_fast(z[u]));
+    }
+    for (int e = 0; e < PER; ++e) {
+      const uint64_t i = u * PER + e;
+      if (i < n) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(out + i * ES);
+        d[0] = w[e * ES / 4];
+        if (ES == 8) d[1] = w[e * ES / 4 + 1];
+      }
+    }
   }
 }
 
@@ -430,7 +487,11 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
   a.ld = ld;
   a.c.k1 = K1;
   a.c.k2 = K2;
-  a.c.inv_rate = 1.0 / rate;
+  {
+    const double ir = -1.0 / rate;
+    a.c.ir_hi = (float)ir;
+    a.c.ir_lo = (float)(ir - (double)a.c.ir_hi);
+  }
   // widest store the row starts allow: out address and row pitch alignment
   const uint64_t align = (reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) & ~((reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) - 1);
   const int vb = (int)std::min<uint64_t>(align, 32);
@@ -444,6 +505,30 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
     case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64>(a, vb, cfg, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype, double rate,
+                             void* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  Consts c{K1, K2, 0.0f, 0.0f};
+  if (dist == MRG_EXPONENTIAL) {
+    const double ir = -1.0 / rate;
+    c.ir_hi = (float)ir;
+    c.ir_lo = (float)(ir - (double)c.ir_hi);
+  }
+  const uint64_t units = dist == MRG_NORMAL ? (n + 1) / 2 : n;
+  const unsigned grid = grid_for(units, 256, 8);
+  char* o = reinterpret_cast<char*>(out);
+  switch (dist * 4 + dtype) {
+    case MRG_UNIFORM * 4 + MRG_F32: transform_kernel<MRG_UNIFORM, MRG_F32><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    case MRG_UNIFORM * 4 + MRG_F64: transform_kernel<MRG_UNIFORM, MRG_F64><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    case MRG_NORMAL * 4 + MRG_F32: transform_kernel<MRG_NORMAL, MRG_F32><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    case MRG_NORMAL * 4 + MRG_F64: transform_kernel<MRG_NORMAL, MRG_F64><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    case MRG_EXPONENTIAL * 4 + MRG_F32: transform_kernel<MRG_EXPONENTIAL, MRG_F32><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    case MRG_EXPONENTIAL * 4 + MRG_F64: transform_kernel<MRG_EXPONENTIAL, MRG_F64><<<grid, 256, 0, st>>>(z, n, o, c); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return after_launch();
 }
 
 }  // namespace mrg

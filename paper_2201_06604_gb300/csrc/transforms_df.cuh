@@ -1,0 +1,194 @@
+// transforms_df.cuh -- normal and exponential transforms in double-float
+// arithmetic (pairs of fp32 values, ~46 significant bits) on the FP32 pipe.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so the
+// transforms are evaluated as unevaluated sums hi + lo of two floats with
+// error-free products (FMA) and sums; every add and multiply of the
+// error-free transformations uses the __f*_rn intrinsics so that the compiler
+// never contracts or reassociates them.
+//
+// Definitions (on the exact rational uniform u = z / M, M = m1 + 1):
+//   Box-Muller (Sec. 3.1, Algorithm 1): R = sqrt(-2 ln u1), Theta = 2 pi u2,
+//     X = R cos Theta, Y = R sin Theta;
+//   exponential (Sec. 3.2): E = -ln(u) / rate.
+//
+// ln u (relative error ~2^-46 over the whole range):
+//   z = zn 2^-s with zn in [2^31, 2^32); bucket k = the 7 bits after the
+//   leading one; C_k = the bucket centre 2^31 + (2k+1) 2^23, except the top
+//   bucket whose centre is M itself.  With d = zn - C_k (exact, |d| < 2^24)
+//   and r = d / C_k (|r| <= 2^-8):
+//     ln u = -s ln 2 + ln(C_k / M) + ln(1 + r),
+//   ln(1 + r) by its Taylor series to r^6.  For z >= 2^31 in the top bucket
+//   the first two terms are exactly zero, so ln u = ln(1 + r) keeps its
+//   relative accuracy as u -> 1.
+// sin / cos of 2 pi z / M (absolute error ~2^-47, relative near zeros):
+//   exact integer reduction z = q D + w, D = M / 4, w in [0, D); reflection
+//   w -> D - w above D/2 (swapping sin and cos); bucket j = (w + 2^22) >> 23
+//   with table angle a_j = (pi/2) j 2^23 / D and residual
+//   delta = (pi/2)(w - j 2^23) / D, |delta| <= 0.0062; sin/cos(delta) by
+//   Taylor series and the angle-addition formulas.  Bucket 0 has a_0 = 0
+//   (sin 0 = 0, cos 0 = 1 exactly), so small angles keep their relative
+//   accuracy and an exact zero of sin or cos comes out as exactly zero.
+#pragma once
+#include <stdint.h>
+
+#include "mrg32k3a_core.cuh"
+
+namespace mrg {
+
+struct df {
+  float hi, lo;
+};
+
+// Table layout (float4 entries), built on the host (host_jump.cpp):
+//   [0, 128)   log:  (1/C_k).hi, (1/C_k).lo, ln(C_k/M).hi, ln(C_k/M).lo
+//   [128, 193) trig: sin(a_j).hi, sin(a_j).lo, cos(a_j).hi, cos(a_j).lo
+constexpr int TAB_LOG = 0;
+constexpr int TAB_TRIG = 128;
+constexpr int TAB_ENTRIES = 193;
+
+// ln 2 and (pi/2)/D as float pairs.
+constexpr float LN2_HI = 0x1.62e430p-1f;    // RN32(ln 2)
+constexpr float LN2_LO = -0x1.05c610p-29f;  // RN32(ln 2 - LN2_HI)
+constexpr float PID_HI = 0x1.921fb6p-30f;   // RN32(pi / (2 D)), D = (m1 + 1) / 4
+constexpr float PID_LO = 0x1.15f92cp-55f;   // RN32(pi / (2 D) - PID_HI)
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+  float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+  float p = __fmul_rn(x.hi, f);
+  float e = __fmaf_rn(x.hi, f, -p);
+  e = __fmaf_rn(x.lo, f, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+
+// Small exact integer (|v| < 2^22) to float without the conversion unit.
+__device__ __forceinline__ float small_int_to_float(int32_t v) {
+  return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+
+// ln(z / M) for z in [1, m1].
+__device__ __forceinline__ df ln_u_df(uint32_t z, const float4* __restrict__ tab) {
+  uint32_t s;
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(s) : "r"(z));
+  const uint32_t zn = z << s;
+  const uint32_t k = (zn >> 24) & 127u;
+  const uint32_t ck = k == 127u ? 4294967088u : 0x80800000u + (k << 24);
+  const int32_t d = (int32_t)(zn - ck);                 // |d| < 2^24: exact in fp32
+  const float4 T = tab[TAB_LOG + k];
+  const df r = df_mul_f(df{T.x, T.y}, (float)d);        // r = d / C_k
+  // ln(1 + r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6)
+  const float rh = r.hi;
+  const float p2 = __fmul_rn(rh, rh);
+  const float e2 = __fmaf_rn(2.0f * rh, r.lo, __fmaf_rn(rh, rh, -p2));   // r^2 = p2 + e2
+  float poly = __fmaf_rn(rh, -1.0f / 6.0f, 0.2f);
+  poly = __fmaf_rn(rh, poly, -0.25f);
+  poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
+  const float c3 = __fmul_rn(__fmul_rn(p2, rh), poly);
+  df l1p = df_add(r, df{-0.5f * p2, __fmaf_rn(-0.5f, e2, c3)});
+  // -s ln2 + ln(C_k / M)
+  const float sf = small_int_to_float((int32_t)s);
+  const float a = __fmul_rn(-sf, LN2_HI);
+  const df sl = df{a, __fmaf_rn(-sf, LN2_LO, __fmaf_rn(-sf, LN2_HI, -a))};
+  return df_add(df_add(sl, df{T.z, T.w}), l1p);
+}
+
+// sqrt of a positive df (relative error ~2^-46).
+__device__ __forceinline__ df df_sqrt(df x) {
+  float y = rsqrtf(x.hi);
+  y = __fmul_rn(y, __fmaf_rn(-0.5f * x.hi, __fmul_rn(y, y), 1.5f));   // one Newton step
+  const float r0 = __fmul_rn(x.hi, y);
+  const float e = __fadd_rn(__fmaf_rn(-r0, r0, x.hi), x.lo);           // x - r0^2
+  return fast_two_sum(r0, __fmul_rn(__fmul_rn(e, y), 0.5f));
+}
+
+// sin and cos of 2 pi z / M for z in [1, m1].
+__device__ __forceinline__ void sincos_turn_df(uint32_t z, const float4* __restrict__ tab, df& sn,
+                                               df& cs) {
+  constexpr uint32_t D = 1073741772u;  // M / 4
+  uint32_t q = z >> 30;
+  uint32_t w = (z & 0x3FFFFFFFu) + 52u * q;  // z - q D  (q D = q 2^30 - 52 q)
+  if (w >= D) { w -= D; ++q; }                // z = q D + w, w in [0, D)
+  const bool refl = 2u * w > D;
+  const uint32_t wr = refl ? D - w : w;       // [0, D/2]
+  const uint32_t j = (wr + 0x400000u) >> 23;  // 0..64
+  const float dwf = small_int_to_float((int32_t)(wr - (j << 23)));   // [-2^22, 2^22)
+  const df delta = df_mul_f(df{PID_HI, PID_LO}, dwf);
+  const float dh = delta.hi;
+  const float d2 = __fmul_rn(dh, dh);
+  // sin(delta) = delta + delta^3 (-1/6 + delta^2 / 120)
+  const float sc = __fmul_rn(__fmul_rn(dh, d2), __fmaf_rn(d2, 1.0f / 120.0f, -1.0f / 6.0f));
+  const df sd = fast_two_sum(dh, __fadd_rn(delta.lo, sc));
+  // cos(delta) - 1 = -delta^2/2 + delta^4 (1/24 - delta^2 / 720)
+  const float e2 = __fmaf_rn(2.0f * dh, delta.lo, __fmaf_rn(dh, dh, -d2));
+  const float cc = __fmul_rn(__fmul_rn(d2, d2), __fmaf_rn(d2, -1.0f / 720.0f, 1.0f / 24.0f));
+  const df cm1 = fast_two_sum(-0.5f * d2, __fmaf_rn(-0.5f, e2, cc));
+  const float4 T = tab[TAB_TRIG + j];
+  const df sj{T.x, T.y}, cj{T.z, T.w};
+  // sin(a + d) = sj + (sj (cos d - 1) + cj sin d);  cos(a + d) = cj + (cj (cos d - 1) - sj sin d)
+  df sp = df_add(sj, df_add(df_mul(sj, cm1), df_mul(cj, sd)));
+  df cp = df_add(cj, df_add(df_mul(cj, cm1), df_neg(df_mul(sj, sd))));
+  // angle = (pi/2) q + phi, phi = reflected or not
+  const bool swap = refl ^ (q & 1u);
+  df s0 = swap ? cp : sp, c0 = swap ? sp : cp;
+  const float ss = (q >= 2u) ? -1.0f : 1.0f;                 // sin sign: quadrants 2, 3
+  const float cs_ = (q == 1u || q == 2u) ? -1.0f : 1.0f;     // cos sign: quadrants 1, 2
+  sn = df{s0.hi * ss, s0.lo * ss};
+  cs = df{c0.hi * cs_, c0.lo * cs_};
+}
+
+// RN-ish conversion of a df to IEEE double bits, in integers (|error| <= 1 ulp
+// of the double).  Requires |hi| normal or zero and |lo| <= ulp(hi).
+__device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
+  const uint32_t hb = __float_as_uint(v.hi);
+  const uint32_t ah = hb & 0x7FFFFFFFu;
+  if (ah == 0) return (uint64_t)(hb & 0x80000000u) << 32;   // +-0
+  const uint32_t eh = ah >> 23;                               // biased fp32 exponent
+  const uint32_t mh = (ah & 0x7FFFFFu) | 0x800000u;          // 24-bit significand
+  // lo in units of 2^(eh - 179) (the double's last place), sign relative to hi
+  const float scale = __uint_as_float(((306u - eh) << 23) ^ (hb & 0x80000000u));
+  const int32_t li = __float2int_rn(__fmul_rn(v.lo, scale));
+  uint64_t V = ((uint64_t)mh << 29) + (uint64_t)(int64_t)li;  // in [2^52 - 2^28, 2^53 + 2^28)
+  uint32_t e64 = eh + 895u;                                   // biased double exponent - 1
+  if (V < (1ull << 52)) { V <<= 1; --e64; }                   // hi a power of two, lo < 0
+  return ((uint64_t)(hb & 0x80000000u) << 32) | (((uint64_t)e64 << 52) + V);
+}
+
+__device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
+
+// Box-Muller on one pair: X, Y as df.
+__device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
+                                              df& x, df& y) {
+  const df l = ln_u_df(z1, tab);
+  const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
+  df sn, cs;
+  sincos_turn_df(z2, tab, sn, cs);
+  x = df_mul(R, cs);
+  y = df_mul(R, sn);
+}
+
+}  // namespace mrg

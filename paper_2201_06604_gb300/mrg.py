@@ -58,6 +58,7 @@ def _load():
         "mrg_create_streams": ([u32p, u64, sp, u32p, vp], i32),
         "mrg_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
         "mrg_skip": ([sp, u64, u64, vp], i32),
+        "mrg_transform": ([vp, u64, i32, i32, ctypes.c_double, vp, vp], i32),
         "mrg_substream_next": ([sp, vp], i32),
         "mrg_reset_substream": ([sp, vp], i32),
         "mrg_reset_stream": ([sp, vp], i32),
@@ -207,6 +208,24 @@ def generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64, rate
     with torch.cuda.device(streams.device):
         _check(lib.mrg_generate(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
                                 out.stride(0), _stream_handle(stream)))
+    return out
+
+
+def transform(z: torch.Tensor, dist="normal", dtype=torch.float64, rate: float = 1.0,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Applies the generate transform to raw draws z (int32 tensor holding
+    uint32 values in [1, m1]; consecutive pairs for normals)."""
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    if d == RAW:
+        raise ValueError("raw draws need no transform")
+    code = _dtype_code(d, dtype)
+    z = z.contiguous()
+    n = z.numel()
+    if out is None:
+        out = torch.empty(n, dtype=dtype, device=z.device)
+    with torch.cuda.device(z.device):
+        _check(lib.mrg_transform(z.data_ptr(), n, d, code, float(rate), out.data_ptr(),
+                                 _stream_handle(stream)))
     return out
 
 

@@ -1,0 +1,124 @@
+"""Accuracy of the double-float transforms on the GPU (through mrg_transform)
+against the oracle's double evaluation of the exact transforms, on random
+integers and on every boundary of the kernels' reductions and tables:
+quarter turns and octants of the angle, the log table's bucket edges at every
+exponent, powers of two and the ends of [1, m1].
+
+Bars: fp64 normals |err| <= 1e-12; fp64 exponentials |err| <= 1e-12 / min(rate, 1);
+fp32 outputs |err| <= 2 ulp of the fp32 spacing at the reference value.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+M1 = O.MRG32K3A[0]
+M = M1 + 1
+D = M // 4
+
+
+@pytest.fixture(scope="module")
+def mrg():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2201_06604_gb300 import mrg as m
+    return m
+
+
+def boundary_integers():
+    z = set()
+    for base in (1, 2, 3, D // 2, D, 2 * D, 3 * D, D + D // 2, 2 * D + D // 2, 3 * D + D // 2,
+                 M1, M // 2, 1 << 31):
+        for d in range(-3, 4):
+            z.add(base + d)
+    # angle table bucket edges inside each octant: w = j 2^23 (+ 2^22 centres)
+    for q in range(4):
+        for j in range(65):
+            for off in (0, 1 << 22):
+                for d in (-1, 0, 1):
+                    w = j * (1 << 23) + off + d
+                    z.add(q * D + w)
+                    z.add(q * D + D - w)
+    # log buckets at every exponent: zn = 2^31 + k 2^24 shifted right by s
+    for s in range(32):
+        for k in range(129):
+            zn = (1 << 31) + k * (1 << 24)
+            for d in (-1, 0, 1):
+                z.add((zn >> s) + d)
+        z.add((M - 208) >> s)
+    for e in range(32):
+        for d in (-2, -1, 0, 1, 2):
+            z.add((1 << e) + d)
+    z = np.array(sorted(v for v in z if 1 <= v <= M1), dtype=np.uint64)
+    return z.astype(np.uint32)
+
+
+def all_inputs(n_random=1 << 21, seed=5):
+    rng = np.random.default_rng(seed)
+    r = rng.integers(1, M1 + 1, size=n_random, dtype=np.uint64).astype(np.uint32)
+    b = boundary_integers()
+    # pair every boundary value with every role (first and second of a pair)
+    rb = rng.integers(1, M1 + 1, size=b.size, dtype=np.uint64).astype(np.uint32)
+    pairs = np.concatenate([np.stack([b, rb], 1).reshape(-1), np.stack([rb, b], 1).reshape(-1)])
+    return np.concatenate([r, pairs])
+
+
+def f32_ulp(ref):
+    return np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+
+
+def run(mrg, z, dist, dtype, rate=1.0):
+    zt = torch.from_numpy(z.view(np.int32)).cuda()
+    return mrg.transform(zt, dist, dtype, rate=rate).cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_normal_transform_accuracy(mrg, dtype):
+    z = all_inputs()
+    got = run(mrg, z, "normal", dtype)
+    ref = O.box_muller_of(z)
+    err = np.abs(got - ref)
+    if dtype == torch.float64:
+        print(f"fp64 normal: max abs err {err.max():.3e} over {z.size} values")
+        assert err.max() <= 1e-12
+    else:
+        ratio = (err / f32_ulp(ref)).max()
+        print(f"fp32 normal: max err {ratio:.3f} ulp over {z.size} values")
+        assert ratio <= 2.0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("rate", [1.0, 0.37, 2.0 ** -64, 2.0 ** 64, 1e6])
+def test_exponential_transform_accuracy(mrg, dtype, rate):
+    z = all_inputs(n_random=1 << 19)
+    got = run(mrg, z, "exponential", dtype, rate=rate)
+    ref = O.exp_of(z, rate)
+    err = np.abs(got - ref)
+    if dtype == torch.float64:
+        tol = 1e-12 / min(rate, 1.0)
+        print(f"fp64 exponential rate={rate}: max abs err {err.max():.3e} (tol {tol:.1e})")
+        assert err.max() <= tol
+    else:
+        ratio = (err / f32_ulp(ref)).max()
+        print(f"fp32 exponential rate={rate}: max err {ratio:.3f} ulp")
+        assert ratio <= 2.0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_uniform_transform_bit_exact(mrg, dtype):
+    z = all_inputs(n_random=1 << 18)
+    got = run(mrg, z, "uniform", dtype)
+    u = z.astype(np.float64) * O.norm()
+    ref = u if dtype == torch.float64 else u.astype(np.float32).astype(np.float64)
+    assert np.array_equal(got, ref)
+
+
+def test_odd_normal_count_and_zero_crossings(mrg):
+    # z2 = D and 3D put Theta exactly on pi/2 and 3 pi/2: X is exactly zero.
+    z = np.array([12345, D, 777, 3 * D, 5], dtype=np.uint32)
+    got = run(mrg, z, "normal", torch.float64)
+    ref = O.box_muller_of(np.array([12345, D, 777, 3 * D, 5, 1], dtype=np.uint32))[:5]
+    assert got[0] == 0.0 and got[2] == 0.0
+    assert np.abs(got - ref).max() <= 1e-12
