@@ -29,6 +29,16 @@ VARIANTS = (("uniform", "f64"), ("uniform", "f32"), ("normal", "f64"), ("normal"
             ("exponential", "f32"))
 ES = {"f64": 8, "f32": 4, "u32": 4}
 
+# Warp-level instructions issued per output by generate_kernel, measured with
+# ncu (smsp__inst_executed.sum x 32 / outputs) on 16384 streams x 4096 draws.
+# These kernels are bound by instruction issue (the FP64 pipe is not used and
+# the recurrence is integer multiply-add work), so the dominant kernel's
+# roofline is issue slots: 4 warp-instructions per cycle per SM.
+INSTR_PER_OUTPUT = {("raw", "u32"): 28.8, ("uniform", "f64"): 45.0, ("uniform", "f32"): 49.9,
+                    ("normal", "f64"): 173.7, ("normal", "f32"): 145.4,
+                    ("exponential", "f32"): 105.2, ("exponential", "f64"): 133.2}
+SM_COUNT = 152
+
 
 def env_rank():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
@@ -153,6 +163,29 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+# DRAM bytes (read + write) per output of generate_kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on 65536 streams x 4096 draws.
+TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.823, ("uniform", "f32"): 3.811,
+                      ("normal", "f64"): 7.815, ("normal", "f32"): 3.816,
+                      ("exponential", "f32"): 3.817}
+
+
+def roofline(dom, hbm, peak_kind, issue_peak, total_out):
+    key = (dom["dist"], dom["dtype"])
+    traffic = TRAFFIC_PER_OUTPUT.get(key)
+    traffic = traffic * total_out if traffic else None
+    if "issue_tinst_s" in dom and dom["hbm_frac"] < 0.5:
+        return {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>", "bound": "alu",
+                "achieved": dom["issue_tinst_s"], "peak": issue_peak, "unit": "Tinst/s",
+                "frac": dom["issue_tinst_s"] / issue_peak, "traffic": traffic,
+                "peak_source": "issue slots: 4 warp-instructions/cycle/SM x 152 SMs x "
+                               "sm_max_mhz (MEASURED_PEAKS.json) x 32 threads",
+                "hbm_gbs": dom["gbs"], "hbm_frac": dom["hbm_frac"]}
+    return {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>", "bound": "hbm",
+            "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["hbm_frac"],
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -242,52 +275,82 @@ def run_gpu(args):
     torch.cuda.synchronize()
     adv_ms = e0.elapsed_time(e1) / 20
 
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = 4 * SM_COUNT * sm_max_mhz * 1e6 * 32 / 1e12   # thread-instr/s, in T
     variants = []
     for i, (d, dt) in enumerate(variants_run):
         t_call = float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
         t_kern = max(t_call - adv_ms, 1e-6)
         algo = total_out * ES[dt] + ns * 24  # outputs written + states read
-        variants.append({"dist": d, "dtype": dt, "ms": t_kern, "draws_per_s": total_out / t_kern * 1e3,
-                         "algo_bytes": algo, "gbs": algo / t_kern / 1e6})
-
-    peaks, peak_kind = load_peaks()
-    hbm = float(peaks["hbm_gbs"])
-    dom = max(variants, key=lambda v: v["ms"])
-    for v in variants:
+        v = {"dist": d, "dtype": dt, "ms": t_kern, "draws_per_s": total_out / t_kern * 1e3,
+             "algo_bytes": algo, "gbs": algo / t_kern / 1e6}
         v["hbm_frac"] = v["gbs"] / hbm
+        ipo = INSTR_PER_OUTPUT.get((d, dt))
+        if ipo:
+            v["issue_tinst_s"] = ipo * total_out / (t_kern * 1e-3) / 1e12
+            v["issue_frac"] = v["issue_tinst_s"] / issue_peak
+        variants.append(v)
+    dom = max(variants, key=lambda v: v["ms"])
 
     draws_step = total_out * len(variants_run)
     bytes_step = sum(total_out * ES[dt] for _, dt in variants_run)
     value = draws_step * world / (per_step_ms / 1e3)
 
-    # e2e through the public API with host buffers: seed from pinned host
-    # memory in, every variant's output copied back to pinned host memory.
+    # e2e through the public API with host buffers: every variant generated
+    # into pinned host memory by mrg_generate_host (chunked; the copy of one
+    # chunk overlaps the generation of the next).  The only input is the
+    # 24-byte creator seed, passed by value to the stream-creation kernel.
     e2e = None
     if not args.skip_e2e:
         host = torch.empty(total_out * 8, dtype=torch.uint8, pin_memory=True)
-        seed_host = torch.tensor(list(seed), dtype=torch.int64).pin_memory()
-        seed_dev = torch.empty_like(seed_host, device=dev)
+        hosts = {"f64": host.view(torch.float64).view(ns, n),
+                 "f32": host[: total_out * 4].view(torch.float32).view(ns, n),
+                 "u32": host[: total_out * 4].view(torch.int32).view(ns, n)}
+        scratch = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
 
         def e2e_step():
-            seed_dev.copy_(seed_host, non_blocking=True)
             create()
             for d, dt in variants_run:
-                mrg.generate(s, n, d, tdt[dt], out=outs[dt])
-                nb = total_out * ES[dt]
-                host[:nb].copy_(buf[:nb], non_blocking=True)
+                mrg.generate_host(s, n, d, tdt[dt], out=hosts[dt], scratch=scratch)
         e2e_step()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         KE = max(1, min(K, 3))
-        a.record(stream)
+        t0 = time.perf_counter()
         for _ in range(KE):
             e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / KE
+        e2e = {"value": draws_step * world / (e2e_ms / 1e3), "unit": "draws/s",
+               "h2d_bytes_per_step": 24, "d2h_bytes_per_step": bytes_step, "ms_per_step": e2e_ms,
+               "d2h_gbs": bytes_step / (e2e_ms / 1e3) / 1e9}
+        del host, scratch
+
+    # fused no-store consumer: 2^20 streams x 4096 draws -> count and sum
+    fused = None
+    if not args.skip_fused:
+        from paper_2201_06604_gb300 import workloads as Wl
+        fs, fd = Wl.FUSED["streams"], Wl.FUSED["draws"]
+        if args.quick:
+            fs = 1 << 16
+        f_st = mrg.create_streams(fs, device=dev, seed=seed)
+        cnt = torch.empty(fs, dtype=torch.int64, device=dev)
+        sm_ = torch.empty(fs, dtype=torch.float64, device=dev)
+        mrg.fused_pi_normsum(f_st, fd, cnt, sm_)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            mrg.fused_pi_normsum(f_st, fd, cnt, sm_)
         b.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b) / KE
-        e2e = {"value": draws_step * world / (e2e_ms / 1e3), "unit": "draws/s",
-               "h2d_bytes_per_step": 48, "d2h_bytes_per_step": bytes_step, "ms_per_step": e2e_ms}
-        del host
+        f_ms = a.elapsed_time(b) / 3
+        pairs = fs * fd // 2
+        fused = {"workload": f"{fs} streams x {fd} draws", "ms": f_ms,
+                 "draws_per_s": fs * fd / (f_ms / 1e3),
+                 "pi_estimate": 4.0 * cnt.sum().item() / pairs}
+        del f_st, cnt, sm_
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -309,14 +372,12 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "outputs (4-8 GiB per variant) larger than L2; no flush"},
         "gbs": bytes_step * world / (per_step_ms / 1e3) / 1e9,
-        "roofline": {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>",
-                     "bound": "hbm", "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s",
-                     "frac": dom["gbs"] / hbm, "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "roofline": roofline(dom, hbm, peak_kind, issue_peak, total_out),
         "variants": variants,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "e2e": e2e,
+        "fused": fused,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -334,6 +395,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small shapes (development only)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")
     ap.add_argument("--draws", type=int, default=0, help="override draws per stream (profiling)")
     ap.add_argument("--only", default="", help="comma list of dist:dtype variants (profiling)")

@@ -119,6 +119,19 @@ int mrg_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams *s,
 int mrg_generate(const mrg_streams *s, uint64_t n_per_stream, int dist, int dtype,
                  double rate, void *out, uint64_t ld, void *stream);
 
+/* mrg_generate into HOST memory: value i of stream j at out_host[j * ld + i]
+ * (out_host should be pinned for full copy bandwidth).  The streams are cut
+ * into chunks that fit half of `scratch` (caller-owned device memory,
+ * scratch_bytes >= 2 * n * element size); chunk c is generated on `stream`
+ * into one half while chunk c-1 is copied to the host from the other half on
+ * a second stream of the library, so generation overlaps the device-to-host
+ * copy.  Same outputs and state updates as mrg_generate.  Synchronises: the
+ * data is on the host when the call returns.  Errors: as mrg_generate, plus
+ * MRG_EINVAL when scratch is NULL or too small for one stream per half. */
+int mrg_generate_host(const mrg_streams *s, uint64_t n_per_stream, int dist, int dtype,
+                      double rate, void *out_host, uint64_t ld, void *scratch,
+                      uint64_t scratch_bytes, void *stream);
+
 /* Applies the output transform of mrg_generate to caller-provided raw draws:
  * z (device, n values in [1, m1], e.g. from MRG_RAW) -> out (device, n values
  * of dtype).  MRG_UNIFORM, MRG_NORMAL (consecutive pairs (z[2k], z[2k+1]) give

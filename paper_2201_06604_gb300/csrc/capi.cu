@@ -4,6 +4,7 @@
 // kernels of kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -128,6 +129,64 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
   e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, consumed, 0, 0, cs(stream));
   if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (advance)");
+  return MRG_OK;
+}
+
+int mrg_generate_host(const mrg_streams* s, uint64_t n, int dist, int dtype, double rate,
+                      void* out_host, uint64_t ld, void* scratch, uint64_t scratch_bytes,
+                      void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (n == 0 || s->n == 0) return MRG_OK;
+  if (!out_host || !scratch) return fail(MRG_EINVAL, "out_host/scratch is NULL");
+  if (ld < n) return fail(MRG_EINVAL, "ld < n");
+  const uint64_t es = dtype == MRG_F64 ? 8 : 4;
+  const uint64_t row = n * es;
+  const uint64_t half = (scratch_bytes / 2) & ~(uint64_t)255;
+  if (half < row) return fail(MRG_EINVAL, "scratch smaller than two stream rows");
+  const uint64_t rows = half / row;
+  int rc = ensure_device();
+  if (rc) return rc;
+  // per-device copy stream and ping-pong events
+  static std::mutex mu;
+  static cudaStream_t copy_st[64];
+  static cudaEvent_t gen_ev[64][2], copy_ev[64][2];
+  int devi = 0;
+  cudaGetDevice(&devi);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!copy_st[devi]) {
+      cudaError_t e = cudaStreamCreateWithFlags(&copy_st[devi], cudaStreamNonBlocking);
+      for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&gen_ev[devi][b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copy_ev[devi][b], cudaEventDisableTiming);
+      }
+      if (e != cudaSuccess) return fail_cuda(e, "creating copy stream/events");
+    }
+  }
+  cudaStream_t gs = cs(stream), ks = copy_st[devi];
+  char* sc = reinterpret_cast<char*>(scratch);
+  char* ho = reinterpret_cast<char*>(out_host);
+  uint64_t c = 0;
+  for (uint64_t r0 = 0; r0 < s->n; r0 += rows, ++c) {
+    const int b = (int)(c & 1);
+    const uint64_t m = std::min<uint64_t>(rows, s->n - r0);
+    mrg_streams v{s->cur + r0, s->start + r0, s->sub + r0, m, s->stride};
+    cudaError_t e = cudaSuccess;
+    if (c >= 2) e = cudaStreamWaitEvent(gs, copy_ev[devi][b], 0);  // half b drained
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
+    rc = mrg_generate(&v, n, dist, dtype, rate, sc + b * half, n, stream);
+    if (rc) return rc;
+    e = cudaEventRecord(gen_ev[devi][b], gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, gen_ev[devi][b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(ho + r0 * ld * es, ld * es, sc + b * half, row, row, m,
+                            cudaMemcpyDeviceToHost, ks);
+    if (e == cudaSuccess) e = cudaEventRecord(copy_ev[devi][b], ks);
+    if (e != cudaSuccess) return fail_cuda(e, "copy to host");
+  }
+  cudaError_t e = cudaStreamSynchronize(ks);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize (generate_host)");
   return MRG_OK;
 }
 

@@ -59,6 +59,7 @@ def _load():
         "mrg_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
         "mrg_skip": ([sp, u64, u64, vp], i32),
         "mrg_transform": ([vp, u64, i32, i32, ctypes.c_double, vp, vp], i32),
+        "mrg_generate_host": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp, u64, vp], i32),
         "mrg_substream_next": ([sp, vp], i32),
         "mrg_reset_substream": ([sp, vp], i32),
         "mrg_reset_stream": ([sp, vp], i32),
@@ -208,6 +209,30 @@ def generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64, rate
     with torch.cuda.device(streams.device):
         _check(lib.mrg_generate(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
                                 out.stride(0), _stream_handle(stream)))
+    return out
+
+
+def generate_host(streams: Streams, n: int, dist="uniform", dtype=torch.float64,
+                  rate: float = 1.0, out: torch.Tensor | None = None,
+                  scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Like generate, but into a host tensor (pinned when allocated here); the
+    device-to-host copy of one chunk of streams overlaps the generation of
+    the next.  `scratch` is a device uint8 tensor (default 512 MiB)."""
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    dt = torch.int32 if d == RAW else dtype
+    code = _dtype_code(d, dt)
+    if out is None:
+        out = torch.empty((streams.n, n), dtype=dt, pin_memory=True)
+    if out.device.type != "cpu" or out.dim() != 2 or out.stride(1) != 1 or out.dtype != dt:
+        raise ValueError("out must be a 2-D host tensor with unit column stride")
+    if out.shape[0] < streams.n or out.shape[1] < n:
+        raise ValueError("out too small")
+    if scratch is None:
+        scratch = torch.empty(512 << 20, dtype=torch.uint8, device=streams.device)
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_generate_host(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
+                                     out.stride(0), scratch.data_ptr(), scratch.numel(),
+                                     _stream_handle(stream)))
     return out
 
 

@@ -290,3 +290,21 @@ def test_fused_full_size_sampled(M):
     n = cfg["streams"] * cfg["draws"] // 2
     p = cnt.sum() / n
     assert abs(p - np.pi / 4) < 5 * np.sqrt(np.pi / 4 * (1 - np.pi / 4) / n)
+
+
+@pytest.mark.parametrize("dist,dtype", [("uniform", torch.float64), ("normal", torch.float32),
+                                        ("raw", torch.int32)])
+def test_generate_host_matches_device(M, dist, dtype):
+    ns, n = 77, 1003
+    a = M.create_streams(ns, seed=SEED)
+    b = M.create_streams(ns, seed=SEED)
+    want = M.generate(a, n, dist, dtype).cpu().numpy()
+    es = 8 if dtype == torch.float64 else 4
+    scratch = torch.empty(2 * 3 * n * es + 100, dtype=torch.uint8, device="cuda")  # 3 rows a half
+    dt = torch.int32 if dist == "raw" else dtype
+    out = torch.full((ns, n + 5), -1, dtype=dt).pin_memory()
+    M.generate_host(b, n, dist, dtype, out=out, scratch=scratch)
+    got = out.numpy()
+    assert np.array_equal(got[:, :n], want)
+    assert (got[:, n:] == -1).all()
+    assert np.array_equal(M.get_state(a), M.get_state(b))
