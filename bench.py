@@ -186,6 +186,61 @@ def roofline(dom, hbm, peak_kind, issue_peak, total_out):
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs"}
 
 
+def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3):
+    """4096 requests, lengths log-uniform in [1e2, 1e6], mixed dist/dtype,
+    request r on stream r, substream 1: one persistent graph-captured launch
+    vs 4096 plain mrg_generate calls (each followed by its state advance)."""
+    import torch
+    reqs = W.batched_requests(1024 if quick else 4096)
+    for q in reqs:
+        q["dist"] = {1: "uniform", 2: "normal", 3: "exponential"}[q["dist"]]
+    nst = len(reqs)
+    s = mrg.create_streams(nst, device=dev, seed=seed)
+    buf_b = mrg.alloc_outputs(reqs, device=dev)
+    outs_b = [q["out"] for q in reqs]
+    b = mrg.Batch(s, max_requests=nst, max_tiles=1 << 17)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.run(reqs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    # plain: position every stream at substream 1, then one call per request
+    plain = [dict(q) for q in reqs]
+    buf_p = mrg.alloc_outputs(plain, device=dev)
+    views = [s.view(r, 1) for r in range(nst)]
+    tdt = {"f32": torch.float32, "f64": torch.float64}
+    mrg.substream_next(s)
+
+    def plain_pass():
+        mrg.reset_substream(s)
+        for r, q in enumerate(plain):
+            mrg.generate(views[r], q["n"], q["dist"], tdt[q["dtype"]], out=q["out"].view(1, -1))
+    plain_pass()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / reps
+    identical = all(torch.equal(a, q["out"]) for a, q in zip(outs_b, plain))
+    draws = sum(q["n"] + (q["n"] & 1 if q["dist"] == "normal" else 0) for q in reqs)
+    nbytes = sum(q["n"] * (8 if q["dtype"] == "f64" else 4) for q in reqs)
+    res = {"workload": f"{nst} requests, n log-uniform [1e2, 1e6], mixed dist/dtype, "
+                       "request r on stream r substream 1",
+           "draws": draws, "bytes": nbytes, "tiles": b.last_tiles,
+           "batched_ms": t_batch, "plain_ms": t_plain, "speedup": t_plain / t_batch,
+           "batched_draws_per_s": draws / (t_batch / 1e3), "batched_gbs": nbytes / (t_batch / 1e3) / 1e9,
+           "plain_launches": 2 * nst, "identical_output": bool(identical)}
+    b.close()
+    del buf_b, buf_p
+    return res
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -352,6 +407,11 @@ def run_gpu(args):
                  "pi_estimate": 4.0 * cnt.sum().item() / pairs}
         del f_st, cnt, sm_
 
+    # batched uneven requests vs back-to-back plain launches at identical output
+    batched = None
+    if not args.skip_batched:
+        batched = run_batched(mrg, W, dev, stream, seed, quick=args.quick)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         import oracle
@@ -378,6 +438,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "fused": fused,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -396,6 +457,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fused", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")
     ap.add_argument("--draws", type=int, default=0, help="override draws per stream (profiling)")
     ap.add_argument("--only", default="", help="comma list of dist:dtype variants (profiling)")

@@ -180,6 +180,53 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- batched requests (one persistent, graph-captured launch) ----------- */
+
+/* One generation request at an absolute position of one stream: draws start
+ * `offset` draws after the start of substream `substream` of stream `stream`
+ * (i.e. start + substream * 2^76 + offset; substreams, Sec. 2.1), and n
+ * outputs of (dist, dtype) go to `out` (device, 32-byte aligned, n elements).
+ * Normals consume n + (n mod 2) draws.  The output is a function of the
+ * request alone: it does not depend on the other requests of the batch, their
+ * order or the launch configuration, and equals what mrg_generate writes for
+ * a single stream positioned at the same draw. */
+typedef struct mrg_request {
+    uint64_t stream;
+    uint64_t substream; /* < 2^51 */
+    uint64_t offset;    /* offset + draws consumed <= 2^62 (inside the substream) */
+    uint64_t n;
+    int32_t dist;
+    int32_t dtype;
+    double rate;        /* exponentials: in [2^-64, 2^64] */
+    void *out;
+} mrg_request;
+
+typedef struct mrg_batch mrg_batch; /* opaque */
+
+/* Creates a batch runner for the streams of `s` (their `start` arrays are
+ * read; no state is written) holding up to max_requests requests and
+ * max_tiles tiles (a tile = up to 32 segments of one request; a request of n
+ * draws takes about ceil(n / 65536) tiles, at least one).  Allocates its
+ * device tables and pinned host staging, and captures one CUDA graph
+ * [tables host->device, claim counter reset, persistent kernel] on `stream`.
+ * Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_batch_create(const mrg_streams *s, uint32_t max_requests, uint64_t max_tiles,
+                     mrg_batch **out, void *stream);
+
+/* Runs nreq requests with one graph launch on `stream` (asynchronous; the
+ * outputs are ready when `stream` reaches the end of the launch).  Waits for
+ * the previous run of the same batch object to finish with its host tables.
+ * Errors: MRG_EINVAL (bad request: stream index, dist/dtype, rate, NULL or
+ * unaligned out), MRG_ERANGE (substream >= 2^51, offset + draws > 2^62, more
+ * requests or tiles than the batch holds), MRG_ECUDA. */
+int mrg_batch_run(mrg_batch *b, const mrg_request *reqs, uint32_t nreq, void *stream);
+
+/* Number of tiles the last mrg_batch_run built. */
+uint64_t mrg_batch_last_tiles(const mrg_batch *b);
+
+/* Frees the batch object (synchronises its last run). */
+int mrg_batch_destroy(mrg_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

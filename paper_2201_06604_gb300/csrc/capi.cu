@@ -304,4 +304,174 @@ int mrg_fused_pi_normsum(const mrg_streams* s, uint64_t draws, int64_t* count, d
   return MRG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched requests
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct mrg_batch {
+  int device = 0;
+  mrg_streams s{};
+  uint32_t max_req = 0;
+  uint64_t max_tiles = 0;
+  uint64_t last_tiles = 0;
+  int grid = 0;
+  void* d_hdr = nullptr;
+  void* d_reqs = nullptr;
+  void* d_tiles = nullptr;
+  mrg::BatchHeaderHost* h_hdr = nullptr;
+  mrg::BatchReqHost* h_reqs = nullptr;
+  mrg::BatchTileHost* h_tiles = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool ran = false;
+};
+
+namespace {
+
+void batch_free(mrg_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  cudaFree(b->d_hdr);
+  cudaFree(b->d_reqs);
+  cudaFree(b->d_tiles);
+  cudaFreeHost(b->h_hdr);
+  cudaFreeHost(b->h_reqs);
+  cudaFreeHost(b->h_tiles);
+  delete b;
+}
+
+// Segment length of a request of `draws` draws: whole 32-byte units, about
+// draws / 32 so that short requests still fill a warp, at most 2048.
+uint32_t batch_seg_len(uint64_t draws) {
+  uint64_t L = (draws + 31) / 32;
+  L = (L + 7) / 8 * 8;
+  if (L < 8) L = 8;
+  if (L > 2048) L = 2048;
+  return (uint32_t)L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mrg_batch_create(const mrg_streams* s, uint32_t max_requests, uint64_t max_tiles,
+                     mrg_batch** out, void* stream) {
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (max_requests == 0 || max_tiles == 0) return fail(MRG_EINVAL, "empty batch capacity");
+  if (max_tiles > (1ull << 32)) return fail(MRG_ERANGE, "max_tiles too large");
+  int rc = ensure_device();
+  if (rc) return rc;
+  mrg_batch* b = new mrg_batch;
+  cudaGetDevice(&b->device);
+  b->s = *s;
+  b->max_req = max_requests;
+  b->max_tiles = max_tiles;
+  b->grid = mrg::batch_grid();
+  const size_t rb = sizeof(mrg::BatchReqHost) * max_requests;
+  const size_t tb = sizeof(mrg::BatchTileHost) * max_tiles;
+  const size_t hb = sizeof(mrg::BatchHeaderHost);
+  cudaError_t e = cudaMalloc(&b->d_hdr, hb);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_reqs, rb);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, tb);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr, hb);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_reqs, rb);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_tiles, tb);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return fail_cuda(e, "allocating batch tables");
+  }
+  // Capture [tables -> device, kernel] once; replays read the staging buffers.
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr, hb, cudaMemcpyHostToDevice, cap);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_reqs, b->h_reqs, rb, cudaMemcpyHostToDevice, cap);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tiles, b->h_tiles, tb, cudaMemcpyHostToDevice, cap);
+  if (e == cudaSuccess)
+    e = mrg::launch_batch(b->d_hdr, b->d_reqs, b->d_tiles, s->start, s->stride, b->grid, cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+  if (e == cudaSuccess) e = e2;
+  b->graph = g;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (cap) cudaStreamDestroy(cap);
+  (void)stream;
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return fail_cuda(e, "capturing the batch graph");
+  }
+  *out = b;
+  return MRG_OK;
+}
+
+int mrg_batch_run(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, void* stream) {
+  if (!b) return fail(MRG_EINVAL, "batch is NULL");
+  if (nreq > 0 && !reqs) return fail(MRG_EINVAL, "reqs is NULL");
+  if (nreq > b->max_req) return fail(MRG_ERANGE, "more requests than the batch holds");
+  if (b->ran) {
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return fail_cuda(e, "waiting for the previous batch");
+  }
+  uint64_t nt = 0;
+  for (uint32_t r = 0; r < nreq; ++r) {
+    const mrg_request& q = reqs[r];
+    const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
+                         ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
+                           q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
+    if (!pair_ok) return fail(MRG_EINVAL, "request with unsupported dist/dtype");
+    if (q.stream >= b->s.n) return fail(MRG_EINVAL, "request stream index out of range");
+    if (q.substream >= (1ull << 51)) return fail(MRG_ERANGE, "substream index >= 2^51");
+    const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
+    if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
+      return fail(MRG_ERANGE, "offset + draws too large");
+    if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
+      return fail(MRG_EINVAL, "request output NULL or not 32-byte aligned");
+    if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
+      return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+    mrg::BatchReqHost& h = b->h_reqs[r];
+    h.out = reinterpret_cast<uint64_t>(q.out);
+    h.n = q.n;
+    h.off = q.offset;
+    h.sub = q.substream;
+    h.stream = q.stream;
+    h.dist = (uint32_t)q.dist;
+    h.dtype = (uint32_t)q.dtype;
+    const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
+    h.ir_hi = (float)ir;
+    h.ir_lo = (float)(ir - (double)h.ir_hi);
+    h.L = batch_seg_len(q.n);
+    h.nseg = (uint32_t)((q.n + h.L - 1) / h.L);
+    const uint64_t tiles = (h.nseg + 31) / 32;
+    if (nt + tiles > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
+    for (uint64_t k = 0; k < tiles; ++k) b->h_tiles[nt + k] = mrg::BatchTileHost{r, (uint32_t)(32 * k)};
+    nt += tiles;
+  }
+  b->h_hdr->next_tile = 0;
+  b->h_hdr->ntiles = nt;
+  b->last_tiles = nt;
+  cudaError_t e = cudaGraphLaunch(b->exec, cs(stream));
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGraphLaunch (batch)");
+  mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
+  b->ran = true;
+  return MRG_OK;
+}
+
+uint64_t mrg_batch_last_tiles(const mrg_batch* b) { return b ? b->last_tiles : 0; }
+
+int mrg_batch_destroy(mrg_batch* b) {
+  if (!b) return MRG_OK;
+  if (b->ran) cudaEventSynchronize(b->done);
+  batch_free(b);
+  return MRG_OK;
+}
+
 }  // extern "C"

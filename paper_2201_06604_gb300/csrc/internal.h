@@ -54,4 +54,28 @@ cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype,
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Batched requests (batch_kernels.cuh).  Host-side mirrors of the device
+// descriptors: 64-byte request and 8-byte tile records.
+struct BatchReqHost {
+  uint64_t out, n, off, sub, stream;
+  uint32_t dist, dtype;
+  float ir_hi, ir_lo;
+  uint32_t L, nseg;
+};
+struct BatchTileHost {
+  uint32_t req, g0;
+};
+struct BatchHeaderHost {
+  unsigned long long next_tile;
+  uint64_t ntiles;
+};
+static_assert(sizeof(BatchReqHost) == 64, "request record layout");
+static_assert(sizeof(BatchTileHost) == 8, "tile record layout");
+
+// Persistent grid size of the batch kernel on the current device.
+int batch_grid();
+// One launch of the persistent batch kernel over the device tables.
+cudaError_t launch_batch(void* hdr, const void* reqs, const void* tiles, const uint32_t* start,
+                         uint64_t stride, int grid, cudaStream_t st);
+
 }  // namespace mrg

@@ -356,6 +356,12 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
   }
 }
 
+}  // namespace mrg
+
+#include "batch_kernels.cuh"
+
+namespace mrg {
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -505,6 +511,29 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
     case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64>(a, vb, cfg, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+int batch_grid() {
+  static std::mutex mu;
+  static int grid[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (grid[dev & 63] == 0) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, 256, 0);
+    grid[dev & 63] = sm_count() * (occ > 0 ? occ : 1);
+  }
+  return grid[dev & 63];
+}
+
+cudaError_t launch_batch(void* hdr, const void* reqs, const void* tiles, const uint32_t* start,
+                         uint64_t stride, int grid, cudaStream_t st) {
+  batch_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<BatchHeader*>(hdr),
+                                     reinterpret_cast<const BatchReq*>(reqs),
+                                     reinterpret_cast<const BatchTile*>(tiles), start, stride,
+                                     K1, K2);
+  return after_launch();
 }
 
 cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype, double rate,

@@ -37,6 +37,12 @@ class MrgError(RuntimeError):
         self.code = code
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_uint64), ("substream", ctypes.c_uint64),
+                ("offset", ctypes.c_uint64), ("n", ctypes.c_uint64), ("dist", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("rate", ctypes.c_double), ("out", ctypes.c_void_p)]
+
+
 class _Streams(ctypes.Structure):
     _fields_ = [("cur", ctypes.c_void_p), ("start", ctypes.c_void_p), ("sub", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("stride", ctypes.c_uint64)]
@@ -66,6 +72,10 @@ def _load():
         "mrg_get_state": ([sp, u32p, vp], i32),
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+        "mrg_batch_create": ([sp, ctypes.c_uint32, u64, ctypes.POINTER(vp), vp], i32),
+        "mrg_batch_run": ([vp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
+        "mrg_batch_last_tiles": ([vp], u64),
+        "mrg_batch_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -303,3 +313,69 @@ def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream
         _check(lib.mrg_fused_pi_normsum(streams.ptr(), draws, count.data_ptr(), sum_.data_ptr(),
                                         _stream_handle(stream)))
     return count, sum_
+
+
+_DT_CODE = {"u32": U32, "f32": F32, "f64": F64}
+_DT_TORCH = {"u32": torch.int32, "f32": torch.float32, "f64": torch.float64}
+
+
+class Batch:
+    """Runner of batched requests over a stream set: one persistent,
+    graph-captured kernel launch per run.  A request is a dict with keys
+    stream, substream, offset (default 0), n, dist ("uniform" / "normal" /
+    "exponential" / "raw" or code), dtype ("f32" / "f64" / "u32"), rate
+    (default 1.0) and out (a device tensor of n elements, 32-byte aligned)."""
+
+    def __init__(self, streams: Streams, max_requests: int = 4096, max_tiles: int = 1 << 16,
+                 stream=None):
+        self.streams = streams
+        self.max_requests = max_requests
+        h = ctypes.c_void_p()
+        with torch.cuda.device(streams.device):
+            _check(lib.mrg_batch_create(streams.ptr(), max_requests, max_tiles, ctypes.byref(h),
+                                        _stream_handle(stream)))
+        self._h = h
+
+    def run(self, requests, stream=None):
+        arr = (_Request * max(len(requests), 1))()
+        for i, q in enumerate(requests):
+            d = _DIST[q["dist"]] if isinstance(q["dist"], str) else int(q["dist"])
+            dt = q.get("dtype", "f64")
+            arr[i] = _Request(q["stream"], q.get("substream", 0), q.get("offset", 0), q["n"], d,
+                              U32 if d == RAW else _DT_CODE[dt], float(q.get("rate", 1.0)),
+                              q["out"].data_ptr() if q["n"] else None)
+        with torch.cuda.device(self.streams.device):
+            _check(lib.mrg_batch_run(self._h, arr, len(requests), _stream_handle(stream)))
+
+    @property
+    def last_tiles(self) -> int:
+        return int(lib.mrg_batch_last_tiles(self._h))
+
+    def close(self):
+        if self._h:
+            lib.mrg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alloc_outputs(requests, device=None, align: int = 256):
+    """One device buffer holding every request's output (aligned slices);
+    sets q["out"] on each request and returns the backing buffer."""
+    offs, total = [], 0
+    for q in requests:
+        es = 8 if q.get("dtype", "f64") == "f64" else 4
+        offs.append(total)
+        total += (q["n"] * es + align - 1) // align * align
+    buf = torch.empty(max(total, align), dtype=torch.uint8, device=device or "cuda")
+    for q, o in zip(requests, offs):
+        dt = q.get("dtype", "f64")
+        if (_DIST[q["dist"]] if isinstance(q["dist"], str) else int(q["dist"])) == RAW:
+            dt = "u32"
+        es = 8 if dt == "f64" else 4
+        q["out"] = buf[o: o + q["n"] * es].view(_DT_TORCH[dt])
+    return buf

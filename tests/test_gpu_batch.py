@@ -1,0 +1,142 @@
+"""Batched requests (one persistent, graph-captured launch): each request's
+output equals the oracle at the same absolute stream position, equals what
+the plain entry point writes for a single stream positioned there (bit for
+bit), and does not depend on the other requests or their order."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2201_06604_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SEED = W.PAPER_SEED
+DISTS = {"raw": O.RAW, "uniform": O.UNIFORM, "normal": O.NORMAL, "exponential": O.EXPONENTIAL}
+
+
+@pytest.fixture(scope="module")
+def M():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2201_06604_gb300 import mrg
+    return mrg
+
+
+def make_requests(ns, count, seed, nmax=20000):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for r in range(count):
+        dist = ["raw", "uniform", "normal", "exponential"][rng.integers(0, 4)]
+        dtype = "u32" if dist == "raw" else ["f32", "f64"][rng.integers(0, 2)]
+        n = int(rng.choice([0, 1, 2, 3, 7, 8, 9, 31, 255, 256, 257, 1000, 4097,
+                            int(rng.integers(1, nmax))]))
+        reqs.append(dict(stream=int(rng.integers(0, ns)), substream=int(rng.integers(0, 3)),
+                         offset=int(rng.integers(0, 1 << 40)) if rng.integers(0, 2) else 0,
+                         n=n, dist=dist, dtype=dtype, rate=float(rng.choice([1.0, 2.5]))))
+    return reqs
+
+
+def oracle_request(start_states, q):
+    st = O.jump(start_states[q["stream"]], (q["substream"] << 76) + q["offset"])
+    out, _ = O.generate_streams(st[None, :], q["n"], DISTS[q["dist"]],
+                                f32=q["dtype"] == "f32", rate=q["rate"])
+    return out[0]
+
+
+def check_close(got, ref, q):
+    if q["dist"] in ("raw", "uniform"):
+        assert np.array_equal(got.astype(ref.dtype) if q["dist"] == "uniform" else got.view(np.uint32),
+                              ref), q
+    elif q["dtype"] == "f64":
+        tol = 1e-12 / min(q["rate"], 1.0)
+        assert np.abs(got - ref).max() <= tol, q
+    else:
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        assert (np.abs(got.astype(np.float64) - ref) <= 2 * ulp).all(), q
+
+
+def test_batch_matches_oracle(M):
+    ns = 300
+    s = M.create_streams(ns, seed=SEED)
+    start, _ = O.create_streams(SEED, ns)
+    reqs = make_requests(ns, 120, seed=11)
+    buf = M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=256, max_tiles=4096)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    assert b.last_tiles >= sum(1 for q in reqs if q["n"] > 0)
+    for q in reqs:
+        if q["n"] == 0:
+            continue
+        got = q["out"].cpu().numpy()
+        check_close(got, oracle_request(start, q), q)
+    b.close()
+    del buf
+
+
+def test_batch_equals_plain_and_is_order_independent(M):
+    ns = 64
+    s = M.create_streams(ns, seed=(1, 2, 3, 4, 5, 6))
+    reqs = make_requests(ns, 80, seed=12)
+    buf1 = M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=128, max_tiles=4096)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    first = [q["out"].clone() for q in reqs]
+    # same requests, reversed order, in a fresh output buffer
+    rev = [dict(q) for q in reversed(reqs)]
+    buf2 = M.alloc_outputs(rev)
+    b.run(rev)
+    torch.cuda.synchronize()
+    for q, a in zip(reversed(rev), first):
+        assert torch.equal(q["out"], a)
+    # plain generate on a single stream positioned at the request's draw
+    for q, a in zip(reqs, first):
+        if q["n"] == 0:
+            continue
+        one = M.create_streams(1, seed=tuple(int(v) for v in M.get_state(s)[1][:, q["stream"]]))
+        for _ in range(q["substream"]):
+            M.substream_next(one)
+        M.skip(one, q["offset"])
+        dt = {"f32": torch.float32, "f64": torch.float64, "u32": torch.int32}[q["dtype"]]
+        p = M.generate(one, q["n"], q["dist"], dt, rate=q["rate"])[0]
+        assert torch.equal(p, a), q
+    b.close()
+    del buf1, buf2
+
+
+def test_batch_alone_equals_in_mix(M):
+    ns = 32
+    s = M.create_streams(ns, seed=SEED)
+    reqs = make_requests(ns, 40, seed=13)
+    M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=64, max_tiles=2048)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    for q in reqs[::7]:
+        alone = dict(q)
+        M.alloc_outputs([alone])
+        b.run([alone])
+        torch.cuda.synchronize()
+        assert torch.equal(alone["out"], q["out"])
+    b.close()
+
+
+def test_batch_errors(M):
+    s = M.create_streams(4, seed=SEED)
+    b = M.Batch(s, max_requests=2, max_tiles=4)
+    out = torch.empty(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MrgError):
+        b.run([dict(stream=4, n=8, dist="uniform", dtype="f64", out=out)])        # bad stream
+    with pytest.raises(M.MrgError):
+        b.run([dict(stream=0, n=8, dist="uniform", dtype="f64", out=out[1:])])    # misaligned
+    with pytest.raises(M.MrgError):
+        b.run([dict(stream=0, n=8, dist="uniform", dtype="u32", out=out)])        # no u32 uniform
+    with pytest.raises(M.MrgError):
+        b.run([dict(stream=0, n=8, dist="uniform", dtype="f64", out=out)] * 3)   # too many
+    big = torch.empty(600000, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MrgError):
+        b.run([dict(stream=0, n=600000, dist="uniform", dtype="f64", out=big)])  # too many tiles
+    b.run([dict(stream=1, n=8, dist="uniform", dtype="f64", out=out)])           # still usable
+    torch.cuda.synchronize()
+    b.close()
