@@ -227,6 +227,24 @@ uint64_t mrg_batch_last_tiles(const mrg_batch *b);
 /* Frees the batch object (synchronises its last run). */
 int mrg_batch_destroy(mrg_batch *b);
 
+/* mrg_batch_run for callers that cannot allocate device memory -- code that
+ * runs inside a CUDA graph capture, plug-ins whose host application owns the
+ * device-memory budget, loops that cannot afford cudaMalloc's implicit
+ * synchronisation.  It allocates nothing: the request table, tile table and
+ * claim counter live in a fixed device array of 192.25 KiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Limits per call: 1024 requests and 16384 tiles (a tile holds up to
+ * 32 segments of one request; a request of n draws takes about
+ * ceil(n / 65536) tiles, at least one); larger calls fail with MRG_ERANGE and
+ * run nothing.  The first call on a device does the set-up (the library's
+ * tables and the device address of the array), so make it before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (different CUDA streams, or several host threads) race; calls ordered on
+ * one stream are safe.  Outputs are those of mrg_batch_run.  The paper has
+ * no counterpart of this entry point.  Errors: as mrg_batch_run. */
+int mrg_batch_run_static(const mrg_streams *s, const mrg_request *reqs, uint32_t nreq,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

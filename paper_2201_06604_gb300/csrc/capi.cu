@@ -70,6 +70,11 @@ inline cudaStream_t cs(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 
 }  // namespace
 
+namespace mrg {
+int ensure_device_ready() { return ensure_device(); }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace mrg
+
 extern "C" {
 
 const char* mrg_last_error(void) { return t_err.c_str(); }

@@ -72,6 +72,11 @@ struct BatchHeaderHost {
 static_assert(sizeof(BatchReqHost) == 64, "request record layout");
 static_assert(sizeof(BatchTileHost) == 8, "tile record layout");
 
+// Library set-up of the current device (jump and transform tables), and the
+// calling thread's error text; both implemented in capi.cu.
+int ensure_device_ready();
+int set_error(int code, const char* msg);
+
 // Persistent grid size of the batch kernel on the current device.
 int batch_grid();
 // One launch of the persistent batch kernel over the device tables.
