@@ -241,6 +241,90 @@ def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3):
     return res
 
 
+def run_serving(mrg, W, dev, seed, seconds=10.0, arena_gb=40):
+    """Poisson arrivals (2000 req/s), sizes log-uniform in [1e3, 1e8] draws,
+    mixed dist/dtype, 2^20 resident streams, request -> uniform stream id (its
+    next substream), outputs in a 40 GB arena released on completion: the
+    serving engine vs the same trace served by serial plain calls."""
+    import collections
+    import torch
+    trace = W.serving_trace(seconds=seconds)
+    for q in trace:
+        q["dist"] = {1: "uniform", 2: "normal", 3: "exponential"}[q["dist"]]
+    ns = 1 << 20
+    streams = mrg.create_streams(ns, device=dev, seed=seed)
+    next_sub = collections.defaultdict(int)
+    for q in trace:
+        q["substream"] = next_sub[q["stream"]]
+        next_sub[q["stream"]] += 1
+    draws = sum(q["n"] + (q["n"] & 1 if q["dist"] == "normal" else 0) for q in trace)
+
+    def pct(lat):
+        a = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "p999_ms": float(np.percentile(a, 99.9)), "mean_ms": float(a.mean())}
+
+    # serving engine
+    sv = mrg.Server(streams, arena_gb << 30, max_slots=8192, ring_tiles=1 << 18, idle_seconds=60.0,
+                    sm_fraction=1.0)
+    lat, arrival, busy = [], {}, 0
+    pending = collections.deque()
+    i, n_req = 0, len(trace)
+    t0 = time.perf_counter()
+    while i < n_req or pending or arrival:
+        now = time.perf_counter() - t0
+        while i < n_req and trace[i]["t"] <= now:
+            pending.append(trace[i])
+            i += 1
+        while pending:
+            q = pending[0]
+            r = sv.submit(q["stream"], q["n"], q["dist"], q["dtype"], q["substream"], 0, q["rate"])
+            if r is None:
+                busy += 1
+                break
+            arrival[r[0]] = q["t"]
+            pending.popleft()
+        done = sv.poll()
+        if done:
+            tc = time.perf_counter() - t0
+            for rid in done:
+                lat.append(tc - arrival.pop(rid))
+                sv.release(rid)
+        if now > seconds + 120:
+            raise RuntimeError("serving run did not drain")
+    t_end = time.perf_counter() - t0
+    sv.close()
+    served = {"requests": n_req, "draws": draws, "draws_per_s": draws / t_end,
+              "wall_s": t_end, "busy_retries": busy, **pct(lat)}
+    del sv
+    torch.cuda.empty_cache()
+
+    # serial plain calls (one request at a time, synchronous)
+    maxn = max(q["n"] for q in trace)
+    out = torch.empty(maxn * 8, dtype=torch.uint8, device=dev)
+    tdt = {"f32": torch.float32, "f64": torch.float64}
+    lat = []
+    t0 = time.perf_counter()
+    for q in trace:
+        now = time.perf_counter() - t0
+        if now < q["t"]:
+            while time.perf_counter() - t0 < q["t"]:
+                pass
+        es = 8 if q["dtype"] == "f64" else 4
+        o = out[: q["n"] * es].view(tdt[q["dtype"]]).view(1, -1)
+        mrg.generate(streams.view(q["stream"], 1), q["n"], q["dist"], tdt[q["dtype"]], out=o)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0 - q["t"])
+    t_end = time.perf_counter() - t0
+    serial = {"draws_per_s": draws / t_end, "wall_s": t_end, **pct(lat)}
+    del out, streams
+    torch.cuda.empty_cache()
+    return {"workload": f"Poisson 2000 req/s for {seconds:g} s ({n_req} requests), n log-uniform "
+                        "[1e3, 1e8], mixed dist/dtype, 2^20 resident streams, 40 GB arena",
+            "offered_draws_per_s": draws / seconds, "server": served, "serial_plain": serial,
+            "p99_speedup": serial["p99_ms"] / served["p99_ms"]}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -412,6 +496,10 @@ def run_gpu(args):
     if not args.skip_batched:
         batched = run_batched(mrg, W, dev, stream, seed, quick=args.quick)
 
+    serving = None
+    if not args.skip_serving:
+        serving = run_serving(mrg, W, dev, seed, seconds=2.0 if args.quick else args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         import oracle
@@ -439,6 +527,7 @@ def run_gpu(args):
         "e2e": e2e,
         "fused": fused,
         "batched": batched,
+        "serving": serving,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -458,6 +547,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")
     ap.add_argument("--draws", type=int, default=0, help="override draws per stream (profiling)")
     ap.add_argument("--only", default="", help="comma list of dist:dtype variants (profiling)")

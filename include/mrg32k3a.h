@@ -245,6 +245,55 @@ int mrg_batch_destroy(mrg_batch *b);
 int mrg_batch_run_static(const mrg_streams *s, const mrg_request *reqs, uint32_t nreq,
                          void *stream);
 
+/* ---- serving engine: continuous batching into one persistent worker ---- */
+
+typedef struct mrg_server mrg_server; /* opaque */
+
+/* Starts a server over the streams of `s` (their `start` arrays are read):
+ * a persistent worker kernel that processes requests appended to a ring while
+ * it runs.  sm_fraction in (0, 1] is the share of every SM's resident blocks
+ * the worker takes: 1 gives it the whole GPU (kernels of other streams then
+ * wait until the worker stops); smaller values leave room for them.  Outputs are placed in `arena` (caller-owned device memory,
+ * 256-byte aligned, arena_bytes long).  max_slots bounds the requests in
+ * flight, ring_tiles (a power of two) the tiles in flight (a request of n
+ * draws takes about ceil(n / 65536) tiles).  The worker exits by itself after
+ * idle_seconds with no published work (a host that stopped feeding it);
+ * later calls then report MRG_ETIMEOUT until mrg_server_restart.
+ * Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_server_create(const mrg_streams *s, void *arena, uint64_t arena_bytes,
+                      uint32_t max_slots, uint64_t ring_tiles, double idle_seconds,
+                      double sm_fraction, mrg_server **out);
+
+/* Admits a request (its `out` field is ignored: the server places the output
+ * in the arena and returns its device address in *out, may be NULL).  The
+ * request is appended to the running worker at once; its output is that of
+ * mrg_batch_run for the same request.  *id identifies it in poll/release.
+ * Errors: MRG_EBUSY (no free slot, ring space or arena memory -- retry after
+ * releasing finished requests), MRG_EINVAL, MRG_ERANGE (larger than the ring
+ * or the arena), MRG_ETIMEOUT (the worker has stopped), MRG_ECUDA. */
+int mrg_server_submit(mrg_server *sv, const mrg_request *req, uint64_t *id, void **out);
+
+/* Writes up to max_ids ids of requests that finished since the last poll to
+ * ids[0..*count).  A finished request's output is complete in device memory
+ * for any work the caller orders after this call.  Returns MRG_ETIMEOUT if
+ * the worker stopped (idle limit), MRG_ECUDA on a device error. */
+int mrg_server_poll(mrg_server *sv, uint64_t *ids, uint32_t max_ids, uint32_t *count);
+
+/* The client's acknowledgement of a finished request: frees its slot and its
+ * arena memory.  MRG_EBUSY if it has not finished, MRG_EINVAL if unknown. */
+int mrg_server_release(mrg_server *sv, uint64_t id);
+
+/* Requests admitted and not yet finished. */
+uint64_t mrg_server_inflight(mrg_server *sv);
+
+/* Relaunches a worker that stopped (idle limit); requests that were in flight
+ * are dropped (their slots and memory freed).  No-op while it runs. */
+int mrg_server_restart(mrg_server *sv);
+
+/* Stops the worker once every admitted request has been processed, waits for
+ * it and frees the server (the arena stays the caller's). */
+int mrg_server_destroy(mrg_server *sv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
 }  // namespace mrg
 
 #include "batch_kernels.cuh"
+#include "serve_kernels.cuh"
 
 namespace mrg {
 
@@ -533,6 +534,23 @@ cudaError_t launch_batch(void* hdr, const void* reqs, const void* tiles, const u
                                      reinterpret_cast<const BatchReq*>(reqs),
                                      reinterpret_cast<const BatchTile*>(tiles), start, stride,
                                      K1, K2);
+  return after_launch();
+}
+
+int serve_grid(double sm_fraction) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, serve_kernel, 256, 0);
+  const int per_sm = std::max(1, (int)(occ * sm_fraction + 0.5));
+  return sm_count() * per_sm;
+}
+
+cudaError_t launch_serve(void* ctl, const void* slots, const void* ring, uint64_t ring_mask,
+                         unsigned int* tiles_done, unsigned int* done_words, const uint32_t* start,
+                         uint64_t stride, uint64_t idle_ns, int grid, cudaStream_t st) {
+  serve_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<ServeCtl*>(ctl),
+                                     reinterpret_cast<const BatchReq*>(slots),
+                                     reinterpret_cast<const ServeTile*>(ring), ring_mask, tiles_done,
+                                     done_words, start, stride, K1, K2, idle_ns);
   return after_launch();
 }
 

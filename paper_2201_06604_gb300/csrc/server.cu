@@ -1,0 +1,356 @@
+// server.cu -- serving engine: continuous batching of generation requests
+// into one persistent worker kernel (serve_kernels.cuh).
+//
+// Admission is by slots, ring space and output memory: a request is admitted
+// only if a slot is free, its tiles fit in the ring and its output fits in
+// the caller's device arena (first fit); otherwise submit returns MRG_EBUSY
+// and the caller keeps it queued.  Admitted requests are appended to the ring
+// of the running worker, so they overlap on the device with requests already
+// in flight.  The client acknowledges a finished request with release, which
+// returns its slot and output memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mrg32k3a.h"
+#include "internal.h"
+
+struct mrg_server {
+  int device = 0;
+  mrg_streams s{};
+  char* arena = nullptr;
+  uint64_t arena_bytes = 0;
+  uint32_t max_slots = 0;
+  uint64_t ring_tiles = 0;      // power of two
+  uint64_t idle_ns = 0;
+  int grid = 0;
+  // host-mapped pinned memory (written by the host, read by the worker)
+  mrg::BatchReqHost* slots_h = nullptr;
+  mrg::ServeTileHost* ring_h = nullptr;
+  unsigned int* done_h = nullptr;          // written by the worker
+  void* slots_d = nullptr;
+  void* ring_d = nullptr;
+  unsigned int* done_d = nullptr;
+  unsigned long long* tail_h = nullptr;    // pinned staging of the published tail
+  unsigned int* stop_h = nullptr;
+  // device memory
+  mrg::ServeCtlHost* ctl_d = nullptr;
+  unsigned int* tiles_done_d = nullptr;
+  cudaStream_t worker = nullptr;
+  cudaStream_t copier = nullptr;
+  bool running = false;
+  bool failed = false;
+  // bookkeeping
+  std::mutex mu;
+  uint64_t tail = 0;
+  uint64_t next_seq = 1;
+  std::vector<uint32_t> free_slots;
+  std::map<uint64_t, uint64_t> free_mem;   // offset -> size
+  struct Inflight {
+    uint32_t slot;
+    uint32_t seq;
+    uint64_t mem_off, mem_size;
+    uint64_t ring_first;
+    bool done;
+  };
+  std::unordered_map<uint64_t, Inflight> inflight;  // id -> state
+  std::multiset<uint64_t> ring_firsts;               // first ring positions of undone requests
+};
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+
+uint32_t seg_len_for(uint64_t draws) {
+  uint64_t L = (draws + 31) / 32;
+  L = (L + 7) / 8 * 8;
+  if (L < 8) L = 8;
+  if (L > 2048) L = 2048;
+  return (uint32_t)L;
+}
+
+bool arena_alloc(mrg_server* sv, uint64_t size, uint64_t* off) {
+  for (auto it = sv->free_mem.begin(); it != sv->free_mem.end(); ++it) {
+    if (it->second >= size) {
+      *off = it->first;
+      const uint64_t rest = it->second - size;
+      const uint64_t next = it->first + size;
+      sv->free_mem.erase(it);
+      if (rest) sv->free_mem[next] = rest;
+      return true;
+    }
+  }
+  return false;
+}
+
+void arena_free(mrg_server* sv, uint64_t off, uint64_t size) {
+  auto it = sv->free_mem.emplace(off, size).first;
+  auto nx = std::next(it);
+  if (nx != sv->free_mem.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    sv->free_mem.erase(nx);
+  }
+  if (it != sv->free_mem.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      sv->free_mem.erase(it);
+    }
+  }
+}
+
+int launch_worker(mrg_server* sv) {
+  mrg::ServeCtlHost c{sv->tail, sv->tail, 0u, 0u};  // resume claiming at the first unpublished position
+  *sv->stop_h = 0;
+  cudaError_t e = cudaMemcpyAsync(sv->ctl_d, &c, sizeof c, cudaMemcpyHostToDevice, sv->worker);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sv->worker);
+  if (e == cudaSuccess)
+    e = mrg::launch_serve(sv->ctl_d, sv->slots_d, sv->ring_d, sv->ring_tiles - 1, sv->tiles_done_d,
+                          sv->done_d, sv->s.start, sv->s.stride, sv->idle_ns, sv->grid, sv->worker);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  sv->running = true;
+  sv->failed = false;
+  return MRG_OK;
+}
+
+// The worker stream finished while it should be running: the idle limit
+// fired (no published work for idle_ns).  Every request still in flight is
+// reported as failed.
+int check_worker(mrg_server* sv) {
+  if (!sv->running) return sv->failed ? MRG_ETIMEOUT : MRG_OK;
+  cudaError_t q = cudaStreamQuery(sv->worker);
+  if (q == cudaErrorNotReady) return MRG_OK;
+  sv->running = false;
+  if (q != cudaSuccess) {
+    sv->failed = true;
+    return mrg::set_error(MRG_ECUDA, cudaGetErrorString(q));
+  }
+  sv->failed = true;
+  return mrg::set_error(MRG_ETIMEOUT, "serving worker reached its idle limit and exited");
+}
+
+void server_free(mrg_server* sv) {
+  if (!sv) return;
+  if (sv->worker) cudaStreamDestroy(sv->worker);
+  if (sv->copier) cudaStreamDestroy(sv->copier);
+  cudaFree(sv->ctl_d);
+  cudaFree(sv->tiles_done_d);
+  cudaFreeHost(sv->slots_h);
+  cudaFreeHost(sv->ring_h);
+  cudaFreeHost(sv->done_h);
+  cudaFreeHost(sv->tail_h);
+  cudaFreeHost(sv->stop_h);
+  delete sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mrg_server_create(const mrg_streams* s, void* arena, uint64_t arena_bytes, uint32_t max_slots,
+                      uint64_t ring_tiles, double idle_seconds, double sm_fraction,
+                      mrg_server** out) {
+  if (!out) return mrg::set_error(MRG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!s || !s->start || s->stride < s->n || s->n == 0) return mrg::set_error(MRG_EINVAL, "bad stream set");
+  if (!arena || arena_bytes < kAlign || reinterpret_cast<uintptr_t>(arena) % kAlign)
+    return mrg::set_error(MRG_EINVAL, "arena NULL, too small or not 256-byte aligned");
+  if (max_slots == 0 || ring_tiles < 2 || (ring_tiles & (ring_tiles - 1)))
+    return mrg::set_error(MRG_EINVAL, "max_slots must be > 0 and ring_tiles a power of two");
+  if (!(idle_seconds > 0.0 && idle_seconds <= 3600.0))
+    return mrg::set_error(MRG_EINVAL, "idle_seconds must lie in (0, 3600]");
+  if (!(sm_fraction > 0.0 && sm_fraction <= 1.0))
+    return mrg::set_error(MRG_EINVAL, "sm_fraction must lie in (0, 1]");
+  int rc = mrg::ensure_device_ready();
+  if (rc) return rc;
+  mrg_server* sv = new mrg_server;
+  cudaGetDevice(&sv->device);
+  sv->s = *s;
+  sv->arena = static_cast<char*>(arena);
+  sv->arena_bytes = arena_bytes / kAlign * kAlign;
+  sv->max_slots = max_slots;
+  sv->ring_tiles = ring_tiles;
+  sv->idle_ns = (uint64_t)(idle_seconds * 1e9);
+  sv->grid = mrg::serve_grid(sm_fraction);
+  cudaError_t e = cudaHostAlloc((void**)&sv->slots_h, sizeof(mrg::BatchReqHost) * max_slots, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->ring_h, sizeof(mrg::ServeTileHost) * ring_tiles, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->done_h, sizeof(unsigned int) * max_slots, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->tail_h, sizeof(unsigned long long), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->stop_h, sizeof(unsigned int), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->slots_d, sv->slots_h, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->ring_d, sv->ring_h, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->done_d, sv->done_h, 0);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sv->ctl_d, sizeof(mrg::ServeCtlHost));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sv->tiles_done_d, sizeof(unsigned int) * max_slots);
+  if (e == cudaSuccess) e = cudaMemset(sv->tiles_done_d, 0, sizeof(unsigned int) * max_slots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->worker, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->copier, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    server_free(sv);
+    return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  }
+  std::memset(sv->done_h, 0, sizeof(unsigned int) * max_slots);
+  for (uint32_t i = max_slots; i-- > 0;) sv->free_slots.push_back(i);
+  sv->free_mem[0] = sv->arena_bytes;
+  rc = launch_worker(sv);
+  if (rc) {
+    server_free(sv);
+    return rc;
+  }
+  *out = sv;
+  return MRG_OK;
+}
+
+int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void** out) {
+  if (!sv || !q || !id) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  int rc = check_worker(sv);
+  if (rc) return rc;
+  const bool pair_ok = (q->dist == MRG_RAW && q->dtype == MRG_U32) ||
+                       ((q->dist == MRG_UNIFORM || q->dist == MRG_NORMAL ||
+                         q->dist == MRG_EXPONENTIAL) && (q->dtype == MRG_F32 || q->dtype == MRG_F64));
+  if (!pair_ok) return mrg::set_error(MRG_EINVAL, "unsupported dist/dtype combination");
+  if (q->stream >= sv->s.n) return mrg::set_error(MRG_EINVAL, "stream index out of range");
+  if (q->n == 0) return mrg::set_error(MRG_EINVAL, "empty request");
+  if (q->substream >= (1ull << 51)) return mrg::set_error(MRG_ERANGE, "substream index >= 2^51");
+  const uint64_t draws = q->dist == MRG_NORMAL ? q->n + (q->n & 1) : q->n;
+  if (q->offset > (1ull << 62) || draws > (1ull << 62) || q->offset + draws > (1ull << 62))
+    return mrg::set_error(MRG_ERANGE, "offset + draws too large");
+  if (q->dist == MRG_EXPONENTIAL && !(q->rate >= 0x1p-64 && q->rate <= 0x1p64))
+    return mrg::set_error(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+  const uint32_t L = seg_len_for(q->n);
+  const uint64_t nseg = (q->n + L - 1) / L;
+  const uint64_t ntiles = (nseg + 31) / 32;
+  const uint64_t bytes = (q->n * (q->dtype == MRG_F64 ? 8 : 4) + kAlign - 1) / kAlign * kAlign;
+  if (ntiles > sv->ring_tiles || bytes > sv->arena_bytes || nseg > 0xFFFFFFFFull)
+    return mrg::set_error(MRG_ERANGE, "request larger than the server's ring or arena");
+  // admission: a slot, ring space, output memory
+  const uint64_t ring_low = sv->ring_firsts.empty() ? sv->tail : *sv->ring_firsts.begin();
+  if (sv->free_slots.empty() || sv->tail + ntiles - ring_low > sv->ring_tiles)
+    return mrg::set_error(MRG_EBUSY, "no free slot or ring space");
+  uint64_t off = 0;
+  if (!arena_alloc(sv, bytes, &off)) return mrg::set_error(MRG_EBUSY, "output arena full");
+  const uint32_t slot = sv->free_slots.back();
+  sv->free_slots.pop_back();
+  const uint64_t seq64 = sv->next_seq++;
+  uint32_t seq = (uint32_t)seq64;
+  if (seq == 0) seq = 1;  // 0 marks "never completed"
+  mrg::BatchReqHost& h = sv->slots_h[slot];
+  h.out = reinterpret_cast<uint64_t>(sv->arena + off);
+  h.n = q->n;
+  h.off = q->offset;
+  h.sub = q->substream;
+  h.stream = q->stream;
+  h.dist = (uint32_t)q->dist;
+  h.dtype = (uint32_t)q->dtype;
+  const double ir = q->dist == MRG_EXPONENTIAL ? -1.0 / q->rate : 0.0;
+  h.ir_hi = (float)ir;
+  h.ir_lo = (float)(ir - (double)h.ir_hi);
+  h.L = L;
+  h.nseg = (uint32_t)nseg;
+  for (uint64_t k = 0; k < ntiles; ++k)
+    sv->ring_h[(sv->tail + k) & (sv->ring_tiles - 1)] =
+        mrg::ServeTileHost{slot, (uint32_t)(32 * k), (uint32_t)ntiles, seq};
+  sv->inflight[seq64] = mrg_server::Inflight{slot, seq, off, bytes, sv->tail, false};
+  sv->ring_firsts.insert(sv->tail);
+  sv->tail += ntiles;
+  std::atomic_thread_fence(std::memory_order_seq_cst);  // records before the tail that covers them
+  *sv->tail_h = sv->tail;
+  cudaError_t e = cudaMemcpyAsync(&sv->ctl_d->tail, sv->tail_h, sizeof(unsigned long long),
+                                  cudaMemcpyHostToDevice, sv->copier);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  *id = seq64;
+  if (out) *out = sv->arena + off;
+  return MRG_OK;
+}
+
+int mrg_server_poll(mrg_server* sv, uint64_t* ids, uint32_t max_ids, uint32_t* count) {
+  if (!sv || !count || (max_ids && !ids)) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *count = 0;
+  for (auto& kv : sv->inflight) {
+    auto& f = kv.second;
+    if (f.done) continue;
+    const unsigned int w = reinterpret_cast<volatile unsigned int*>(sv->done_h)[f.slot];
+    if (w != f.seq) continue;
+    f.done = true;
+    sv->ring_firsts.erase(sv->ring_firsts.find(f.ring_first));
+    if (*count < max_ids) ids[(*count)++] = kv.first;
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  return check_worker(sv);
+}
+
+int mrg_server_release(mrg_server* sv, uint64_t id) {
+  if (!sv) return mrg::set_error(MRG_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->inflight.find(id);
+  if (it == sv->inflight.end()) return mrg::set_error(MRG_EINVAL, "unknown request id");
+  if (!it->second.done) return mrg::set_error(MRG_EBUSY, "request not finished");
+  sv->free_slots.push_back(it->second.slot);
+  arena_free(sv, it->second.mem_off, it->second.mem_size);
+  sv->inflight.erase(it);
+  return MRG_OK;
+}
+
+uint64_t mrg_server_inflight(mrg_server* sv) {
+  if (!sv) return 0;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  uint64_t k = 0;
+  for (auto& kv : sv->inflight) k += kv.second.done ? 0 : 1;
+  return k;
+}
+
+int mrg_server_restart(mrg_server* sv) {
+  if (!sv) return mrg::set_error(MRG_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  check_worker(sv);
+  if (sv->running) return MRG_OK;
+  cudaError_t e = cudaStreamSynchronize(sv->worker);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sv->copier);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  // requests that were in flight when the worker stopped are dropped
+  for (auto it = sv->inflight.begin(); it != sv->inflight.end();) {
+    if (!it->second.done) {
+      sv->free_slots.push_back(it->second.slot);
+      arena_free(sv, it->second.mem_off, it->second.mem_size);
+      it = sv->inflight.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  sv->ring_firsts.clear();
+  e = cudaMemset(sv->tiles_done_d, 0, sizeof(unsigned int) * sv->max_slots);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  return launch_worker(sv);
+}
+
+int mrg_server_destroy(mrg_server* sv) {
+  if (!sv) return MRG_OK;
+  int rc = MRG_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->running) {
+      // stop only affects warps waiting for unpublished positions: every
+      // published tile is still processed before the worker exits
+      *sv->stop_h = 1;
+      cudaError_t e = cudaMemcpyAsync(&sv->ctl_d->stop, sv->stop_h, sizeof(unsigned int),
+                                      cudaMemcpyHostToDevice, sv->copier);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(sv->worker);
+      if (e != cudaSuccess) rc = mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+      sv->running = false;
+    }
+    cudaStreamSynchronize(sv->copier);
+  }
+  server_free(sv);
+  return rc;
+}
+
+}  // extern "C"

@@ -76,6 +76,17 @@ def _load():
         "mrg_batch_run": ([vp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
         "mrg_batch_last_tiles": ([vp], u64),
         "mrg_batch_destroy": ([vp], i32),
+        "mrg_batch_run_static": ([sp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
+        "mrg_server_create": ([sp, vp, u64, ctypes.c_uint32, u64, ctypes.c_double,
+                               ctypes.c_double, ctypes.POINTER(vp)], i32),
+        "mrg_server_submit": ([vp, ctypes.POINTER(_Request), ctypes.POINTER(u64),
+                               ctypes.POINTER(vp)], i32),
+        "mrg_server_poll": ([vp, ctypes.POINTER(u64), ctypes.c_uint32,
+                             ctypes.POINTER(ctypes.c_uint32)], i32),
+        "mrg_server_release": ([vp, u64], i32),
+        "mrg_server_inflight": ([vp], u64),
+        "mrg_server_restart": ([vp], i32),
+        "mrg_server_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -379,3 +390,70 @@ def alloc_outputs(requests, device=None, align: int = 256):
         es = 8 if dt == "f64" else 4
         q["out"] = buf[o: o + q["n"] * es].view(_DT_TORCH[dt])
     return buf
+
+
+class Server:
+    """Serving engine: a persistent worker kernel that requests join while it
+    runs (continuous batching).  Admission is by free slots, ring space and
+    output memory in the arena; submit returns None when the request must wait
+    (the caller keeps it queued and retries after releasing finished ones)."""
+
+    def __init__(self, streams: Streams, arena_bytes: int, max_slots: int = 4096,
+                 ring_tiles: int = 1 << 16, idle_seconds: float = 30.0, sm_fraction: float = 0.5):
+        self.streams = streams
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=streams.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(streams.device):
+            _check(lib.mrg_server_create(streams.ptr(), self.arena.data_ptr(), arena_bytes,
+                                         max_slots, ring_tiles, float(idle_seconds),
+                                         float(sm_fraction), ctypes.byref(h)))
+        self._h = h
+        self._ids = (ctypes.c_uint64 * max_slots)()
+        self._cap = max_slots
+
+    def submit(self, stream: int, n: int, dist="uniform", dtype="f64", substream: int = 0,
+               offset: int = 0, rate: float = 1.0):
+        """Returns (id, output tensor view in the arena) or None if busy."""
+        d = _DIST[dist] if isinstance(dist, str) else int(dist)
+        dt = "u32" if d == RAW else dtype
+        req = _Request(stream, substream, offset, n, d, _DT_CODE[dt], float(rate), None)
+        rid, out = ctypes.c_uint64(), ctypes.c_void_p()
+        rc = lib.mrg_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid), ctypes.byref(out))
+        if rc == EBUSY:
+            return None
+        _check(rc)
+        es = 8 if dt == "f64" else 4
+        off = out.value - self.arena.data_ptr()
+        return rid.value, self.arena[off: off + n * es].view(_DT_TORCH[dt])
+
+    def poll(self):
+        cnt = ctypes.c_uint32()
+        _check(lib.mrg_server_poll(self._h, self._ids, self._cap, ctypes.byref(cnt)))
+        return [self._ids[i] for i in range(cnt.value)]
+
+    def poll_status(self):
+        """(ids, status code) without raising."""
+        cnt = ctypes.c_uint32()
+        rc = lib.mrg_server_poll(self._h, self._ids, self._cap, ctypes.byref(cnt))
+        return [self._ids[i] for i in range(cnt.value)], rc
+
+    def release(self, rid: int):
+        _check(lib.mrg_server_release(self._h, rid))
+
+    def inflight(self) -> int:
+        return int(lib.mrg_server_inflight(self._h))
+
+    def restart(self):
+        _check(lib.mrg_server_restart(self._h))
+
+    def close(self):
+        if self._h:
+            rc = lib.mrg_server_destroy(self._h)
+            self._h = None
+            _check(rc)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
