@@ -253,12 +253,17 @@ typedef struct mrg_server mrg_server; /* opaque */
  * a persistent worker kernel that processes requests appended to a ring while
  * it runs.  sm_fraction in (0, 1] is the share of every SM's resident blocks
  * the worker takes: 1 gives it the whole GPU (kernels of other streams then
- * wait until the worker stops); smaller values leave room for them.  Outputs are placed in `arena` (caller-owned device memory,
- * 256-byte aligned, arena_bytes long).  max_slots bounds the requests in
- * flight, ring_tiles (a power of two) the tiles in flight (a request of n
- * draws takes about ceil(n / 65536) tiles).  The worker exits by itself after
+ * wait until the worker stops); smaller values leave room for them.  Outputs
+ * are placed in `arena` (caller-owned device memory, 256-byte aligned,
+ * arena_bytes long).  max_slots bounds the requests in flight, ring_tiles (a
+ * power of two) the tiles published and not yet finished (a request of n
+ * draws takes about min(8192, n / 1024) tiles of up to 32 segments).  The worker exits by itself after
  * idle_seconds with no published work (a host that stopped feeding it);
- * later calls then report MRG_ETIMEOUT until mrg_server_restart.
+ * later calls then report MRG_ETIMEOUT until mrg_server_restart.  While the
+ * worker runs, a device-wide synchronisation (cudaDeviceSynchronize) waits
+ * for it, and so can the first launch of a kernel that the process has not
+ * loaded yet (CUDA's lazy module loading): the library loads its own kernels
+ * at set-up; warm up other kernels first or set CUDA_MODULE_LOADING=EAGER.
  * Errors: MRG_EINVAL, MRG_ECUDA. */
 int mrg_server_create(const mrg_streams *s, void *arena, uint64_t arena_bytes,
                       uint32_t max_slots, uint64_t ring_tiles, double idle_seconds,
@@ -268,9 +273,12 @@ int mrg_server_create(const mrg_streams *s, void *arena, uint64_t arena_bytes,
  * in the arena and returns its device address in *out, may be NULL).  The
  * request is appended to the running worker at once; its output is that of
  * mrg_batch_run for the same request.  *id identifies it in poll/release.
- * Errors: MRG_EBUSY (no free slot, ring space or arena memory -- retry after
- * releasing finished requests), MRG_EINVAL, MRG_ERANGE (larger than the ring
- * or the arena), MRG_ETIMEOUT (the worker has stopped), MRG_ECUDA. */
+ * The request's tiles enter the worker's ring in chunks, round-robin with the
+ * other requests in flight, on this call and on every later submit and poll:
+ * keep polling while requests are in flight.
+ * Errors: MRG_EBUSY (no free slot or arena memory -- retry after releasing
+ * finished requests), MRG_EINVAL, MRG_ERANGE (larger than the arena),
+ * MRG_ETIMEOUT (the worker has stopped), MRG_ECUDA. */
 int mrg_server_submit(mrg_server *sv, const mrg_request *req, uint64_t *id, void **out);
 
 /* Writes up to max_ids ids of requests that finished since the last poll to

@@ -54,6 +54,8 @@ int ensure_device() {
   if (e != cudaSuccess) return fail_cuda(e, "uploading jump tables");
   e = mrg::upload_transform_table(&ttab[0][0], sizeof(ttab));
   if (e != cudaSuccess) return fail_cuda(e, "uploading transform tables");
+  e = mrg::preload_kernels();
+  if (e != cudaSuccess) return fail_cuda(e, "loading the library's kernels");
   ready[dev] = true;
   return MRG_OK;
 }

@@ -74,17 +74,22 @@ static_assert(sizeof(BatchTileHost) == 8, "tile record layout");
 
 // Serving engine (serve_kernels.cuh): control block and ring record mirrors.
 struct ServeCtlHost {
-  unsigned long long head, tail;
-  unsigned int stop, status;
+  alignas(128) unsigned long long head;
+  alignas(128) unsigned long long tail;
+  alignas(128) unsigned int stop;
+  alignas(128) unsigned int status;
 };
 struct ServeTileHost {
   uint32_t slot, g0, ntiles, seq;
 };
 static_assert(sizeof(ServeTileHost) == 16, "ring record layout");
 int serve_grid(double sm_fraction);
+// Loads every kernel of the library on the current device (see kernels.cu).
+cudaError_t preload_kernels();
 cudaError_t launch_serve(void* ctl, const void* slots, const void* ring, uint64_t ring_mask,
-                         unsigned int* tiles_done, unsigned int* done_words, const uint32_t* start,
-                         uint64_t stride, uint64_t idle_ns, int grid, cudaStream_t st);
+                         unsigned int* tiles_done, unsigned int* done_words,
+                         unsigned long long* head_mirror, const uint32_t* start, uint64_t stride,
+                         uint64_t idle_ns, int grid, cudaStream_t st);
 
 // Library set-up of the current device (jump and transform tables), and the
 // calling thread's error text; both implemented in capi.cu.

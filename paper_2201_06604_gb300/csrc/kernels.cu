@@ -537,6 +537,50 @@ cudaError_t launch_batch(void* hdr, const void* reqs, const void* tiles, const u
   return after_launch();
 }
 
+namespace {
+template <int DIST, int DT>
+void preload_gen(int& bad) {
+  cudaFuncAttributes a;
+  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 32>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 16>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 8>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 4>) != cudaSuccess;
+}
+template <int DIST, int DT>
+void preload_tr(int& bad) {
+  cudaFuncAttributes a;
+  bad |= cudaFuncGetAttributes(&a, transform_kernel<DIST, DT>) != cudaSuccess;
+}
+}  // namespace
+
+// Loads every kernel of the library now.  With CUDA's lazy module loading a
+// kernel is otherwise loaded at its first launch, and loading may have to
+// wait for kernels already running -- such as a serving worker that runs
+// until it is stopped.
+cudaError_t preload_kernels() {
+  int bad = 0;
+  cudaFuncAttributes a;
+  preload_gen<MRG_RAW, MRG_U32>(bad);
+  preload_gen<MRG_UNIFORM, MRG_F32>(bad);
+  preload_gen<MRG_UNIFORM, MRG_F64>(bad);
+  preload_gen<MRG_NORMAL, MRG_F32>(bad);
+  preload_gen<MRG_NORMAL, MRG_F64>(bad);
+  preload_gen<MRG_EXPONENTIAL, MRG_F32>(bad);
+  preload_gen<MRG_EXPONENTIAL, MRG_F64>(bad);
+  preload_tr<MRG_UNIFORM, MRG_F32>(bad);
+  preload_tr<MRG_UNIFORM, MRG_F64>(bad);
+  preload_tr<MRG_NORMAL, MRG_F32>(bad);
+  preload_tr<MRG_NORMAL, MRG_F64>(bad);
+  preload_tr<MRG_EXPONENTIAL, MRG_F32>(bad);
+  preload_tr<MRG_EXPONENTIAL, MRG_F64>(bad);
+  bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, batch_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, serve_kernel) != cudaSuccess;
+  return bad ? cudaErrorInvalidDeviceFunction : cudaSuccess;
+}
+
 int serve_grid(double sm_fraction) {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, serve_kernel, 256, 0);
@@ -545,12 +589,13 @@ int serve_grid(double sm_fraction) {
 }
 
 cudaError_t launch_serve(void* ctl, const void* slots, const void* ring, uint64_t ring_mask,
-                         unsigned int* tiles_done, unsigned int* done_words, const uint32_t* start,
-                         uint64_t stride, uint64_t idle_ns, int grid, cudaStream_t st) {
+                         unsigned int* tiles_done, unsigned int* done_words,
+                         unsigned long long* head_mirror, const uint32_t* start, uint64_t stride,
+                         uint64_t idle_ns, int grid, cudaStream_t st) {
   serve_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<ServeCtl*>(ctl),
                                      reinterpret_cast<const BatchReq*>(slots),
                                      reinterpret_cast<const ServeTile*>(ring), ring_mask, tiles_done,
-                                     done_words, start, stride, K1, K2, idle_ns);
+                                     done_words, head_mirror, start, stride, K1, K2, idle_ns);
   return after_launch();
 }
 

@@ -2,8 +2,9 @@
 // by kernels.cu).
 //
 // The host admits requests into slots (descriptor records in host-mapped
-// pinned memory), appends their tiles to a ring (also host-mapped) and
-// publishes the new ring tail with one small copy into device memory.  Warps
+// pinned memory), appends their tiles to a ring (also host-mapped) in chunks,
+// round-robin over the requests in flight, and publishes the new ring tail
+// with one small copy into device memory.  Warps
 // claim ring positions from a device counter; a warp whose position is not
 // published yet waits for it with a bounded, backed-off poll of the
 // device-side tail.  The warp that finishes the last tile of a request
@@ -21,11 +22,13 @@
 
 namespace mrg {
 
-struct ServeCtl {                 // device memory
-  unsigned long long head;        // claim counter (ring positions)
-  unsigned long long tail;        // published ring positions (host copies)
-  unsigned int stop;              // host: exit when no published work is left
-  unsigned int status;            // worker exit reason: 0 stop, 2 idle limit
+// Each word on its own 128-byte line: the claim counter's atomics and the
+// idle warps' polls of the tail do not contend for one L2 line.
+struct ServeCtl {                                 // device memory
+  alignas(128) unsigned long long head;           // claim counter (ring positions)
+  alignas(128) unsigned long long tail;           // published ring positions (host copies)
+  alignas(128) unsigned int stop;                 // host: exit when no published work is left
+  alignas(128) unsigned int status;               // worker exit reason: 0 stop, 2 idle limit
 };
 
 struct ServeTile {                // 16 bytes, in the host-mapped ring
@@ -57,6 +60,7 @@ __global__ void __launch_bounds__(256) serve_kernel(ServeCtl* ctl, const BatchRe
                                                     const ServeTile* ring, uint64_t ring_mask,
                                                     unsigned int* tiles_done,
                                                     unsigned int* done_words,
+                                                    unsigned long long* head_mirror,
                                                     const uint32_t* start, uint64_t stride,
                                                     uint64_t k1, uint64_t k2, uint64_t idle_ns) {
   __shared__ float4 s_tab[TAB_ENTRIES];
@@ -67,13 +71,17 @@ __global__ void __launch_bounds__(256) serve_kernel(ServeCtl* ctl, const BatchRe
     int go = 1;
     if (lane == 0) {
       t = atomicAdd(&ctl->head, 1ull);
+      // let the host see roughly how far the claims have got (it keeps the
+      // published backlog short so that new requests are not queued behind it)
+      if ((t & 31u) == 0)
+        asm volatile("st.relaxed.sys.global.u64 [%0], %1;" :: "l"(head_mirror), "l"(t) : "memory");
       uint64_t since = global_ns();
-      unsigned int backoff = 64;
+      unsigned int backoff = 128;
       while (ld_acquire_u64(&ctl->tail) <= t) {   // position not published yet
         if (ld_volatile_u32(&ctl->stop)) { go = 0; break; }
         if (global_ns() - since > idle_ns) { atomicMax(&ctl->status, 2u); go = 0; break; }
-        __nanosleep(backoff);
-        if (backoff < 8192) backoff <<= 1;
+        __nanosleep(backoff);                     // at most ~16 us between polls
+        if (backoff < 16384) backoff <<= 1;
       }
     }
     t = __shfl_sync(0xffffffffu, t, 0);
@@ -99,11 +107,11 @@ __global__ void __launch_bounds__(256) serve_kernel(ServeCtl* ctl, const BatchRe
     batch_tile(&R, &bt, 0, start, stride, k1, k2, s_tab);
     __syncwarp();
     if (lane == 0) {
-      __threadfence_system();  // this warp's outputs, visible system-wide, before the count
+      __threadfence();                 // this warp's outputs before its count
       const unsigned int k = atomicAdd(&tiles_done[T.slot], 1u) + 1u;
       if (k == T.ntiles) {
         tiles_done[T.slot] = 0u;       // the slot is reused only after the host sees completion
-        __threadfence_system();
+        __threadfence_system();        // cumulative: every tile counted above, system-wide
         asm volatile("st.release.sys.global.u32 [%0], %1;" :: "l"(done_words + T.slot), "r"(T.seq) : "memory");
       }
     }

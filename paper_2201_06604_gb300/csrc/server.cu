@@ -1,23 +1,30 @@
 // server.cu -- serving engine: continuous batching of generation requests
 // into one persistent worker kernel (serve_kernels.cuh).
 //
-// Admission is by slots, ring space and output memory: a request is admitted
-// only if a slot is free, its tiles fit in the ring and its output fits in
-// the caller's device arena (first fit); otherwise submit returns MRG_EBUSY
-// and the caller keeps it queued.  Admitted requests are appended to the ring
-// of the running worker, so they overlap on the device with requests already
-// in flight.  The client acknowledges a finished request with release, which
-// returns its slot and output memory.
+// Admission is by slots and output memory: a request is admitted only if a
+// slot is free and its output fits in the caller's device arena (first fit);
+// otherwise submit returns MRG_EBUSY and the caller keeps it queued.  The
+// tiles of admitted requests go to the ring of the running worker in chunks
+// of kChunk, round-robin over the requests in flight (pump), so a small
+// request that arrives behind a large one waits for at most one chunk per
+// request ahead of it instead of the large request's whole backlog; pump runs
+// on every submit and poll.  Requests overlap on the device with those
+// already in flight.  The client acknowledges a finished request with
+// release, which returns its slot and output memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
+#include <deque>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <set>
+#include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <time.h>
 
 #include "../../include/mrg32k3a.h"
 #include "internal.h"
@@ -39,6 +46,8 @@ struct mrg_server {
   void* ring_d = nullptr;
   unsigned int* done_d = nullptr;
   unsigned long long* tail_h = nullptr;    // pinned staging of the published tail
+  unsigned long long* head_h = nullptr;    // mapped: claim counter mirror (written by the worker)
+  unsigned long long* head_d = nullptr;
   unsigned int* stop_h = nullptr;
   // device memory
   mrg::ServeCtlHost* ctl_d = nullptr;
@@ -57,22 +66,36 @@ struct mrg_server {
     uint32_t slot;
     uint32_t seq;
     uint64_t mem_off, mem_size;
-    uint64_t ring_first;
+    uint64_t ntiles, emitted;
+    uint64_t ring_first;     // first ring position (valid once emitted > 0)
     bool done;
   };
   std::unordered_map<uint64_t, Inflight> inflight;  // id -> state
   std::multiset<uint64_t> ring_firsts;               // first ring positions of undone requests
+  std::deque<uint64_t> emit_queue;                   // ids with tiles still to emit
+  // feeder thread: keeps the ring's backlog topped up while tiles are pending
+  std::thread feeder;
+  std::atomic<bool> quit{false};
 };
 
 namespace {
 
 constexpr uint64_t kAlign = 256;
+constexpr uint64_t kChunk = 256;       // tiles of one request per round-robin turn
+constexpr uint64_t kBacklog = 8192;    // published tiles not yet claimed, at most (about one
+                                       // per resident warp of the whole GPU)
 
+// Segment length for latency.  A request that arrives while others occupy
+// the warps waits for about one tile's duration, which grows with the
+// segment length, so segments are short: n / 8192 draws, at least 32 (the
+// jump to a segment costs about as much as a few dozen draws), at most 128;
+// a large request is then many tiles that keep every warp busy, fed into the
+// ring a chunk at a time.
 uint32_t seg_len_for(uint64_t draws) {
-  uint64_t L = (draws + 31) / 32;
+  uint64_t L = (draws + 8191) / 8192;
   L = (L + 7) / 8 * 8;
-  if (L < 8) L = 8;
-  if (L > 2048) L = 2048;
+  if (L < 32) L = 32;
+  if (L > 128) L = 128;
   return (uint32_t)L;
 }
 
@@ -106,14 +129,55 @@ void arena_free(mrg_server* sv, uint64_t off, uint64_t size) {
   }
 }
 
+// Appends chunks of pending tiles to the ring, round-robin over requests,
+// while there is ring space, and publishes the new tail.
+int pump(mrg_server* sv) {
+  const uint64_t ring_low = sv->ring_firsts.empty() ? sv->tail : *sv->ring_firsts.begin();
+  uint64_t space = sv->ring_tiles - (sv->tail - ring_low);
+  const uint64_t claimed = *reinterpret_cast<volatile unsigned long long*>(sv->head_h);
+  const uint64_t backlog = sv->tail > claimed ? sv->tail - claimed : 0;
+  space = std::min<uint64_t>(space, backlog < kBacklog ? kBacklog - backlog : 0);
+  const uint64_t tail0 = sv->tail;
+  size_t turns = sv->emit_queue.size();
+  while (space > 0 && turns-- > 0) {
+    const uint64_t id = sv->emit_queue.front();
+    sv->emit_queue.pop_front();
+    auto& f = sv->inflight[id];
+    const uint64_t k = std::min<uint64_t>(std::min<uint64_t>(kChunk, f.ntiles - f.emitted), space);
+    if (f.emitted == 0) {
+      f.ring_first = sv->tail;
+      sv->ring_firsts.insert(sv->tail);
+    }
+    for (uint64_t i = 0; i < k; ++i)
+      sv->ring_h[(sv->tail + i) & (sv->ring_tiles - 1)] =
+          mrg::ServeTileHost{f.slot, (uint32_t)(32 * (f.emitted + i)), (uint32_t)f.ntiles, f.seq};
+    f.emitted += k;
+    sv->tail += k;
+    space -= k;
+    if (f.emitted < f.ntiles) sv->emit_queue.push_back(id);
+    if (turns == 0 && space > 0 && !sv->emit_queue.empty()) turns = sv->emit_queue.size();
+  }
+  if (sv->tail == tail0) return MRG_OK;
+  std::atomic_thread_fence(std::memory_order_seq_cst);  // records before the tail that covers them
+  *sv->tail_h = sv->tail;
+  cudaError_t e = cudaMemcpyAsync(&sv->ctl_d->tail, sv->tail_h, sizeof(unsigned long long),
+                                  cudaMemcpyHostToDevice, sv->copier);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  return MRG_OK;
+}
+
 int launch_worker(mrg_server* sv) {
-  mrg::ServeCtlHost c{sv->tail, sv->tail, 0u, 0u};  // resume claiming at the first unpublished position
+  mrg::ServeCtlHost c{};
+  c.head = sv->tail;  // resume claiming at the first unpublished position
+  c.tail = sv->tail;
+  *sv->head_h = sv->tail;
   *sv->stop_h = 0;
   cudaError_t e = cudaMemcpyAsync(sv->ctl_d, &c, sizeof c, cudaMemcpyHostToDevice, sv->worker);
   if (e == cudaSuccess) e = cudaStreamSynchronize(sv->worker);
   if (e == cudaSuccess)
     e = mrg::launch_serve(sv->ctl_d, sv->slots_d, sv->ring_d, sv->ring_tiles - 1, sv->tiles_done_d,
-                          sv->done_d, sv->s.start, sv->s.stride, sv->idle_ns, sv->grid, sv->worker);
+                          sv->done_d, sv->head_d, sv->s.start, sv->s.stride, sv->idle_ns, sv->grid,
+                          sv->worker);
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   sv->running = true;
   sv->failed = false;
@@ -136,8 +200,27 @@ int check_worker(mrg_server* sv) {
   return mrg::set_error(MRG_ETIMEOUT, "serving worker reached its idle limit and exited");
 }
 
+void feeder_main(mrg_server* sv) {
+  timespec ts{0, 2000};  // 2 us between rounds
+  while (!sv->quit.load(std::memory_order_relaxed)) {
+    bool pending;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (sv->running && !sv->emit_queue.empty()) pump(sv);
+      pending = !sv->emit_queue.empty();
+    }
+    if (!pending) ts.tv_nsec = 20000;   // idle: 20 us
+    else ts.tv_nsec = 2000;
+    nanosleep(&ts, nullptr);
+  }
+}
+
 void server_free(mrg_server* sv) {
   if (!sv) return;
+  if (sv->feeder.joinable()) {
+    sv->quit.store(true);
+    sv->feeder.join();
+  }
   if (sv->worker) cudaStreamDestroy(sv->worker);
   if (sv->copier) cudaStreamDestroy(sv->copier);
   cudaFree(sv->ctl_d);
@@ -147,6 +230,7 @@ void server_free(mrg_server* sv) {
   cudaFreeHost(sv->done_h);
   cudaFreeHost(sv->tail_h);
   cudaFreeHost(sv->stop_h);
+  cudaFreeHost(sv->head_h);
   delete sv;
 }
 
@@ -184,6 +268,8 @@ int mrg_server_create(const mrg_streams* s, void* arena, uint64_t arena_bytes, u
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->done_h, sizeof(unsigned int) * max_slots, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->tail_h, sizeof(unsigned long long), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->stop_h, sizeof(unsigned int), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->head_h, sizeof(unsigned long long), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->head_d, sv->head_h, 0);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->slots_d, sv->slots_h, 0);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->ring_d, sv->ring_h, 0);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->done_d, sv->done_h, 0);
@@ -204,6 +290,7 @@ int mrg_server_create(const mrg_streams* s, void* arena, uint64_t arena_bytes, u
     server_free(sv);
     return rc;
   }
+  sv->feeder = std::thread(feeder_main, sv);
   *out = sv;
   return MRG_OK;
 }
@@ -229,12 +316,10 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
   const uint64_t nseg = (q->n + L - 1) / L;
   const uint64_t ntiles = (nseg + 31) / 32;
   const uint64_t bytes = (q->n * (q->dtype == MRG_F64 ? 8 : 4) + kAlign - 1) / kAlign * kAlign;
-  if (ntiles > sv->ring_tiles || bytes > sv->arena_bytes || nseg > 0xFFFFFFFFull)
-    return mrg::set_error(MRG_ERANGE, "request larger than the server's ring or arena");
-  // admission: a slot, ring space, output memory
-  const uint64_t ring_low = sv->ring_firsts.empty() ? sv->tail : *sv->ring_firsts.begin();
-  if (sv->free_slots.empty() || sv->tail + ntiles - ring_low > sv->ring_tiles)
-    return mrg::set_error(MRG_EBUSY, "no free slot or ring space");
+  if (bytes > sv->arena_bytes || nseg > 0xFFFFFFFFull)
+    return mrg::set_error(MRG_ERANGE, "request larger than the server's arena");
+  // admission: a slot and output memory (tiles go to the ring in chunks)
+  if (sv->free_slots.empty()) return mrg::set_error(MRG_EBUSY, "no free slot");
   uint64_t off = 0;
   if (!arena_alloc(sv, bytes, &off)) return mrg::set_error(MRG_EBUSY, "output arena full");
   const uint32_t slot = sv->free_slots.back();
@@ -255,17 +340,10 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
   h.ir_lo = (float)(ir - (double)h.ir_hi);
   h.L = L;
   h.nseg = (uint32_t)nseg;
-  for (uint64_t k = 0; k < ntiles; ++k)
-    sv->ring_h[(sv->tail + k) & (sv->ring_tiles - 1)] =
-        mrg::ServeTileHost{slot, (uint32_t)(32 * k), (uint32_t)ntiles, seq};
-  sv->inflight[seq64] = mrg_server::Inflight{slot, seq, off, bytes, sv->tail, false};
-  sv->ring_firsts.insert(sv->tail);
-  sv->tail += ntiles;
-  std::atomic_thread_fence(std::memory_order_seq_cst);  // records before the tail that covers them
-  *sv->tail_h = sv->tail;
-  cudaError_t e = cudaMemcpyAsync(&sv->ctl_d->tail, sv->tail_h, sizeof(unsigned long long),
-                                  cudaMemcpyHostToDevice, sv->copier);
-  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  sv->inflight[seq64] = mrg_server::Inflight{slot, seq, off, bytes, ntiles, 0, 0, false};
+  sv->emit_queue.push_back(seq64);
+  rc = pump(sv);
+  if (rc) return rc;
   *id = seq64;
   if (out) *out = sv->arena + off;
   return MRG_OK;
@@ -285,6 +363,8 @@ int mrg_server_poll(mrg_server* sv, uint64_t* ids, uint32_t max_ids, uint32_t* c
     if (*count < max_ids) ids[(*count)++] = kv.first;
   }
   std::atomic_thread_fence(std::memory_order_acquire);
+  int rc = pump(sv);
+  if (rc) return rc;
   return check_worker(sv);
 }
 
@@ -327,6 +407,7 @@ int mrg_server_restart(mrg_server* sv) {
     }
   }
   sv->ring_firsts.clear();
+  sv->emit_queue.clear();
   e = cudaMemset(sv->tiles_done_d, 0, sizeof(unsigned int) * sv->max_slots);
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   return launch_worker(sv);
@@ -336,7 +417,15 @@ int mrg_server_destroy(mrg_server* sv) {
   if (!sv) return MRG_OK;
   int rc = MRG_OK;
   {
-    std::lock_guard<std::mutex> lk(sv->mu);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    // let the feeder publish every admitted tile first (bounded by the ring)
+    for (int spin = 0; sv->running && !sv->emit_queue.empty() && spin < 200000; ++spin) {
+      lk.unlock();
+      timespec ts{0, 10000};
+      nanosleep(&ts, nullptr);
+      lk.lock();
+      check_worker(sv);
+    }
     if (sv->running) {
       // stop only affects warps waiting for unpublished positions: every
       // published tile is still processed before the worker exits

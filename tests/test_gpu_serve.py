@@ -43,44 +43,58 @@ def mix(ns, count, seed, nmax=300000):
     return out
 
 
-def wait_all(sv, ids, timeout=30.0):
-    pending, done = set(ids), []
-    t0 = time.time()
-    while pending:
-        for i in sv.poll():
-            pending.discard(i)
-            done.append(i)
-        assert time.time() - t0 < timeout, f"{len(pending)} requests not finished"
-    return done
+class Client:
+    """Submits with retry (polling while the server is busy, since finished
+    requests free ring space only when they are polled) and remembers the
+    ids finished so far."""
 
+    def __init__(self, sv):
+        self.sv = sv
+        self.finished = set()
 
-def submit_all(sv, reqs, stagger=0.0):
-    got = []
-    for q in reqs:
-        r = None
-        while r is None:
-            r = sv.submit(q["stream"], q["n"], q["dist"], q["dtype"], q["substream"], q["offset"],
-                          q["rate"])
-        got.append(r)
-        if stagger:
-            time.sleep(stagger)
-    return got
+    def submit_all(self, reqs, stagger=0.0, timeout=30.0):
+        got = []
+        t0 = time.time()
+        for q in reqs:
+            r = None
+            while r is None:
+                r = self.sv.submit(q["stream"], q["n"], q["dist"], q["dtype"], q["substream"],
+                                   q["offset"], q["rate"])
+                if r is None:
+                    self.finished.update(self.sv.poll())
+                assert time.time() - t0 < timeout, "server stayed busy"
+            got.append(r)
+            if stagger:
+                time.sleep(stagger)
+        return got
+
+    def wait(self, ids, timeout=30.0):
+        pending = set(ids) - self.finished
+        t0 = time.time()
+        while pending:
+            done = self.sv.poll()
+            self.finished.update(done)
+            pending.difference_update(done)
+            assert time.time() - t0 < timeout, f"{len(pending)} requests not finished"
 
 
 def test_server_matches_batch_and_oracle(M):
     ns = 512
     s = M.create_streams(ns, seed=SEED)
     reqs = mix(ns, 60, seed=31)
-    sv = M.Server(s, 256 << 20, max_slots=64, ring_tiles=1 << 12)
-    got = submit_all(sv, reqs)
-    wait_all(sv, [i for i, _ in got])
     ref = [dict(q) for q in reqs]
     M.alloc_outputs(ref)
-    b = M.Batch(s, max_requests=64, max_tiles=1 << 12)
+    b = M.Batch(s, max_requests=64, max_tiles=1 << 12)   # allocate before the worker runs
+    sv = M.Server(s, 256 << 20, max_slots=64, ring_tiles=1 << 12)
+    c = Client(sv)
+    got = c.submit_all(reqs)
+    c.wait([i for i, _ in got])
     b.run(ref)
-    torch.cuda.synchronize()
+    # a device-wide synchronize would wait for the running worker: sync the
+    # stream, and compare on the host (no new device kernels while it runs)
+    torch.cuda.current_stream().synchronize()
     for (rid, out), r in zip(got, ref):
-        assert torch.equal(out, r["out"]), r
+        assert np.array_equal(out.cpu().numpy(), r["out"].cpu().numpy()), r
     # spot-check a uniform request against the oracle
     start, _ = O.create_streams(SEED, ns)
     for (rid, out), q in zip(got, reqs):
@@ -100,22 +114,23 @@ def test_alone_equals_mix(M):
     s = M.create_streams(ns, seed=(3, 1, 4, 1, 5, 9))
     reqs = mix(ns, 50, seed=32, nmax=2_000_000)
     sv = M.Server(s, 1 << 30, max_slots=64, ring_tiles=1 << 13)
-    got = submit_all(sv, reqs, stagger=0.0005)   # arrivals while earlier ones run
-    wait_all(sv, [i for i, _ in got])
-    mixed = [out.clone() for _, out in got]
+    c = Client(sv)
+    got = c.submit_all(reqs, stagger=0.0005)   # arrivals while earlier ones run
+    c.wait([i for i, _ in got])
+    mixed = [out.cpu() for _, out in got]
     for rid, _ in got:
         sv.release(rid)
     for q, m in list(zip(reqs, mixed))[::5]:
-        (rid, out), = submit_all(sv, [q])
-        wait_all(sv, [rid])
-        assert torch.equal(out, m), q
+        (rid, out), = c.submit_all([q])
+        c.wait([rid])
+        assert torch.equal(out.cpu(), m), q
         sv.release(rid)
     sv.close()
 
 
 def test_admission_by_memory_and_slots(M):
     s = M.create_streams(8, seed=SEED)
-    sv = M.Server(s, 1 << 20, max_slots=3, ring_tiles=64)   # 1 MiB arena
+    sv = M.Server(s, 1 << 20, max_slots=3, ring_tiles=256)  # 1 MiB arena
     a = sv.submit(0, 100_000, "uniform", "f64")            # 800 KB
     assert a is not None
     assert sv.submit(1, 100_000, "uniform", "f64") is None  # arena full
@@ -123,13 +138,14 @@ def test_admission_by_memory_and_slots(M):
     c = sv.submit(3, 1000, "uniform", "f32")
     assert b is not None and c is not None
     assert sv.submit(4, 8, "uniform", "f32") is None        # no free slot
-    wait_all(sv, [a[0], b[0], c[0]])
+    cl = Client(sv)
+    cl.wait([a[0], b[0], c[0]])
     with pytest.raises(M.MrgError):
         sv.release(12345678)
     sv.release(a[0])
     d = sv.submit(1, 100_000, "uniform", "f64")             # admitted after release
     assert d is not None
-    wait_all(sv, [d[0]])
+    cl.wait([d[0]])
     for r in (b, c, d):
         sv.release(r[0])
     assert sv.inflight() == 0
@@ -148,14 +164,14 @@ def test_worker_idle_limit_is_detected_and_restarts(M):
     sv.restart()
     r = sv.submit(0, 10, "uniform", "f64")
     assert r is not None
-    wait_all(sv, [r[0]], timeout=5.0)
+    Client(sv).wait([r[0]], timeout=5.0)
     sv.release(r[0])
     sv.close()
 
 
 def test_destroy_with_requests_in_flight(M):
     s = M.create_streams(64, seed=SEED)
-    sv = M.Server(s, 1 << 30, max_slots=16, ring_tiles=1 << 12)
+    sv = M.Server(s, 1 << 30, max_slots=16, ring_tiles=1 << 16)
     for k in range(8):
         assert sv.submit(k, 3_000_000, "normal", "f64") is not None
     sv.close()          # processes what was admitted, then stops
