@@ -375,6 +375,19 @@ def run_gpu(args):
             if events is not None:
                 events[i][1].record(stream)
 
+    # Autotune the generate kernel's launch shape for every variant of the
+    # workload (untimed; the library then launches each variant with the
+    # shape it recorded for this size class).
+    tuned = {}
+    if not args.no_tune:
+        create()
+        for d, dt in variants_run:
+            best, table = mrg.tune_generate(s, n, d, tdt[dt], out=outs[dt], reps=2)
+            default_ms = table[0][1]
+            best_ms = min(ms for _, ms in table)
+            tuned[f"{d}:{dt}"] = {"shape": best, "ms": best_ms, "default_ms": default_ms,
+                                  "candidates": len(table)}
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -522,6 +535,7 @@ def run_gpu(args):
         "gbs": bytes_step * world / (per_step_ms / 1e3) / 1e9,
         "roofline": roofline(dom, hbm, peak_kind, issue_peak, total_out),
         "variants": variants,
+        "tuned": tuned or None,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -543,6 +557,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="small shapes (development only)")
+    ap.add_argument("--no-tune", action="store_true", help="launch with the library defaults")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fused", action="store_true")

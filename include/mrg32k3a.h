@@ -180,6 +180,63 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- launch shape and its autotuner ------------------------------------ */
+
+/* Launch shape of the generate kernel.  It changes how the work is cut, never
+ * the output: every lane segment starts with a jump to its absolute offset
+ * in the stream (Sec. 2.1 jump-ahead), so any shape writes the same bytes. */
+typedef struct mrg_launch_config {
+    uint64_t seg_len;       /* draws per lane segment, rounded up to a multiple of 8
+                               and capped at the row; 0 = library heuristic */
+    uint32_t block;         /* threads per block: a multiple of 32, <= 256; 0 = 256 */
+    uint32_t vec_bytes;     /* widest per-lane store: 32, 16, 8 or 4 bytes; 0 = 32.  The
+                               alignment of out and of the row pitch may lower it */
+    uint32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (<= 64);
+                               0 = the occupancy maximum */
+    uint32_t reserved;      /* set to 0 */
+} mrg_launch_config;
+
+/* One timed candidate of the autotuner: its shape and the mean kernel time. */
+typedef struct mrg_tune_entry {
+    mrg_launch_config cfg;
+    float ms;
+} mrg_tune_entry;
+
+/* mrg_generate with an explicit launch shape (cfg, host, read during the
+ * call).  Same outputs and state updates as mrg_generate.  Errors: those of
+ * mrg_generate, and MRG_EINVAL for a cfg outside the ranges above. */
+int mrg_generate_config(const mrg_streams *s, uint64_t n, int dist, int dtype, double rate,
+                        void *out, uint64_t ld, const mrg_launch_config *cfg, void *stream);
+
+/* Autotuner: times the generate kernel for (s, n, dist, dtype, rate, out, ld)
+ * under the library default and a set of candidate shapes (segment lengths
+ * 256 .. 16384 draws x blocks of 128 / 256 threads x 32- / 16-byte stores),
+ * each warmed up once and then launched `reps` times (0 = 3, at most 100)
+ * between two CUDA events on `stream`.  Records the fastest for the current
+ * device and the size class (dist, dtype, bit length of s->n * n, bit length
+ * of n); later mrg_generate calls of that class launch with it.  The stream
+ * states are not advanced; out receives the values mrg_generate would write.
+ * results (host, may be NULL if max_results is 0) receives up to max_results
+ * timed candidates, *n_results their number, *best (may be NULL) the chosen
+ * shape.  Synchronises `stream`.  Not an optimisation the paper describes:
+ * its kernels have a fixed shape (Sec. 2.2).  Errors: as mrg_generate, and
+ * MRG_EINVAL for n or s->n equal to 0. */
+int mrg_tune_generate(const mrg_streams *s, uint64_t n, int dist, int dtype, double rate,
+                      void *out, uint64_t ld, uint32_t reps, mrg_tune_entry *results,
+                      uint32_t max_results, uint32_t *n_results, mrg_launch_config *best,
+                      void *stream);
+
+/* The shape mrg_generate uses on the current device for this size class
+ * (all fields 0 except block = 256 and vec_bytes = 32 when nothing is tuned). */
+int mrg_tune_lookup(int dist, int dtype, uint64_t n_streams, uint64_t n, mrg_launch_config *cfg);
+
+/* Records cfg for the size class on the current device (e.g. a shape saved
+ * from an earlier process); cfg = NULL removes the entry. */
+int mrg_tune_set(int dist, int dtype, uint64_t n_streams, uint64_t n, const mrg_launch_config *cfg);
+
+/* Forgets every tuned shape on every device. */
+void mrg_tune_clear(void);
+
 /* ---- batched requests (one persistent, graph-captured launch) ----------- */
 
 /* One generation request at an absolute position of one stream: draws start
@@ -201,6 +258,29 @@ typedef struct mrg_request {
     void *out;
 } mrg_request;
 
+/* How the batch runner and the serving engine cut requests into work: a
+ * request of n draws gets lane segments of
+ *   L = clamp(ceil(n / target_segments) rounded up to a multiple of 8,
+ *             seg_min, seg_max)
+ * draws, and 32 consecutive segments of one request form a warp tile.  Short
+ * segments spread a request over more lanes; long ones amortise the jump
+ * that starts every segment.  Outputs never depend on the tiling (every
+ * segment jumps to its absolute position).  Valid: 8 <= seg_min <= seg_max
+ * <= 2^20, both multiples of 8, target_segments >= 1. */
+typedef struct mrg_tiling {
+    uint32_t seg_min;
+    uint32_t seg_max;
+    uint64_t target_segments;
+} mrg_tiling;
+
+/* One timed tiling of mrg_batch_tune: the tiling, its tile count and the
+ * mean time of one batch launch. */
+typedef struct mrg_batch_tune_entry {
+    mrg_tiling tiling;
+    uint64_t tiles;
+    float ms;
+} mrg_batch_tune_entry;
+
 typedef struct mrg_batch mrg_batch; /* opaque */
 
 /* Creates a batch runner for the streams of `s` (their `start` arrays are
@@ -220,6 +300,29 @@ int mrg_batch_create(const mrg_streams *s, uint32_t max_requests, uint64_t max_t
  * unaligned out), MRG_ERANGE (substream >= 2^51, offset + draws > 2^62, more
  * requests or tiles than the batch holds), MRG_ECUDA. */
 int mrg_batch_run(mrg_batch *b, const mrg_request *reqs, uint32_t nreq, void *stream);
+
+/* Sets the tiling of later runs of this batch object (t = NULL restores the
+ * default {8, 2048, 32}: about one warp of segments per request, at most
+ * 2048 draws per lane).  Errors: MRG_EINVAL (tiling outside the ranges of
+ * mrg_tiling). */
+int mrg_batch_set_tiling(mrg_batch *b, const mrg_tiling *t);
+
+/* The tiling later runs of this batch object use. */
+int mrg_batch_get_tiling(const mrg_batch *b, mrg_tiling *t);
+
+/* Autotuner of the batch tiling: runs the nreq requests (they must be valid
+ * for mrg_batch_run, and their outputs are written) under the current
+ * tiling and a set of candidates (seg_min 8 / 64 x seg_max 512 / 2048 / 8192
+ * x target_segments 32 / 256 / 2048, skipping those whose tiles exceed the
+ * batch's capacity), each warmed up once and then launched `reps` times
+ * (0 = 3, at most 100) between CUDA events on `stream`, and keeps the
+ * fastest as the batch's tiling.  results (may be NULL if max_results is 0)
+ * receives up to max_results timed tilings, *n_results their number, *best
+ * (may be NULL) the chosen one.  Synchronises `stream`.  Not an optimisation
+ * the paper describes.  Errors: as mrg_batch_run. */
+int mrg_batch_tune(mrg_batch *b, const mrg_request *reqs, uint32_t nreq, uint32_t reps,
+                   mrg_batch_tune_entry *results, uint32_t max_results, uint32_t *n_results,
+                   mrg_tiling *best, void *stream);
 
 /* Number of tiles the last mrg_batch_run built. */
 uint64_t mrg_batch_last_tiles(const mrg_batch *b);
@@ -290,6 +393,11 @@ int mrg_server_poll(mrg_server *sv, uint64_t *ids, uint32_t max_ids, uint32_t *c
 /* The client's acknowledgement of a finished request: frees its slot and its
  * arena memory.  MRG_EBUSY if it has not finished, MRG_EINVAL if unknown. */
 int mrg_server_release(mrg_server *sv, uint64_t id);
+
+/* Sets the tiling of requests admitted from now on (t = NULL restores the
+ * default {32, 128, 8192}: short segments, so that a request that arrives
+ * while others run waits for about one short tile).  Errors: MRG_EINVAL. */
+int mrg_server_set_tiling(mrg_server *sv, const mrg_tiling *t);
 
 /* Requests admitted and not yet finished. */
 uint64_t mrg_server_inflight(mrg_server *sv);

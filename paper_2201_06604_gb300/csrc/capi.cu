@@ -130,7 +130,7 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
   int rc = ensure_device();
   if (rc) return rc;
-  mrg::GenConfig cfg;
+  const mrg::GenConfig cfg = mrg::generate_config_for(dist, dtype, s->n, n);
   cudaError_t e = mrg::launch_generate(dev(s), n, dist, dtype, rate, out, ld, cfg, cs(stream));
   if (e != cudaSuccess) return fail_cuda(e, "generate_kernel");
   const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
@@ -334,6 +334,7 @@ struct mrg_batch {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool ran = false;
+  mrg_tiling tiling{8, 2048, 32};
 };
 
 namespace {
@@ -352,14 +353,64 @@ void batch_free(mrg_batch* b) {
   delete b;
 }
 
-// Segment length of a request of `draws` draws: whole 32-byte units, about
-// draws / 32 so that short requests still fill a warp, at most 2048.
-uint32_t batch_seg_len(uint64_t draws) {
-  uint64_t L = (draws + 31) / 32;
-  L = (L + 7) / 8 * 8;
-  if (L < 8) L = 8;
-  if (L > 2048) L = 2048;
-  return (uint32_t)L;
+bool tiling_ok(const mrg_tiling& t) {
+  return t.seg_min >= 8 && t.seg_min % 8 == 0 && t.seg_max % 8 == 0 && t.seg_min <= t.seg_max &&
+         t.seg_max <= (1u << 20) && t.target_segments >= 1;
+}
+
+// Validates the requests and writes the host request and tile tables of `b`
+// under tiling `t`; *ntiles receives the tile count.
+int build_batch_tables(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, const mrg_tiling& t,
+                       uint64_t* ntiles) {
+  uint64_t nt = 0;
+  for (uint32_t r = 0; r < nreq; ++r) {
+    const mrg_request& q = reqs[r];
+    const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
+                         ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
+                           q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
+    if (!pair_ok) return fail(MRG_EINVAL, "request with unsupported dist/dtype");
+    if (q.stream >= b->s.n) return fail(MRG_EINVAL, "request stream index out of range");
+    if (q.substream >= (1ull << 51)) return fail(MRG_ERANGE, "substream index >= 2^51");
+    const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
+    if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
+      return fail(MRG_ERANGE, "offset + draws too large");
+    if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
+      return fail(MRG_EINVAL, "request output NULL or not 32-byte aligned");
+    if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
+      return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+    const uint32_t L = mrg::tiled_seg_len(q.n, t.seg_min, t.seg_max, t.target_segments);
+    const uint64_t nseg = (q.n + L - 1) / L;
+    if (nseg > 0xFFFFFFFFull) return fail(MRG_ERANGE, "request has more than 2^32 segments");
+    mrg::BatchReqHost& h = b->h_reqs[r];
+    h.out = reinterpret_cast<uint64_t>(q.out);
+    h.n = q.n;
+    h.off = q.offset;
+    h.sub = q.substream;
+    h.stream = q.stream;
+    h.dist = (uint32_t)q.dist;
+    h.dtype = (uint32_t)q.dtype;
+    const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
+    h.ir_hi = (float)ir;
+    h.ir_lo = (float)(ir - (double)h.ir_hi);
+    h.L = L;
+    h.nseg = (uint32_t)nseg;
+    const uint64_t tiles = (nseg + 31) / 32;
+    if (nt + tiles > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
+    for (uint64_t k = 0; k < tiles; ++k) b->h_tiles[nt + k] = mrg::BatchTileHost{r, (uint32_t)(32 * k)};
+    nt += tiles;
+  }
+  *ntiles = nt;
+  return MRG_OK;
+}
+
+// Tile count of the requests under tiling t (no table is written).
+uint64_t count_tiles(const mrg_request* reqs, uint32_t nreq, const mrg_tiling& t) {
+  uint64_t nt = 0;
+  for (uint32_t r = 0; r < nreq; ++r) {
+    const uint32_t L = mrg::tiled_seg_len(reqs[r].n, t.seg_min, t.seg_max, t.target_segments);
+    nt += ((reqs[r].n + L - 1) / L + 31) / 32;
+  }
+  return nt;
 }
 
 }  // namespace
@@ -428,39 +479,8 @@ int mrg_batch_run(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, void* st
     if (e != cudaSuccess) return fail_cuda(e, "waiting for the previous batch");
   }
   uint64_t nt = 0;
-  for (uint32_t r = 0; r < nreq; ++r) {
-    const mrg_request& q = reqs[r];
-    const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
-                         ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
-                           q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
-    if (!pair_ok) return fail(MRG_EINVAL, "request with unsupported dist/dtype");
-    if (q.stream >= b->s.n) return fail(MRG_EINVAL, "request stream index out of range");
-    if (q.substream >= (1ull << 51)) return fail(MRG_ERANGE, "substream index >= 2^51");
-    const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
-    if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
-      return fail(MRG_ERANGE, "offset + draws too large");
-    if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
-      return fail(MRG_EINVAL, "request output NULL or not 32-byte aligned");
-    if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
-      return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
-    mrg::BatchReqHost& h = b->h_reqs[r];
-    h.out = reinterpret_cast<uint64_t>(q.out);
-    h.n = q.n;
-    h.off = q.offset;
-    h.sub = q.substream;
-    h.stream = q.stream;
-    h.dist = (uint32_t)q.dist;
-    h.dtype = (uint32_t)q.dtype;
-    const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
-    h.ir_hi = (float)ir;
-    h.ir_lo = (float)(ir - (double)h.ir_hi);
-    h.L = batch_seg_len(q.n);
-    h.nseg = (uint32_t)((q.n + h.L - 1) / h.L);
-    const uint64_t tiles = (h.nseg + 31) / 32;
-    if (nt + tiles > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
-    for (uint64_t k = 0; k < tiles; ++k) b->h_tiles[nt + k] = mrg::BatchTileHost{r, (uint32_t)(32 * k)};
-    nt += tiles;
-  }
+  int rc = build_batch_tables(b, reqs, nreq, b->tiling, &nt);
+  if (rc) return rc;
   b->h_hdr->next_tile = 0;
   b->h_hdr->ntiles = nt;
   b->last_tiles = nt;
@@ -469,6 +489,91 @@ int mrg_batch_run(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, void* st
   if (e != cudaSuccess) return fail_cuda(e, "cudaGraphLaunch (batch)");
   mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
   b->ran = true;
+  return MRG_OK;
+}
+
+int mrg_batch_set_tiling(mrg_batch* b, const mrg_tiling* t) {
+  if (!b) return fail(MRG_EINVAL, "batch is NULL");
+  const mrg_tiling d{8, 2048, 32};
+  if (t && !tiling_ok(*t)) return fail(MRG_EINVAL, "tiling outside its ranges");
+  b->tiling = t ? *t : d;
+  return MRG_OK;
+}
+
+int mrg_batch_get_tiling(const mrg_batch* b, mrg_tiling* t) {
+  if (!b || !t) return fail(MRG_EINVAL, "NULL argument");
+  *t = b->tiling;
+  return MRG_OK;
+}
+
+int mrg_batch_tune(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, uint32_t reps,
+                   mrg_batch_tune_entry* results, uint32_t max_results, uint32_t* n_results,
+                   mrg_tiling* best, void* stream) {
+  if (n_results) *n_results = 0;
+  if (!b) return fail(MRG_EINVAL, "batch is NULL");
+  if (nreq == 0 || !reqs) return fail(MRG_EINVAL, "no requests to tune on");
+  if (max_results && !results) return fail(MRG_EINVAL, "results is NULL");
+  if (nreq > b->max_req) return fail(MRG_ERANGE, "more requests than the batch holds");
+  if (reps == 0) reps = 3;
+  if (reps > 100) reps = 100;
+  std::vector<mrg_tiling> cand{b->tiling};
+  for (uint32_t lo : {8u, 64u})
+    for (uint32_t hi : {512u, 2048u, 8192u})
+      for (uint64_t tg : {32ull, 256ull, 2048ull}) {
+        const mrg_tiling t{lo, hi, tg};
+        if (t.seg_min == b->tiling.seg_min && t.seg_max == b->tiling.seg_max &&
+            t.target_segments == b->tiling.target_segments)
+          continue;
+        if (count_tiles(reqs, nreq, t) <= b->max_tiles) cand.push_back(t);
+      }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail_cuda(e, "cudaEventCreate (batch tune)");
+  }
+  const mrg_tiling keep = b->tiling;
+  float best_ms = 0.0f;
+  size_t best_i = 0;
+  uint32_t nr = 0;
+  int rc = MRG_OK;
+  for (size_t i = 0; i < cand.size() && rc == MRG_OK; ++i) {
+    b->tiling = cand[i];
+    float ms = 0.0f;
+    rc = mrg_batch_run(b, reqs, nreq, stream);  // warm-up (and validation)
+    const uint64_t tiles = b->last_tiles;
+    if (rc == MRG_OK) {
+      // the graph reads the host tables when it runs: wait for the warm-up
+      // before timing replays of the same tables
+      e = cudaEventRecord(e0, cs(stream));
+      for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaGraphLaunch(b->exec, cs(stream));
+        if (e == cudaSuccess) mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, cs(stream));
+      if (e == cudaSuccess) e = cudaEventRecord(b->done, cs(stream));
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = fail_cuda(e, "timing a tiling (batch tune)");
+    }
+    if (rc != MRG_OK) break;
+    ms /= (float)reps;
+    if (nr < max_results) results[nr++] = mrg_batch_tune_entry{cand[i], tiles, ms};
+    if (i == 0 || ms < best_ms) {
+      best_ms = ms;
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MRG_OK) {
+    b->tiling = keep;
+    return rc;
+  }
+  b->tiling = cand[best_i];
+  if (best) *best = cand[best_i];
+  if (n_results) *n_results = nr;
   return MRG_OK;
 }
 

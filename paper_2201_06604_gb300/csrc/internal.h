@@ -21,7 +21,14 @@ struct GenConfig {
   uint64_t seg_len = 0;   // draws per segment (rounded up to a multiple of 8); 0 = heuristic
   int block = 256;        // threads per block (multiple of 32, <= 256)
   int max_blocks = 0;     // 0 = fill every SM
+  int vec_bytes = 32;     // widest per-lane store (32, 16, 8 or 4); alignment may lower it
+  int per_sm = 0;         // resident blocks per SM the grid is sized for; 0 = occupancy maximum
 };
+
+// The launch configuration mrg_generate uses for (dist, dtype) on ns streams
+// of n draws on the current device: a tuned one if the autotuner recorded
+// one for that size class, else the defaults above (tune.cu).
+GenConfig generate_config_for(int dist, int dtype, uint64_t ns, uint64_t n);
 
 extern std::atomic<uint64_t> g_launches;
 
@@ -95,6 +102,18 @@ cudaError_t launch_serve(void* ctl, const void* slots, const void* ring, uint64_
 // calling thread's error text; both implemented in capi.cu.
 int ensure_device_ready();
 int set_error(int code, const char* msg);
+
+// Segment length (draws per lane) of a request of `draws` draws under a
+// tiling: ceil(draws / target) rounded up to whole 32-byte units (8 values),
+// clamped to [seg_min, seg_max].
+inline uint32_t tiled_seg_len(uint64_t draws, uint32_t seg_min, uint32_t seg_max,
+                              uint64_t target) {
+  uint64_t L = (draws + target - 1) / target;
+  L = (L + 7) / 8 * 8;
+  if (L < seg_min) L = seg_min;
+  if (L > seg_max) L = seg_max;
+  return (uint32_t)L;
+}
 
 // Persistent grid size of the batch kernel on the current device.
 int batch_grid();

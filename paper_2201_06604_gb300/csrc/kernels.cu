@@ -445,7 +445,8 @@ cudaError_t launch_gen_t(const GenArgs& a, const GenConfig& cfg, cudaStream_t st
   const uint64_t ntiles = (a.total + 31) / 32;
   const uint64_t wpb = block / 32;
   uint64_t blocks = (ntiles + wpb - 1) / wpb;
-  uint64_t cap = (uint64_t)sm_count() * occ;
+  const int per_sm = cfg.per_sm > 0 ? std::min(cfg.per_sm, occ) : occ;
+  uint64_t cap = (uint64_t)sm_count() * per_sm;
   if (cfg.max_blocks > 0) cap = std::min<uint64_t>(cap, (uint64_t)cfg.max_blocks);
   blocks = std::max<uint64_t>(1, std::min(blocks, cap));
   kern<<<(unsigned)blocks, block, 0, st>>>(a);
@@ -501,7 +502,8 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
   }
   // widest store the row starts allow: out address and row pitch alignment
   const uint64_t align = (reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) & ~((reinterpret_cast<uintptr_t>(out) | (ld * es) | 32) - 1);
-  const int vb = (int)std::min<uint64_t>(align, 32);
+  const int vmax = (cfg.vec_bytes == 4 || cfg.vec_bytes == 8 || cfg.vec_bytes == 16) ? cfg.vec_bytes : 32;
+  const int vb = (int)std::min<uint64_t>(align, (uint64_t)vmax);
   switch (dist * 4 + dtype) {
     case MRG_RAW * 4 + MRG_U32: return launch_gen_dt<MRG_RAW, MRG_U32>(a, vb, cfg, st);
     case MRG_UNIFORM * 4 + MRG_F32: return launch_gen_dt<MRG_UNIFORM, MRG_F32>(a, vb, cfg, st);

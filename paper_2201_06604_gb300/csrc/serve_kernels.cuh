@@ -1,10 +1,12 @@
 // serve_kernels.cuh -- the persistent worker of the serving engine (included
 // by kernels.cu).
 //
-// The host admits requests into slots (descriptor records in host-mapped
-// pinned memory), appends their tiles to a ring (also host-mapped) in chunks,
+// The host admits requests into slots (descriptor records in device memory),
+// appends their tiles to a ring (also in device memory) in chunks,
 // round-robin over the requests in flight, and publishes the new ring tail
-// with one small copy into device memory.  Warps
+// with one small copy that follows the record copies on the same stream.
+// Records are read with volatile (L1-bypassing) loads, since a ring entry is
+// rewritten by the copy engine on every lap of the ring.  Warps
 // claim ring positions from a device counter; a warp whose position is not
 // published yet waits for it with a bounded, backed-off poll of the
 // device-side tail.  The warp that finishes the last tile of a request
@@ -31,7 +33,7 @@ struct ServeCtl {                                 // device memory
   alignas(128) unsigned int status;               // worker exit reason: 0 stop, 2 idle limit
 };
 
-struct ServeTile {                // 16 bytes, in the host-mapped ring
+struct ServeTile {                // 16 bytes, in the device-memory ring
   uint32_t slot;
   uint32_t g0;                    // first segment of the tile
   uint32_t ntiles;                // tiles of this request

@@ -3,7 +3,16 @@
 //
 // Admission is by slots and output memory: a request is admitted only if a
 // slot is free and its output fits in the caller's device arena (first fit);
-// otherwise submit returns MRG_EBUSY and the caller keeps it queued.  The
+// otherwise submit returns MRG_EBUSY and the caller keeps it queued.
+//
+// Request descriptors and ring records live in device memory.  The host
+// writes them into pinned staging arrays and copies them on its copy stream,
+// followed, in the same stream, by the new ring tail; the worker's warps read
+// the tail with an acquire load and the records with L1-bypassing loads.
+// (Host-mapped records read by the warps directly over the C2C link took
+// 0.1-0.4 ms per tile under load; device-memory reads take microseconds.)
+// Each tail publication copies from its own staging word, so a copy still
+// pending can never pick up a newer tail whose records are not copied yet.  The
 // tiles of admitted requests go to the ring of the running worker in chunks
 // of kChunk, round-robin over the requests in flight (pump), so a small
 // request that arrives behind a large one waits for at most one chunk per
@@ -38,14 +47,19 @@ struct mrg_server {
   uint64_t ring_tiles = 0;      // power of two
   uint64_t idle_ns = 0;
   int grid = 0;
-  // host-mapped pinned memory (written by the host, read by the worker)
+  // pinned host staging of the device-resident descriptors and ring
   mrg::BatchReqHost* slots_h = nullptr;
   mrg::ServeTileHost* ring_h = nullptr;
-  unsigned int* done_h = nullptr;          // written by the worker
-  void* slots_d = nullptr;
-  void* ring_d = nullptr;
+  mrg::BatchReqHost* slots_d = nullptr;     // device memory
+  mrg::ServeTileHost* ring_d = nullptr;     // device memory
+  // host-mapped pinned memory written by the worker
+  unsigned int* done_h = nullptr;
   unsigned int* done_d = nullptr;
-  unsigned long long* tail_h = nullptr;    // pinned staging of the published tail
+  // staging words of published tails, one per publication (round robin), and
+  // the event that marks each one's copy as done
+  unsigned long long* tail_h = nullptr;
+  cudaEvent_t tail_ev[256] = {};
+  uint64_t publications = 0;
   unsigned long long* head_h = nullptr;    // mapped: claim counter mirror (written by the worker)
   unsigned long long* head_d = nullptr;
   unsigned int* stop_h = nullptr;
@@ -76,28 +90,24 @@ struct mrg_server {
   // feeder thread: keeps the ring's backlog topped up while tiles are pending
   std::thread feeder;
   std::atomic<bool> quit{false};
+  mrg_tiling tiling{32, 128, 8192};
 };
 
 namespace {
 
 constexpr uint64_t kAlign = 256;
+constexpr unsigned kTailWords = 256;   // staging words of published tails (round robin)
 constexpr uint64_t kChunk = 256;       // tiles of one request per round-robin turn
 constexpr uint64_t kBacklog = 8192;    // published tiles not yet claimed, at most (about one
                                        // per resident warp of the whole GPU)
 
-// Segment length for latency.  A request that arrives while others occupy
+// Default tiling, for latency.  A request that arrives while others occupy
 // the warps waits for about one tile's duration, which grows with the
 // segment length, so segments are short: n / 8192 draws, at least 32 (the
 // jump to a segment costs about as much as a few dozen draws), at most 128;
 // a large request is then many tiles that keep every warp busy, fed into the
-// ring a chunk at a time.
-uint32_t seg_len_for(uint64_t draws) {
-  uint64_t L = (draws + 8191) / 8192;
-  L = (L + 7) / 8 * 8;
-  if (L < 32) L = 32;
-  if (L > 128) L = 128;
-  return (uint32_t)L;
-}
+// ring a chunk at a time.  mrg_server_set_tiling changes it.
+constexpr mrg_tiling kDefaultTiling{32, 128, 8192};
 
 bool arena_alloc(mrg_server* sv, uint64_t size, uint64_t* off) {
   for (auto it = sv->free_mem.begin(); it != sv->free_mem.end(); ++it) {
@@ -158,10 +168,26 @@ int pump(mrg_server* sv) {
     if (turns == 0 && space > 0 && !sv->emit_queue.empty()) turns = sv->emit_queue.size();
   }
   if (sv->tail == tail0) return MRG_OK;
-  std::atomic_thread_fence(std::memory_order_seq_cst);  // records before the tail that covers them
-  *sv->tail_h = sv->tail;
-  cudaError_t e = cudaMemcpyAsync(&sv->ctl_d->tail, sv->tail_h, sizeof(unsigned long long),
-                                  cudaMemcpyHostToDevice, sv->copier);
+  // records [tail0, tail) to the device ring (two copies if they wrap), then
+  // the tail, all on the copy stream (executed in this order)
+  const uint64_t mask = sv->ring_tiles - 1;
+  cudaError_t e = cudaSuccess;
+  for (uint64_t p = tail0; p < sv->tail && e == cudaSuccess;) {
+    const uint64_t i = p & mask;
+    const uint64_t k = std::min<uint64_t>(sv->tail - p, sv->ring_tiles - i);
+    e = cudaMemcpyAsync(sv->ring_d + i, sv->ring_h + i, k * sizeof(mrg::ServeTileHost),
+                        cudaMemcpyHostToDevice, sv->copier);
+    p += k;
+  }
+  const unsigned w = (unsigned)(sv->publications++ % kTailWords);
+  if (e == cudaSuccess && sv->publications > kTailWords)
+    e = cudaEventSynchronize(sv->tail_ev[w]);  // the copy that last used this word is done
+  if (e == cudaSuccess) {
+    sv->tail_h[w] = sv->tail;
+    e = cudaMemcpyAsync(&sv->ctl_d->tail, sv->tail_h + w, sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, sv->copier);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(sv->tail_ev[w], sv->copier);
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   return MRG_OK;
 }
@@ -223,7 +249,11 @@ void server_free(mrg_server* sv) {
   }
   if (sv->worker) cudaStreamDestroy(sv->worker);
   if (sv->copier) cudaStreamDestroy(sv->copier);
+  for (cudaEvent_t ev : sv->tail_ev)
+    if (ev) cudaEventDestroy(ev);
   cudaFree(sv->ctl_d);
+  cudaFree(sv->slots_d);
+  cudaFree(sv->ring_d);
   cudaFree(sv->tiles_done_d);
   cudaFreeHost(sv->slots_h);
   cudaFreeHost(sv->ring_h);
@@ -263,15 +293,17 @@ int mrg_server_create(const mrg_streams* s, void* arena, uint64_t arena_bytes, u
   sv->ring_tiles = ring_tiles;
   sv->idle_ns = (uint64_t)(idle_seconds * 1e9);
   sv->grid = mrg::serve_grid(sm_fraction);
-  cudaError_t e = cudaHostAlloc((void**)&sv->slots_h, sizeof(mrg::BatchReqHost) * max_slots, cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->ring_h, sizeof(mrg::ServeTileHost) * ring_tiles, cudaHostAllocMapped);
+  cudaError_t e = cudaHostAlloc((void**)&sv->slots_h, sizeof(mrg::BatchReqHost) * max_slots, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->ring_h, sizeof(mrg::ServeTileHost) * ring_tiles, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sv->slots_d, sizeof(mrg::BatchReqHost) * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sv->ring_d, sizeof(mrg::ServeTileHost) * ring_tiles);
+  for (unsigned k = 0; k < kTailWords && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&sv->tail_ev[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->done_h, sizeof(unsigned int) * max_slots, cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->tail_h, sizeof(unsigned long long), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->tail_h, sizeof(unsigned long long) * kTailWords, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->stop_h, sizeof(unsigned int), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->head_h, sizeof(unsigned long long), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->head_d, sv->head_h, 0);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->slots_d, sv->slots_h, 0);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sv->ring_d, sv->ring_h, 0);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->done_d, sv->done_h, 0);
   if (e == cudaSuccess) e = cudaMalloc((void**)&sv->ctl_d, sizeof(mrg::ServeCtlHost));
   if (e == cudaSuccess) e = cudaMalloc((void**)&sv->tiles_done_d, sizeof(unsigned int) * max_slots);
@@ -312,7 +344,8 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
     return mrg::set_error(MRG_ERANGE, "offset + draws too large");
   if (q->dist == MRG_EXPONENTIAL && !(q->rate >= 0x1p-64 && q->rate <= 0x1p64))
     return mrg::set_error(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
-  const uint32_t L = seg_len_for(q->n);
+  const uint32_t L = mrg::tiled_seg_len(q->n, sv->tiling.seg_min, sv->tiling.seg_max,
+                                        sv->tiling.target_segments);
   const uint64_t nseg = (q->n + L - 1) / L;
   const uint64_t ntiles = (nseg + 31) / 32;
   const uint64_t bytes = (q->n * (q->dtype == MRG_F64 ? 8 : 4) + kAlign - 1) / kAlign * kAlign;
@@ -340,6 +373,15 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
   h.ir_lo = (float)(ir - (double)h.ir_hi);
   h.L = L;
   h.nseg = (uint32_t)nseg;
+  // the descriptor reaches the device before any ring record that names it
+  // (same copy stream); its staging entry is rewritten only after the slot is
+  // released, long after this copy
+  cudaError_t e = cudaMemcpyAsync(sv->slots_d + slot, &h, sizeof h, cudaMemcpyHostToDevice, sv->copier);
+  if (e != cudaSuccess) {
+    sv->free_slots.push_back(slot);
+    arena_free(sv, off, bytes);
+    return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  }
   sv->inflight[seq64] = mrg_server::Inflight{slot, seq, off, bytes, ntiles, 0, 0, false};
   sv->emit_queue.push_back(seq64);
   rc = pump(sv);
@@ -377,6 +419,16 @@ int mrg_server_release(mrg_server* sv, uint64_t id) {
   sv->free_slots.push_back(it->second.slot);
   arena_free(sv, it->second.mem_off, it->second.mem_size);
   sv->inflight.erase(it);
+  return MRG_OK;
+}
+
+int mrg_server_set_tiling(mrg_server* sv, const mrg_tiling* t) {
+  if (!sv) return mrg::set_error(MRG_EINVAL, "server is NULL");
+  if (t && !(t->seg_min >= 8 && t->seg_min % 8 == 0 && t->seg_max % 8 == 0 &&
+             t->seg_min <= t->seg_max && t->seg_max <= (1u << 20) && t->target_segments >= 1))
+    return mrg::set_error(MRG_EINVAL, "tiling outside its ranges");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->tiling = t ? *t : kDefaultTiling;
   return MRG_OK;
 }
 

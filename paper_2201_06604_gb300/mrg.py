@@ -43,6 +43,41 @@ class _Request(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("rate", ctypes.c_double), ("out", ctypes.c_void_p)]
 
 
+class LaunchConfig(ctypes.Structure):
+    """Launch shape of the generate kernel (mrg_launch_config); 0 = default."""
+    _fields_ = [("seg_len", ctypes.c_uint64), ("block", ctypes.c_uint32),
+                ("vec_bytes", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"seg_len": int(self.seg_len), "block": int(self.block),
+                "vec_bytes": int(self.vec_bytes), "blocks_per_sm": int(self.blocks_per_sm)}
+
+
+class _TuneEntry(ctypes.Structure):
+    _fields_ = [("cfg", LaunchConfig), ("ms", ctypes.c_float)]
+
+
+class Tiling(ctypes.Structure):
+    """Request tiling of the batch runner and the serving engine (mrg_tiling)."""
+    _fields_ = [("seg_min", ctypes.c_uint32), ("seg_max", ctypes.c_uint32),
+                ("target_segments", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {"seg_min": int(self.seg_min), "seg_max": int(self.seg_max),
+                "target_segments": int(self.target_segments)}
+
+
+def _tiling(t) -> Tiling:
+    if isinstance(t, Tiling):
+        return t
+    return Tiling(int(t["seg_min"]), int(t["seg_max"]), int(t["target_segments"]))
+
+
+class _BatchTuneEntry(ctypes.Structure):
+    _fields_ = [("tiling", Tiling), ("tiles", ctypes.c_uint64), ("ms", ctypes.c_float)]
+
+
 class _Streams(ctypes.Structure):
     _fields_ = [("cur", ctypes.c_void_p), ("start", ctypes.c_void_p), ("sub", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("stride", ctypes.c_uint64)]
@@ -72,9 +107,24 @@ def _load():
         "mrg_get_state": ([sp, u32p, vp], i32),
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+        "mrg_generate_config": ([sp, u64, i32, i32, ctypes.c_double, vp, u64,
+                                 ctypes.POINTER(LaunchConfig), vp], i32),
+        "mrg_tune_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, ctypes.c_uint32,
+                               ctypes.POINTER(_TuneEntry), ctypes.c_uint32,
+                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(LaunchConfig), vp],
+                              i32),
+        "mrg_tune_lookup": ([i32, i32, u64, u64, ctypes.POINTER(LaunchConfig)], i32),
+        "mrg_tune_set": ([i32, i32, u64, u64, ctypes.POINTER(LaunchConfig)], i32),
+        "mrg_tune_clear": ([], None),
         "mrg_batch_create": ([sp, ctypes.c_uint32, u64, ctypes.POINTER(vp), vp], i32),
         "mrg_batch_run": ([vp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
         "mrg_batch_last_tiles": ([vp], u64),
+        "mrg_batch_set_tiling": ([vp, ctypes.POINTER(Tiling)], i32),
+        "mrg_batch_get_tiling": ([vp, ctypes.POINTER(Tiling)], i32),
+        "mrg_batch_tune": ([vp, ctypes.POINTER(_Request), ctypes.c_uint32, ctypes.c_uint32,
+                            ctypes.POINTER(_BatchTuneEntry), ctypes.c_uint32,
+                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(Tiling), vp], i32),
+        "mrg_server_set_tiling": ([vp, ctypes.POINTER(Tiling)], i32),
         "mrg_batch_destroy": ([vp], i32),
         "mrg_batch_run_static": ([sp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
         "mrg_server_create": ([sp, vp, u64, ctypes.c_uint32, u64, ctypes.c_double,
@@ -233,6 +283,78 @@ def generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64, rate
     return out
 
 
+def _gen_args(streams, n, dist, dtype, out):
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    dt = torch.int32 if d == RAW else dtype
+    code = _dtype_code(d, dt)
+    if out is None:
+        out = torch.empty((streams.n, n), dtype=dt, device=streams.device)
+    if out.dim() != 2 or out.shape[0] < streams.n or out.shape[1] < n or out.stride(1) != 1:
+        raise ValueError("out must be [>= n_streams, >= n] with unit column stride")
+    if out.dtype != dt:
+        raise ValueError(f"out dtype {out.dtype} != {dt}")
+    return d, code, out
+
+
+def _config(cfg) -> LaunchConfig:
+    if isinstance(cfg, LaunchConfig):
+        return cfg
+    c = LaunchConfig()
+    for k, v in dict(cfg).items():
+        setattr(c, k, int(v))
+    return c
+
+
+def generate_config(streams: Streams, n: int, cfg, dist="uniform", dtype=torch.float64,
+                    rate: float = 1.0, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """generate() with an explicit launch shape (dict or LaunchConfig with
+    seg_len, block, vec_bytes, blocks_per_sm); same output for any shape."""
+    d, code, out = _gen_args(streams, n, dist, dtype, out)
+    c = _config(cfg)
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_generate_config(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
+                                       out.stride(0), ctypes.byref(c), _stream_handle(stream)))
+    return out
+
+
+def tune_generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64,
+                  rate: float = 1.0, out: torch.Tensor | None = None, reps: int = 3,
+                  stream=None):
+    """Runs the library's autotuner for this generate call (states are not
+    advanced) and returns (best shape dict, [(shape dict, ms), ...])."""
+    d, code, out = _gen_args(streams, n, dist, dtype, out)
+    res = (_TuneEntry * 64)()
+    nres = ctypes.c_uint32()
+    best = LaunchConfig()
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_tune_generate(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
+                                     out.stride(0), reps, res, 64, ctypes.byref(nres),
+                                     ctypes.byref(best), _stream_handle(stream)))
+    return best.as_dict(), [(res[i].cfg.as_dict(), float(res[i].ms)) for i in range(nres.value)]
+
+
+def tune_lookup(dist, dtype, n_streams: int, n: int, device=None) -> dict:
+    """The launch shape generate() uses for this size class."""
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    c = LaunchConfig()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(lib.mrg_tune_lookup(d, _dtype_code(d, dtype), n_streams, n, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def tune_set(dist, dtype, n_streams: int, n: int, cfg, device=None):
+    """Records a launch shape for a size class (cfg=None removes it)."""
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    c = None if cfg is None else ctypes.byref(_config(cfg))
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(lib.mrg_tune_set(d, _dtype_code(d, dtype), n_streams, n, c))
+
+
+def tune_clear():
+    lib.mrg_tune_clear()
+
+
 def generate_host(streams: Streams, n: int, dist="uniform", dtype=torch.float64,
                   rate: float = 1.0, out: torch.Tensor | None = None,
                   scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -347,7 +469,8 @@ class Batch:
                                         _stream_handle(stream)))
         self._h = h
 
-    def run(self, requests, stream=None):
+    @staticmethod
+    def _requests(requests):
         arr = (_Request * max(len(requests), 1))()
         for i, q in enumerate(requests):
             d = _DIST[q["dist"]] if isinstance(q["dist"], str) else int(q["dist"])
@@ -355,8 +478,37 @@ class Batch:
             arr[i] = _Request(q["stream"], q.get("substream", 0), q.get("offset", 0), q["n"], d,
                               U32 if d == RAW else _DT_CODE[dt], float(q.get("rate", 1.0)),
                               q["out"].data_ptr() if q["n"] else None)
+        return arr
+
+    def run(self, requests, stream=None):
+        arr = self._requests(requests)
         with torch.cuda.device(self.streams.device):
             _check(lib.mrg_batch_run(self._h, arr, len(requests), _stream_handle(stream)))
+
+    def set_tiling(self, tiling=None):
+        """tiling: dict(seg_min, seg_max, target_segments) or None (default)."""
+        _check(lib.mrg_batch_set_tiling(self._h, None if tiling is None
+                                        else ctypes.byref(_tiling(tiling))))
+
+    def get_tiling(self) -> dict:
+        t = Tiling()
+        _check(lib.mrg_batch_get_tiling(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def tune(self, requests, reps: int = 3, stream=None):
+        """Runs the library's tiling autotuner on these requests (their
+        outputs are written) and keeps the fastest tiling; returns
+        (best tiling dict, [(tiling dict, tiles, ms), ...])."""
+        arr = self._requests(requests)
+        res = (_BatchTuneEntry * 64)()
+        nres = ctypes.c_uint32()
+        best = Tiling()
+        with torch.cuda.device(self.streams.device):
+            _check(lib.mrg_batch_tune(self._h, arr, len(requests), reps, res, 64,
+                                      ctypes.byref(nres), ctypes.byref(best),
+                                      _stream_handle(stream)))
+        return best.as_dict(), [(res[i].tiling.as_dict(), int(res[i].tiles), float(res[i].ms))
+                                for i in range(nres.value)]
 
     @property
     def last_tiles(self) -> int:
@@ -439,6 +591,11 @@ class Server:
 
     def release(self, rid: int):
         _check(lib.mrg_server_release(self._h, rid))
+
+    def set_tiling(self, tiling=None):
+        """Tiling of requests admitted from now on (None: the default)."""
+        _check(lib.mrg_server_set_tiling(self._h, None if tiling is None
+                                         else ctypes.byref(_tiling(tiling))))
 
     def inflight(self) -> int:
         return int(lib.mrg_server_inflight(self._h))

@@ -140,3 +140,72 @@ def test_batch_errors(M):
     b.run([dict(stream=1, n=8, dist="uniform", dtype="f64", out=out)])           # still usable
     torch.cuda.synchronize()
     b.close()
+
+
+TILINGS = [dict(seg_min=8, seg_max=8, target_segments=1),
+           dict(seg_min=8, seg_max=2048, target_segments=32),
+           dict(seg_min=64, seg_max=512, target_segments=2048),
+           dict(seg_min=8, seg_max=1 << 20, target_segments=1),
+           dict(seg_min=256, seg_max=8192, target_segments=7)]
+
+
+def test_every_tiling_writes_the_same_bytes(M):
+    ns = 50
+    s = M.create_streams(ns, seed=SEED)
+    reqs = make_requests(ns, 60, seed=21)
+    M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=64, max_tiles=1 << 14)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    assert b.get_tiling() == dict(seg_min=8, seg_max=2048, target_segments=32)
+    ref = [q["out"].clone() for q in reqs]
+    tiles = set()
+    for t in TILINGS:
+        b.set_tiling(t)
+        assert b.get_tiling() == t
+        again = [dict(q) for q in reqs]
+        M.alloc_outputs(again)
+        b.run(again)
+        torch.cuda.synchronize()
+        tiles.add(b.last_tiles)
+        for q, a in zip(again, ref):
+            assert torch.equal(q["out"], a), (t, q)
+    assert len(tiles) >= 3          # the tilings really cut the work differently
+    b.set_tiling(None)
+    assert b.get_tiling()["seg_max"] == 2048
+    for bad in (dict(seg_min=4, seg_max=64, target_segments=1),
+                dict(seg_min=64, seg_max=32, target_segments=1),
+                dict(seg_min=8, seg_max=100, target_segments=1),
+                dict(seg_min=8, seg_max=64, target_segments=0)):
+        with pytest.raises(M.MrgError):
+            b.set_tiling(bad)
+    b.close()
+
+
+def test_batch_tuner_keeps_the_fastest_tiling(M):
+    ns = 256
+    s = M.create_streams(ns, seed=SEED)
+    start, _ = O.create_streams(SEED, ns)
+    rng = np.random.default_rng(5)
+    reqs = [dict(stream=r, substream=1, offset=0, n=int(10 ** rng.uniform(2, 5)),
+                 dist=["uniform", "normal", "exponential"][r % 3], dtype=["f32", "f64"][r % 2],
+                 rate=1.0) for r in range(ns)]
+    M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=ns, max_tiles=1 << 15)
+    best, table = b.tune(reqs, reps=2)
+    torch.cuda.synchronize()
+    assert len(table) >= 5
+    assert table[0][0] == dict(seg_min=8, seg_max=2048, target_segments=32)   # current first
+    fastest = min(table, key=lambda e: e[2])
+    assert best == fastest[0] and b.get_tiling() == best
+    # outputs written by the tuner are the requests' outputs
+    for q in reqs[::17]:
+        check_close(q["out"].cpu().numpy(), oracle_request(start, q), q)
+    ref = [q["out"].clone() for q in reqs]
+    again = [dict(q) for q in reqs]
+    M.alloc_outputs(again)
+    b.run(again)
+    torch.cuda.synchronize()
+    for q, a in zip(again, ref):
+        assert torch.equal(q["out"], a)
+    b.close()

@@ -176,3 +176,26 @@ def test_destroy_with_requests_in_flight(M):
         assert sv.submit(k, 3_000_000, "normal", "f64") is not None
     sv.close()          # processes what was admitted, then stops
     torch.cuda.synchronize()
+
+
+def test_tiling_changes_no_output(M):
+    ns = 64
+    s = M.create_streams(ns, seed=SEED)
+    reqs = mix(ns, 24, seed=33, nmax=3_000_000)
+    sv = M.Server(s, 1 << 30, max_slots=64, ring_tiles=1 << 14)
+    c = Client(sv)
+    results = []
+    for t in (None, dict(seg_min=8, seg_max=8, target_segments=1),
+              dict(seg_min=256, seg_max=4096, target_segments=512)):
+        sv.set_tiling(t)
+        got = c.submit_all(reqs)
+        c.wait([i for i, _ in got])
+        results.append([out.cpu() for _, out in got])
+        for rid, _ in got:
+            sv.release(rid)
+    for other in results[1:]:
+        for a, b in zip(results[0], other):
+            assert torch.equal(a, b)
+    with pytest.raises(M.MrgError):
+        sv.set_tiling(dict(seg_min=8, seg_max=12, target_segments=1))
+    sv.close()
