@@ -186,7 +186,7 @@ def roofline(dom, hbm, peak_kind, issue_peak, total_out):
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs"}
 
 
-def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3):
+def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3, tune=True):
     """4096 requests, lengths log-uniform in [1e2, 1e6], mixed dist/dtype,
     request r on stream r, substream 1: one persistent graph-captured launch
     vs 4096 plain mrg_generate calls (each followed by its state advance)."""
@@ -202,12 +202,25 @@ def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3):
     b.run(reqs)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        b.run(reqs)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) / reps
+
+    prepared = b.prepare(reqs)   # requests marshalled once (a C caller has none of this)
+
+    def time_batch(r):
+        b.run(r)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    t_default = time_batch(prepared)
+    tiling, tiles_default = b.get_tiling(), b.last_tiles
+    if tune:
+        # the library's tiling autotuner on this request mix (untimed)
+        tiling, table = b.tune(prepared, reps=3)
+    t_batch = time_batch(prepared)
+    t_python = time_batch(reqs)  # the same runs with the request list marshalled every time
     # plain: position every stream at substream 1, then one call per request
     plain = [dict(q) for q in reqs]
     buf_p = mrg.alloc_outputs(plain, device=dev)
@@ -232,7 +245,9 @@ def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3):
     nbytes = sum(q["n"] * (8 if q["dtype"] == "f64" else 4) for q in reqs)
     res = {"workload": f"{nst} requests, n log-uniform [1e2, 1e6], mixed dist/dtype, "
                        "request r on stream r substream 1",
-           "draws": draws, "bytes": nbytes, "tiles": b.last_tiles,
+           "draws": draws, "bytes": nbytes, "tiles": b.last_tiles, "tiling": tiling,
+           "untuned_ms": t_default, "untuned_tiles": tiles_default,
+           "batched_ms_python_marshalling": t_python,
            "batched_ms": t_batch, "plain_ms": t_plain, "speedup": t_plain / t_batch,
            "batched_draws_per_s": draws / (t_batch / 1e3), "batched_gbs": nbytes / (t_batch / 1e3) / 1e9,
            "plain_launches": 2 * nst, "identical_output": bool(identical)}
@@ -507,7 +522,7 @@ def run_gpu(args):
     # batched uneven requests vs back-to-back plain launches at identical output
     batched = None
     if not args.skip_batched:
-        batched = run_batched(mrg, W, dev, stream, seed, quick=args.quick)
+        batched = run_batched(mrg, W, dev, stream, seed, quick=args.quick, tune=not args.no_tune)
 
     serving = None
     if not args.skip_serving:

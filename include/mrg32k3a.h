@@ -285,10 +285,12 @@ typedef struct mrg_batch mrg_batch; /* opaque */
 
 /* Creates a batch runner for the streams of `s` (their `start` arrays are
  * read; no state is written) holding up to max_requests requests and
- * max_tiles tiles (a tile = up to 32 segments of one request; a request of n
- * draws takes about ceil(n / 65536) tiles, at least one).  Allocates its
- * device tables and pinned host staging, and captures one CUDA graph
- * [tables host->device, claim counter reset, persistent kernel] on `stream`.
+ * max_tiles tiles (a tile = up to 32 segments of one request; under the
+ * default tiling a request of n draws takes about ceil(n / 8192) tiles, at
+ * least one).  Allocates its device tables and pinned host staging, and
+ * captures one CUDA graph [tables and claim counters host->device, then one
+ * persistent kernel per output variant, each a programmatic dependent of the
+ * previous one] on a stream of its own.
  * Errors: MRG_EINVAL, MRG_ECUDA. */
 int mrg_batch_create(const mrg_streams *s, uint32_t max_requests, uint64_t max_tiles,
                      mrg_batch **out, void *stream);
@@ -302,8 +304,8 @@ int mrg_batch_create(const mrg_streams *s, uint32_t max_requests, uint64_t max_t
 int mrg_batch_run(mrg_batch *b, const mrg_request *reqs, uint32_t nreq, void *stream);
 
 /* Sets the tiling of later runs of this batch object (t = NULL restores the
- * default {8, 2048, 32}: about one warp of segments per request, at most
- * 2048 draws per lane).  Errors: MRG_EINVAL (tiling outside the ranges of
+ * default {8, 256, 32}: about one warp of segments per request, at most
+ * 256 draws per lane, so that no tile outlasts the rest of the batch by much).  Errors: MRG_EINVAL (tiling outside the ranges of
  * mrg_tiling). */
 int mrg_batch_set_tiling(mrg_batch *b, const mrg_tiling *t);
 
@@ -312,8 +314,8 @@ int mrg_batch_get_tiling(const mrg_batch *b, mrg_tiling *t);
 
 /* Autotuner of the batch tiling: runs the nreq requests (they must be valid
  * for mrg_batch_run, and their outputs are written) under the current
- * tiling and a set of candidates (seg_min 8 / 64 x seg_max 512 / 2048 / 8192
- * x target_segments 32 / 256 / 2048, skipping those whose tiles exceed the
+ * tiling and a set of candidates (seg_min 8 / 64 x seg_max 128 / 256 / 512 /
+ * 2048 x target_segments 32 / 256 / 2048, skipping those whose tiles exceed the
  * batch's capacity), each warmed up once and then launched `reps` times
  * (0 = 3, at most 100) between CUDA events on `stream`, and keeps the
  * fastest as the batch's tiling.  results (may be NULL if max_results is 0)

@@ -59,16 +59,16 @@ __device__ __forceinline__ void batch_segment(TState& st, const BatchReq& R, uin
   }
 }
 
-// Processes tile t.  All 32 lanes of the warp call it.
-__device__ __forceinline__ void batch_tile(const BatchReq* __restrict__ reqs,
-                                           const BatchTile* __restrict__ tiles, uint64_t t,
-                                           const uint32_t* __restrict__ start, uint64_t stride,
-                                           uint64_t k1, uint64_t k2,
-                                           const float4* __restrict__ tab) {
+// One tile of request R of a known variant: segments g0 .. g0 + 31.  All 32
+// lanes of the warp call it.
+template <int DIST, int DT>
+__device__ __forceinline__ void batch_tile_v(const BatchReq& R, uint32_t g0,
+                                             const uint32_t* __restrict__ start, uint64_t stride,
+                                             uint64_t k1, uint64_t k2,
+                                             const float4* __restrict__ tab) {
+  constexpr int ES = DT == MRG_F64 ? 8 : 4;
   const int lane = threadIdx.x & 31;
-  const BatchTile T = tiles[t];
-  const BatchReq R = reqs[T.req];
-  const uint32_t g = T.g0 + lane;
+  const uint32_t g = g0 + lane;
   const bool valid = g < R.nseg;
   const uint64_t seg_off = (uint64_t)g * R.L;
   const uint32_t cnt = valid ? (uint32_t)min((uint64_t)R.L, R.n - seg_off) : 0u;
@@ -80,19 +80,32 @@ __device__ __forceinline__ void batch_tile(const BatchReq* __restrict__ reqs,
   jump_lanes(st0, R.off + (valid ? seg_off : 0), 0);
   TState st = to_offset(st0);
   const Consts c{k1, k2, R.ir_hi, R.ir_lo};
-  char* gdst = reinterpret_cast<char*>(R.out) + seg_off * (R.dtype == MRG_F64 ? 8 : 4);
+  char* gdst = reinterpret_cast<char*>(R.out) + seg_off * ES;
+  batch_segment<DIST, DT>(st, R, cnt, gdst, cmax, c, tab);
+}
+
+// Processes tile t of any variant (dispatch on the request's variant).  All
+// 32 lanes of the warp call it.
+__device__ __forceinline__ void batch_tile(const BatchReq* __restrict__ reqs,
+                                           const BatchTile* __restrict__ tiles, uint64_t t,
+                                           const uint32_t* __restrict__ start, uint64_t stride,
+                                           uint64_t k1, uint64_t k2,
+                                           const float4* __restrict__ tab) {
+  const BatchTile T = tiles[t];
+  const BatchReq R = reqs[T.req];
   switch (R.dist * 4 + R.dtype) {
-    case MRG_RAW * 4 + MRG_U32: batch_segment<MRG_RAW, MRG_U32>(st, R, cnt, gdst, cmax, c, tab); break;
-    case MRG_UNIFORM * 4 + MRG_F32: batch_segment<MRG_UNIFORM, MRG_F32>(st, R, cnt, gdst, cmax, c, tab); break;
-    case MRG_UNIFORM * 4 + MRG_F64: batch_segment<MRG_UNIFORM, MRG_F64>(st, R, cnt, gdst, cmax, c, tab); break;
-    case MRG_NORMAL * 4 + MRG_F32: batch_segment<MRG_NORMAL, MRG_F32>(st, R, cnt, gdst, cmax, c, tab); break;
-    case MRG_NORMAL * 4 + MRG_F64: batch_segment<MRG_NORMAL, MRG_F64>(st, R, cnt, gdst, cmax, c, tab); break;
-    case MRG_EXPONENTIAL * 4 + MRG_F32: batch_segment<MRG_EXPONENTIAL, MRG_F32>(st, R, cnt, gdst, cmax, c, tab); break;
-    default: batch_segment<MRG_EXPONENTIAL, MRG_F64>(st, R, cnt, gdst, cmax, c, tab); break;
+    case MRG_RAW * 4 + MRG_U32: batch_tile_v<MRG_RAW, MRG_U32>(R, T.g0, start, stride, k1, k2, tab); break;
+    case MRG_UNIFORM * 4 + MRG_F32: batch_tile_v<MRG_UNIFORM, MRG_F32>(R, T.g0, start, stride, k1, k2, tab); break;
+    case MRG_UNIFORM * 4 + MRG_F64: batch_tile_v<MRG_UNIFORM, MRG_F64>(R, T.g0, start, stride, k1, k2, tab); break;
+    case MRG_NORMAL * 4 + MRG_F32: batch_tile_v<MRG_NORMAL, MRG_F32>(R, T.g0, start, stride, k1, k2, tab); break;
+    case MRG_NORMAL * 4 + MRG_F64: batch_tile_v<MRG_NORMAL, MRG_F64>(R, T.g0, start, stride, k1, k2, tab); break;
+    case MRG_EXPONENTIAL * 4 + MRG_F32: batch_tile_v<MRG_EXPONENTIAL, MRG_F32>(R, T.g0, start, stride, k1, k2, tab); break;
+    default: batch_tile_v<MRG_EXPONENTIAL, MRG_F64>(R, T.g0, start, stride, k1, k2, tab); break;
   }
 }
 
-// Persistent worker: warps claim tiles until the table is exhausted.
+// Persistent worker over a table of mixed variants: warps claim tiles until
+// the table is exhausted.
 __global__ void __launch_bounds__(256) batch_kernel(BatchHeader* hdr, const BatchReq* reqs,
                                                     const BatchTile* tiles, const uint32_t* start,
                                                     uint64_t stride, uint64_t k1, uint64_t k2) {
@@ -106,6 +119,49 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchHeader* hdr, const Batc
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= ntiles) break;
     batch_tile(reqs, tiles, t, start, stride, k1, k2, s_tab);
+  }
+}
+
+// Range of one variant in a variant-grouped tile table (device-resident,
+// rewritten before every run).  Its claim counter lives apart, in a counter
+// array that the batch graph zeroes at the start of every replay.
+struct VariantRange {
+  uint64_t begin, end;  // tiles [begin, end) of the table
+};
+constexpr int kCounterStride = 16;  // counters 128 bytes apart (one L2 line each)
+
+// Persistent worker over the tiles of ONE variant (a range of a table grouped
+// by variant).  A batch launches one of these per variant, each a
+// programmatic dependent of the previous one: each kernel's code is one
+// transform path, so warps sharing an SM sub-partition do not evict each
+// other's instructions from its instruction cache, as the seven inlined paths
+// of batch_kernel do when variants mix on one SM (measured: instruction-fetch
+// stalls were the largest stall reason of the mixed kernel).
+template <int DIST, int DT>
+__global__ void __launch_bounds__(256) batch_variant_kernel(const VariantRange* rng,
+                                                            unsigned long long* next,
+                                                            const BatchReq* reqs,
+                                                            const BatchTile* tiles,
+                                                            const uint32_t* start, uint64_t stride,
+                                                            uint64_t k1, uint64_t k2) {
+  // The next variant's kernel is launched as a programmatic dependent: let it
+  // be scheduled as soon as every block of this grid is resident, so that its
+  // blocks take over SMs as this grid's blocks run out of tiles (the two
+  // kernels touch disjoint outputs and neither reads what the other writes).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr bool TABLES = DIST == MRG_NORMAL || DIST == MRG_EXPONENTIAL;
+  __shared__ float4 s_tab[TABLES ? TAB_ENTRIES : 1];
+  if constexpr (TABLES) load_ttab(s_tab);
+  const int lane = threadIdx.x & 31;
+  const uint64_t begin = rng->begin, end = rng->end;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = begin + atomicAdd(next, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= end) break;
+    const BatchTile T = tiles[t];
+    const BatchReq R = reqs[T.req];
+    batch_tile_v<DIST, DT>(R, T.g0, start, stride, k1, k2, s_tab);
   }
 }
 

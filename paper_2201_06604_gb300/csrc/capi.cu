@@ -317,24 +317,35 @@ int mrg_fused_pi_normsum(const mrg_streams* s, uint64_t draws, int64_t* count, d
 
 }  // extern "C"
 
+// Host staging of one run's tables (pinned).  A batch object has two, used in
+// turn, so that the tables of the next run are built while the GPU still
+// copies or runs the previous one.
+struct BatchStaging {
+  mrg::VariantRangeHost* ranges = nullptr;  // kVariants tile ranges
+  mrg::BatchReqHost* reqs = nullptr;
+  mrg::BatchTileHost* tiles = nullptr;
+  cudaEvent_t copied = nullptr;             // the copies out of this staging are done
+  bool used = false;
+};
+
 struct mrg_batch {
   int device = 0;
   mrg_streams s{};
   uint32_t max_req = 0;
   uint64_t max_tiles = 0;
   uint64_t last_tiles = 0;
-  int grid = 0;
-  void* d_hdr = nullptr;
+  void* d_ranges = nullptr;
+  unsigned long long* d_counters = nullptr;
   void* d_reqs = nullptr;
   void* d_tiles = nullptr;
-  mrg::BatchHeaderHost* h_hdr = nullptr;
-  mrg::BatchReqHost* h_reqs = nullptr;
-  mrg::BatchTileHost* h_tiles = nullptr;
+  BatchStaging stage[2];
+  int next_stage = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;               // end of the last run's kernels
   bool ran = false;
-  mrg_tiling tiling{8, 2048, 32};
+  mrg_tiling tiling{8, 256, 32};
+  std::vector<uint32_t> order;  // request order of the tile table (host scratch)
 };
 
 namespace {
@@ -344,12 +355,16 @@ void batch_free(mrg_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->done) cudaEventDestroy(b->done);
-  cudaFree(b->d_hdr);
+  cudaFree(b->d_ranges);
+  cudaFree(b->d_counters);
   cudaFree(b->d_reqs);
   cudaFree(b->d_tiles);
-  cudaFreeHost(b->h_hdr);
-  cudaFreeHost(b->h_reqs);
-  cudaFreeHost(b->h_tiles);
+  for (BatchStaging& st : b->stage) {
+    if (st.copied) cudaEventDestroy(st.copied);
+    cudaFreeHost(st.ranges);
+    cudaFreeHost(st.reqs);
+    cudaFreeHost(st.tiles);
+  }
   delete b;
 }
 
@@ -358,10 +373,10 @@ bool tiling_ok(const mrg_tiling& t) {
          t.seg_max <= (1u << 20) && t.target_segments >= 1;
 }
 
-// Validates the requests and writes the host request and tile tables of `b`
-// under tiling `t`; *ntiles receives the tile count.
-int build_batch_tables(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, const mrg_tiling& t,
-                       uint64_t* ntiles) {
+// Validates the requests and writes the request, tile and range tables of
+// one run into staging S under tiling `t`; *ntiles receives the tile count.
+int build_batch_tables(mrg_batch* b, BatchStaging& S, const mrg_request* reqs, uint32_t nreq,
+                       const mrg_tiling& t, uint64_t* ntiles) {
   uint64_t nt = 0;
   for (uint32_t r = 0; r < nreq; ++r) {
     const mrg_request& q = reqs[r];
@@ -381,7 +396,7 @@ int build_batch_tables(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, con
     const uint32_t L = mrg::tiled_seg_len(q.n, t.seg_min, t.seg_max, t.target_segments);
     const uint64_t nseg = (q.n + L - 1) / L;
     if (nseg > 0xFFFFFFFFull) return fail(MRG_ERANGE, "request has more than 2^32 segments");
-    mrg::BatchReqHost& h = b->h_reqs[r];
+    mrg::BatchReqHost& h = S.reqs[r];
     h.out = reinterpret_cast<uint64_t>(q.out);
     h.n = q.n;
     h.off = q.offset;
@@ -394,11 +409,33 @@ int build_batch_tables(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, con
     h.ir_lo = (float)(ir - (double)h.ir_hi);
     h.L = L;
     h.nseg = (uint32_t)nseg;
-    const uint64_t tiles = (nseg + 31) / 32;
-    if (nt + tiles > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
-    for (uint64_t k = 0; k < tiles; ++k) b->h_tiles[nt + k] = mrg::BatchTileHost{r, (uint32_t)(32 * k)};
-    nt += tiles;
+    nt += (nseg + 31) / 32;
+    if (nt > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
   }
+  // Tile order: grouped by output variant (one persistent kernel per variant
+  // runs its group), and within a variant by segment length, longest first,
+  // so that the last tiles claimed are the shortest (a short tail).
+  auto& order = b->order;
+  order.resize(nreq);
+  for (uint32_t r = 0; r < nreq; ++r) order[r] = r;
+  auto rank = [&](uint32_t r) { return mrg::kVariantRank[S.reqs[r].dist * 4 + S.reqs[r].dtype]; };
+  std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    const int rx = rank(x), ry = rank(y);
+    if (rx != ry) return rx < ry;
+    if (S.reqs[x].L != S.reqs[y].L) return S.reqs[x].L > S.reqs[y].L;
+    return x < y;
+  });
+  for (int v = 0; v < mrg::kVariants; ++v) S.ranges[v] = mrg::VariantRangeHost{0, 0};
+  uint64_t k = 0;
+  int v = 0;
+  for (uint32_t r : order) {
+    const int rv = rank(r);
+    for (; v < rv; ++v) S.ranges[v + 1].begin = S.ranges[v + 1].end = k;
+    const uint64_t tiles = (S.reqs[r].nseg + 31) / 32;
+    for (uint64_t j = 0; j < tiles; ++j) S.tiles[k++] = mrg::BatchTileHost{r, (uint32_t)(32 * j)};
+    S.ranges[rv].end = k;
+  }
+  for (; v + 1 < mrg::kVariants; ++v) S.ranges[v + 1].begin = S.ranges[v + 1].end = k;
   *ntiles = nt;
   return MRG_OK;
 }
@@ -431,30 +468,34 @@ int mrg_batch_create(const mrg_streams* s, uint32_t max_requests, uint64_t max_t
   b->s = *s;
   b->max_req = max_requests;
   b->max_tiles = max_tiles;
-  b->grid = mrg::batch_grid();
   const size_t rb = sizeof(mrg::BatchReqHost) * max_requests;
   const size_t tb = sizeof(mrg::BatchTileHost) * max_tiles;
-  const size_t hb = sizeof(mrg::BatchHeaderHost);
-  cudaError_t e = cudaMalloc(&b->d_hdr, hb);
+  const size_t hb = sizeof(mrg::VariantRangeHost) * mrg::kVariants;
+  const size_t cb = sizeof(unsigned long long) * mrg::kBatchCounterStride * mrg::kVariants;
+  cudaError_t e = cudaMalloc(&b->d_ranges, hb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counters, cb);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_reqs, rb);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, tb);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr, hb);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_reqs, rb);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_tiles, tb);
+  for (BatchStaging& st : b->stage) {
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&st.ranges, hb);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&st.reqs, rb);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&st.tiles, tb);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.copied, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     batch_free(b);
     return fail_cuda(e, "allocating batch tables");
   }
-  // Capture [tables -> device, kernel] once; replays read the staging buffers.
+  // Capture [claim counters = 0, one persistent kernel per variant] once.
+  // Each run copies its tables into the device tables before launching it.
   cudaStream_t cap = nullptr;
   e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr, hb, cudaMemcpyHostToDevice, cap);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_reqs, b->h_reqs, rb, cudaMemcpyHostToDevice, cap);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tiles, b->h_tiles, tb, cudaMemcpyHostToDevice, cap);
-  if (e == cudaSuccess)
-    e = mrg::launch_batch(b->d_hdr, b->d_reqs, b->d_tiles, s->start, s->stride, b->grid, cap);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, cb, cap);
+  for (int v = 0; v < mrg::kVariants && e == cudaSuccess; ++v)
+    e = mrg::launch_batch_variant(v, b->d_ranges, b->d_counters, b->d_reqs, b->d_tiles, s->start,
+                                  s->stride, cap);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cap, &g);
   if (e == cudaSuccess) e = e2;
@@ -474,27 +515,42 @@ int mrg_batch_run(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, void* st
   if (!b) return fail(MRG_EINVAL, "batch is NULL");
   if (nreq > 0 && !reqs) return fail(MRG_EINVAL, "reqs is NULL");
   if (nreq > b->max_req) return fail(MRG_ERANGE, "more requests than the batch holds");
-  if (b->ran) {
-    cudaError_t e = cudaEventSynchronize(b->done);
-    if (e != cudaSuccess) return fail_cuda(e, "waiting for the previous batch");
+  BatchStaging& S = b->stage[b->next_stage];
+  if (S.used) {  // the copies out of this staging (two runs ago) must be done
+    cudaError_t e = cudaEventSynchronize(S.copied);
+    if (e != cudaSuccess) return fail_cuda(e, "waiting for an earlier batch's table copies");
   }
   uint64_t nt = 0;
-  int rc = build_batch_tables(b, reqs, nreq, b->tiling, &nt);
+  int rc = build_batch_tables(b, S, reqs, nreq, b->tiling, &nt);
   if (rc) return rc;
-  b->h_hdr->next_tile = 0;
-  b->h_hdr->ntiles = nt;
+  cudaStream_t st = cs(stream);
+  cudaError_t e = cudaSuccess;
+  // the device tables are shared by all runs: the previous run's kernels
+  // must be done with them, whatever stream it ran on
+  if (b->ran) e = cudaStreamWaitEvent(st, b->done, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_ranges, S.ranges, sizeof(mrg::VariantRangeHost) * mrg::kVariants,
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nreq)
+    e = cudaMemcpyAsync(b->d_reqs, S.reqs, sizeof(mrg::BatchReqHost) * nreq, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nt)
+    e = cudaMemcpyAsync(b->d_tiles, S.tiles, sizeof(mrg::BatchTileHost) * nt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(S.copied, st);
+  if (e != cudaSuccess) return fail_cuda(e, "copying the batch tables");
+  S.used = true;
+  b->next_stage ^= 1;
   b->last_tiles = nt;
-  cudaError_t e = cudaGraphLaunch(b->exec, cs(stream));
-  if (e == cudaSuccess) e = cudaEventRecord(b->done, cs(stream));
+  e = cudaGraphLaunch(b->exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, st);
   if (e != cudaSuccess) return fail_cuda(e, "cudaGraphLaunch (batch)");
-  mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
+  mrg::g_launches.fetch_add(mrg::kVariants, std::memory_order_relaxed);
   b->ran = true;
   return MRG_OK;
 }
 
 int mrg_batch_set_tiling(mrg_batch* b, const mrg_tiling* t) {
   if (!b) return fail(MRG_EINVAL, "batch is NULL");
-  const mrg_tiling d{8, 2048, 32};
+  const mrg_tiling d{8, 256, 32};
   if (t && !tiling_ok(*t)) return fail(MRG_EINVAL, "tiling outside its ranges");
   b->tiling = t ? *t : d;
   return MRG_OK;
@@ -518,8 +574,9 @@ int mrg_batch_tune(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, uint32_
   if (reps > 100) reps = 100;
   std::vector<mrg_tiling> cand{b->tiling};
   for (uint32_t lo : {8u, 64u})
-    for (uint32_t hi : {512u, 2048u, 8192u})
+    for (uint32_t hi : {128u, 256u, 512u, 2048u})
       for (uint64_t tg : {32ull, 256ull, 2048ull}) {
+        if (lo > hi) continue;
         const mrg_tiling t{lo, hi, tg};
         if (t.seg_min == b->tiling.seg_min && t.seg_max == b->tiling.seg_max &&
             t.target_segments == b->tiling.target_segments)
@@ -544,12 +601,12 @@ int mrg_batch_tune(mrg_batch* b, const mrg_request* reqs, uint32_t nreq, uint32_
     rc = mrg_batch_run(b, reqs, nreq, stream);  // warm-up (and validation)
     const uint64_t tiles = b->last_tiles;
     if (rc == MRG_OK) {
-      // the graph reads the host tables when it runs: wait for the warm-up
-      // before timing replays of the same tables
+      // replays reuse the device tables the warm-up copied (the graph zeroes
+      // the claim counters itself)
       e = cudaEventRecord(e0, cs(stream));
       for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) {
         e = cudaGraphLaunch(b->exec, cs(stream));
-        if (e == cudaSuccess) mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (e == cudaSuccess) mrg::g_launches.fetch_add(mrg::kVariants, std::memory_order_relaxed);
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, cs(stream));
       if (e == cudaSuccess) e = cudaEventRecord(b->done, cs(stream));

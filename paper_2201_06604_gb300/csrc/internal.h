@@ -115,6 +115,30 @@ inline uint32_t tiled_seg_len(uint64_t draws, uint32_t seg_min, uint32_t seg_max
   return (uint32_t)L;
 }
 
+// Range of one variant in a variant-grouped tile table (device mirror:
+// VariantRange in batch_kernels.cuh), and the spacing of the per-variant
+// claim counters (in 8-byte words).
+struct VariantRangeHost {
+  uint64_t begin, end;
+};
+static_assert(sizeof(VariantRangeHost) == 16, "variant range layout");
+constexpr int kBatchCounterStride = 16;
+
+// Output variants in the order the batch runner groups and launches them
+// (by instruction count per output, costliest first):
+//   0 normal f64, 1 normal f32, 2 exponential f64, 3 exponential f32,
+//   4 uniform f32, 5 uniform f64, 6 raw u32.
+constexpr int kVariants = 7;
+// rank of dist * 4 + dtype in that order (9 = not a variant)
+constexpr int kVariantRank[16] = {6, 9, 9, 9,  9, 4, 5, 9,  9, 1, 0, 9,  9, 3, 2, 9};
+
+// One launch of the persistent kernel of variant k over its range of the
+// tile table (ranges: kVariants records; counters: kVariants claim counters
+// kBatchCounterStride words apart, zero before the launch).
+cudaError_t launch_batch_variant(int k, const void* ranges, unsigned long long* counters,
+                                 const void* reqs, const void* tiles, const uint32_t* start,
+                                 uint64_t stride, cudaStream_t st);
+
 // Persistent grid size of the batch kernel on the current device.
 int batch_grid();
 // One launch of the persistent batch kernel over the device tables.

@@ -540,6 +540,67 @@ cudaError_t launch_batch(void* hdr, const void* reqs, const void* tiles, const u
 }
 
 namespace {
+
+template <int DIST, int DT>
+cudaError_t launch_bv(const void* ranges, unsigned long long* counter, const void* reqs,
+                      const void* tiles, const uint32_t* start, uint64_t stride,
+                      bool programmatic, cudaStream_t st) {
+  auto kern = batch_variant_kernel<DIST, DT>;
+  static std::mutex mu;
+  static int grid[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int g;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (grid[dev & 63] == 0) {
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+      grid[dev & 63] = sm_count() * (occ > 0 ? occ : 1);
+    }
+    g = grid[dev & 63];
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = programmatic ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<const VariantRange*>(ranges),
+                                     counter, reinterpret_cast<const BatchReq*>(reqs),
+                                     reinterpret_cast<const BatchTile*>(tiles), start, stride,
+                                     (uint64_t)K1, (uint64_t)K2);
+  if (e != cudaSuccess) return e;
+  return after_launch();
+}
+
+}  // namespace
+
+cudaError_t launch_batch_variant(int k, const void* ranges, unsigned long long* counters,
+                                 const void* reqs, const void* tiles, const uint32_t* start,
+                                 uint64_t stride, cudaStream_t st) {
+  const void* r = reinterpret_cast<const char*>(ranges) + k * sizeof(VariantRange);
+  unsigned long long* c = counters + k * kCounterStride;
+  const bool p = k > 0;  // variants 1..6 follow the previous kernel programmatically
+  switch (k) {
+    case 0: return launch_bv<MRG_NORMAL, MRG_F64>(r, c, reqs, tiles, start, stride, p, st);
+    case 1: return launch_bv<MRG_NORMAL, MRG_F32>(r, c, reqs, tiles, start, stride, p, st);
+    case 2: return launch_bv<MRG_EXPONENTIAL, MRG_F64>(r, c, reqs, tiles, start, stride, p, st);
+    case 3: return launch_bv<MRG_EXPONENTIAL, MRG_F32>(r, c, reqs, tiles, start, stride, p, st);
+    case 4: return launch_bv<MRG_UNIFORM, MRG_F32>(r, c, reqs, tiles, start, stride, p, st);
+    case 5: return launch_bv<MRG_UNIFORM, MRG_F64>(r, c, reqs, tiles, start, stride, p, st);
+    case 6: return launch_bv<MRG_RAW, MRG_U32>(r, c, reqs, tiles, start, stride, p, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static_assert(sizeof(VariantRange) == sizeof(VariantRangeHost), "variant range layout");
+static_assert(kCounterStride == kBatchCounterStride, "claim counter spacing");
+
+namespace {
 template <int DIST, int DT>
 void preload_gen(int& bad) {
   cudaFuncAttributes a;
@@ -552,6 +613,7 @@ template <int DIST, int DT>
 void preload_tr(int& bad) {
   cudaFuncAttributes a;
   bad |= cudaFuncGetAttributes(&a, transform_kernel<DIST, DT>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<DIST, DT>) != cudaSuccess;
 }
 }  // namespace
 
@@ -575,6 +637,7 @@ cudaError_t preload_kernels() {
   preload_tr<MRG_NORMAL, MRG_F64>(bad);
   preload_tr<MRG_EXPONENTIAL, MRG_F32>(bad);
   preload_tr<MRG_EXPONENTIAL, MRG_F64>(bad);
+  bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<MRG_RAW, MRG_U32>) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;

@@ -452,6 +452,21 @@ _DT_CODE = {"u32": U32, "f32": F32, "f64": F64}
 _DT_TORCH = {"u32": torch.int32, "f32": torch.float32, "f64": torch.float64}
 
 
+class PreparedRequests:
+    """A request list marshalled into C request records (see Batch)."""
+
+    def __init__(self, requests):
+        self.n = len(requests)
+        self.arr = (_Request * max(self.n, 1))()
+        for i, q in enumerate(requests):
+            d = _DIST[q["dist"]] if isinstance(q["dist"], str) else int(q["dist"])
+            dt = q.get("dtype", "f64")
+            self.arr[i] = _Request(q["stream"], q.get("substream", 0), q.get("offset", 0), q["n"], d,
+                                   U32 if d == RAW else _DT_CODE[dt], float(q.get("rate", 1.0)),
+                                   q["out"].data_ptr() if q["n"] else None)
+        self._keep = [q["out"] for q in requests if q["n"]]   # outputs stay alive
+
+
 class Batch:
     """Runner of batched requests over a stream set: one persistent,
     graph-captured kernel launch per run.  A request is a dict with keys
@@ -470,20 +485,23 @@ class Batch:
         self._h = h
 
     @staticmethod
+    def prepare(requests) -> "PreparedRequests":
+        """Marshals a request list once into the C request records, for
+        callers that run the same requests repeatedly (run() accepts the
+        result in place of the list)."""
+        return PreparedRequests(requests)
+
+    @staticmethod
     def _requests(requests):
-        arr = (_Request * max(len(requests), 1))()
-        for i, q in enumerate(requests):
-            d = _DIST[q["dist"]] if isinstance(q["dist"], str) else int(q["dist"])
-            dt = q.get("dtype", "f64")
-            arr[i] = _Request(q["stream"], q.get("substream", 0), q.get("offset", 0), q["n"], d,
-                              U32 if d == RAW else _DT_CODE[dt], float(q.get("rate", 1.0)),
-                              q["out"].data_ptr() if q["n"] else None)
-        return arr
+        if isinstance(requests, PreparedRequests):
+            return requests.arr, requests.n
+        p = PreparedRequests(requests)
+        return p.arr, p.n
 
     def run(self, requests, stream=None):
-        arr = self._requests(requests)
+        arr, n = self._requests(requests)
         with torch.cuda.device(self.streams.device):
-            _check(lib.mrg_batch_run(self._h, arr, len(requests), _stream_handle(stream)))
+            _check(lib.mrg_batch_run(self._h, arr, n, _stream_handle(stream)))
 
     def set_tiling(self, tiling=None):
         """tiling: dict(seg_min, seg_max, target_segments) or None (default)."""
@@ -499,12 +517,12 @@ class Batch:
         """Runs the library's tiling autotuner on these requests (their
         outputs are written) and keeps the fastest tiling; returns
         (best tiling dict, [(tiling dict, tiles, ms), ...])."""
-        arr = self._requests(requests)
+        arr, n = self._requests(requests)
         res = (_BatchTuneEntry * 64)()
         nres = ctypes.c_uint32()
         best = Tiling()
         with torch.cuda.device(self.streams.device):
-            _check(lib.mrg_batch_tune(self._h, arr, len(requests), reps, res, 64,
+            _check(lib.mrg_batch_tune(self._h, arr, n, reps, res, 64,
                                       ctypes.byref(nres), ctypes.byref(best),
                                       _stream_handle(stream)))
         return best.as_dict(), [(res[i].tiling.as_dict(), int(res[i].tiles), float(res[i].ms))

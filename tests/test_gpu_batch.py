@@ -157,7 +157,7 @@ def test_every_tiling_writes_the_same_bytes(M):
     b = M.Batch(s, max_requests=64, max_tiles=1 << 14)
     b.run(reqs)
     torch.cuda.synchronize()
-    assert b.get_tiling() == dict(seg_min=8, seg_max=2048, target_segments=32)
+    assert b.get_tiling() == dict(seg_min=8, seg_max=256, target_segments=32)
     ref = [q["out"].clone() for q in reqs]
     tiles = set()
     for t in TILINGS:
@@ -172,7 +172,7 @@ def test_every_tiling_writes_the_same_bytes(M):
             assert torch.equal(q["out"], a), (t, q)
     assert len(tiles) >= 3          # the tilings really cut the work differently
     b.set_tiling(None)
-    assert b.get_tiling()["seg_max"] == 2048
+    assert b.get_tiling()["seg_max"] == 256
     for bad in (dict(seg_min=4, seg_max=64, target_segments=1),
                 dict(seg_min=64, seg_max=32, target_segments=1),
                 dict(seg_min=8, seg_max=100, target_segments=1),
@@ -195,7 +195,7 @@ def test_batch_tuner_keeps_the_fastest_tiling(M):
     best, table = b.tune(reqs, reps=2)
     torch.cuda.synchronize()
     assert len(table) >= 5
-    assert table[0][0] == dict(seg_min=8, seg_max=2048, target_segments=32)   # current first
+    assert table[0][0] == dict(seg_min=8, seg_max=256, target_segments=32)    # current first
     fastest = min(table, key=lambda e: e[2])
     assert best == fastest[0] and b.get_tiling() == best
     # outputs written by the tuner are the requests' outputs
@@ -208,4 +208,32 @@ def test_batch_tuner_keeps_the_fastest_tiling(M):
     torch.cuda.synchronize()
     for q, a in zip(again, ref):
         assert torch.equal(q["out"], a)
+    b.close()
+
+
+def test_back_to_back_runs_without_sync(M):
+    """Runs issued back to back (host tables double-buffered, device tables
+    shared) on one stream and then alternating between two streams give the
+    same outputs as runs issued one at a time."""
+    ns = 128
+    s = M.create_streams(ns, seed=SEED)
+    sets = [make_requests(ns, 50, seed=40 + k, nmax=200000) for k in range(4)]
+    b = M.Batch(s, max_requests=64, max_tiles=1 << 14)
+    refs = []
+    for reqs in sets:
+        M.alloc_outputs(reqs)
+        b.run(reqs)
+        torch.cuda.synchronize()
+        refs.append([q["out"].clone() for q in reqs])
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    for mode in ("one stream", "two streams"):
+        again = [[dict(q) for q in reqs] for reqs in sets]
+        for k, reqs in enumerate(again):
+            M.alloc_outputs(reqs)
+            st = streams[k % 2] if mode == "two streams" else streams[0]
+            b.run(M.Batch.prepare(reqs) if k % 2 else reqs, stream=st)
+        torch.cuda.synchronize()
+        for reqs, ref in zip(again, refs):
+            for q, a in zip(reqs, ref):
+                assert torch.equal(q["out"], a), (mode, q)
     b.close()
