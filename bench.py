@@ -519,6 +519,25 @@ def run_gpu(args):
                  "pi_estimate": 4.0 * cnt.sum().item() / pairs}
         del f_st, cnt, sm_
 
+    # the paper's own generator (MRG31k3p) on the same materialised shape
+    g31 = None
+    if not args.skip_mrg31k3p:
+        s31 = mrg.create_streams(ns, device=dev, seed=tuple(W.PAPER_SEED), generator="mrg31k3p")
+        g31 = {"workload": f"{ns} streams x {n} draws, MRG31k3p (streams 2^134 apart)"}
+        for d, dt in (("uniform", "f64"), ("normal", "f64"), ("uniform", "f32")):
+            mrg.generate(s31, n, d, tdt[dt], out=outs[dt])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                mrg.generate(s31, n, d, tdt[dt], out=outs[dt])
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 3
+            g31[f"{d}:{dt}"] = {"ms": t, "draws_per_s": total_out / (t / 1e3),
+                                "gbs": total_out * ES[dt] / (t / 1e3) / 1e9}
+        del s31
+
     # batched uneven requests vs back-to-back plain launches at identical output
     batched = None
     if not args.skip_batched:
@@ -555,6 +574,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "fused": fused,
+        "mrg31k3p": g31,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
@@ -577,6 +597,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-mrg31k3p", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")

@@ -180,6 +180,39 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- MRG31k3p, the paper's own generator --------------------------------
+ * The package of the paper is built on MRG31k3p (L'Ecuyer and Touzin 2000;
+ * Sec. 2): x1[n] = (2^22 x1[n-2] + (2^7 + 1) x1[n-3]) mod (2^31 - 1),
+ * x2[n] = (2^15 x2[n-1] + (2^15 + 1) x2[n-3]) mod (2^31 - 21069),
+ * z = (x1 - x2) mod (2^31 - 1) with 0 mapped to 2^31 - 1 (an integer in
+ * [1, 2^31 - 1], Sec. 2.2), uniforms u = z / 2^31 (exact in fp64; fp32 =
+ * RN32(u)), streams 2^134 steps apart (Sec. 2.1).  Its streams use the same
+ * mrg_streams layout and word order as MRG32k3a's; the paper prints this
+ * generator's stream starts (Sec. 2.1), uniforms (Sec. 2.2) and
+ * exponentials (Sec. 3.2).  mrg_get_state, mrg_set_state, mrg_reset_stream
+ * and mrg_reset_substream serve both generators (they copy words); the other
+ * MRG32k3a entry points apply MRG32k3a's matrices and must not be given
+ * MRG31k3p streams.  */
+
+/* x1 words < 2^31 - 1, x2 words < 2^31 - 21069, neither triple all zero. */
+int mrg31k3p_seed_check(const uint32_t seed[6]);
+
+/* mrg_create_streams for MRG31k3p: stream i starts i * 2^134 steps after
+ * seed (Sec. 2.1, createStreamsGpu); next_seed (may be NULL) receives the
+ * creator state after n streams.  Errors: as mrg_create_streams. */
+int mrg31k3p_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams *s,
+                            uint32_t next_seed[6], void *stream);
+
+/* mrg_generate for MRG31k3p streams (Sec. 2.2 runifGpu, Sec. 3.1 rnormGpu,
+ * Sec. 3.2 rexpGpu): the same layout, variants, draw accounting and state
+ * advance; normals and exponentials are the transforms of u = z / 2^31 with
+ * the accuracy stated for mrg_generate.  Errors: as mrg_generate. */
+int mrg31k3p_generate(const mrg_streams *s, uint64_t n_per_stream, int dist, int dtype,
+                      double rate, void *out, uint64_t ld, void *stream);
+
+/* Advances every MRG31k3p stream's cur by k < 2^64 steps. */
+int mrg31k3p_skip(const mrg_streams *s, uint64_t k, void *stream);
+
 /* ---- launch shape and its autotuner ------------------------------------ */
 
 /* Launch shape of the generate kernel.  It changes how the work is cut, never

@@ -36,6 +36,8 @@ int ensure_device() {
   static bool ready[64] = {};
   static uint32_t tab[2][mrg::host::kJumpBits][9];
   static float ttab[mrg::host::kTransformEntries][4];
+  static uint32_t tab31[2][mrg::host::g31::kJumpBits][9];
+  static float ttab31[mrg::host::kTransformEntries][4];
   static bool tab_built = false;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -48,12 +50,17 @@ int ensure_device() {
       return fail(MRG_ECUDA, "RN64(1/(m1+1)) does not match the kernels' constant");
     mrg::host::jump_table_u32(tab);
     mrg::host::transform_table(ttab);
+    mrg::host::g31::jump_table_u32(tab31);
+    mrg::host::transform_table_m32(ttab31);
     tab_built = true;
   }
   e = mrg::upload_tables(&tab[0][0][0], sizeof(tab));
   if (e != cudaSuccess) return fail_cuda(e, "uploading jump tables");
   e = mrg::upload_transform_table(&ttab[0][0], sizeof(ttab));
   if (e != cudaSuccess) return fail_cuda(e, "uploading transform tables");
+  e = mrg::upload_tables31(&tab31[0][0][0], sizeof(tab31));
+  if (e == cudaSuccess) e = mrg::upload_transform_table31(&ttab31[0][0], sizeof(ttab31));
+  if (e != cudaSuccess) return fail_cuda(e, "uploading MRG31k3p tables");
   e = mrg::preload_kernels();
   if (e != cudaSuccess) return fail_cuda(e, "loading the library's kernels");
   ready[dev] = true;
@@ -136,6 +143,75 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
   e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, consumed, 0, 0, cs(stream));
   if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (advance)");
+  return MRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MRG31k3p, the paper's own generator
+// ---------------------------------------------------------------------------
+
+int mrg31k3p_seed_check(const uint32_t seed[6]) {
+  if (!seed) return fail(MRG_EINVAL, "seed is NULL");
+  if (!mrg::host::g31::state_valid(seed))
+    return fail(MRG_EINVAL, "invalid MRG31k3p seed: need x1 words < 2^31 - 1, x2 words < "
+                            "2^31 - 21069, no all-zero triple");
+  return MRG_OK;
+}
+
+int mrg31k3p_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams* s,
+                            uint32_t next_seed[6], void* stream) {
+  int rc = mrg31k3p_seed_check(seed);
+  if (rc) return rc;
+  if (n > (1ull << 63)) return fail(MRG_ERANGE, "too many streams");
+  if (n > 0 && !streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (n > 0 && n > s->n) return fail(MRG_EINVAL, "n exceeds the stream set");
+  if (n > 0) {
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = mrg::launch_create31(seed, n, dev(s), cs(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "create31_kernel");
+  }
+  if (next_seed) {
+    uint32_t t[6];
+    std::memcpy(t, seed, sizeof t);
+    mrg::host::g31::jump_pow2_multiple(t, n, mrg::host::g31::kStreamLog2);
+    std::memcpy(next_seed, t, sizeof t);
+  }
+  return MRG_OK;
+}
+
+int mrg31k3p_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double rate,
+                      void* out, uint64_t ld, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  bool pair_ok = (dist == MRG_RAW && dtype == MRG_U32) ||
+                 ((dist == MRG_UNIFORM || dist == MRG_NORMAL || dist == MRG_EXPONENTIAL) &&
+                  (dtype == MRG_F32 || dtype == MRG_F64));
+  if (!pair_ok) return fail(MRG_EINVAL, "unsupported dist/dtype combination");
+  if (dist == MRG_EXPONENTIAL && !(rate >= 0x1p-64 && rate <= 0x1p64))
+    return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+  if (n == 0 || s->n == 0) return MRG_OK;
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  if (ld < n) return fail(MRG_EINVAL, "ld < n");
+  if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
+    return fail(MRG_EINVAL, "out is not aligned to its element size");
+  if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_generate31(dev(s), n, dist, dtype, rate, out, ld, mrg::GenConfig{},
+                                         cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "generate31_kernel");
+  const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
+  e = mrg::launch_jump31(s->cur, s->stride, s->n, consumed, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump31_kernel (advance)");
+  return MRG_OK;
+}
+
+int mrg31k3p_skip(const mrg_streams* s, uint64_t k, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (s->n == 0 || k == 0) return MRG_OK;
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_jump31(s->cur, s->stride, s->n, k, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "jump31_kernel (skip)");
   return MRG_OK;
 }
 

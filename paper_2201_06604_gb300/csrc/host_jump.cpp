@@ -111,10 +111,9 @@ void split(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
 }
-}  // namespace
 
-void transform_table(float out[kTransformEntries][4]) {
-  const double M = 4294967088.0;       // m1 + 1
+// Tables for uniforms u = z / M (z < M <= 2^32), quarter turn D = M / 4.
+void transform_table_for(double M, double D, float out[kTransformEntries][4]) {
   // log buckets: centre C_k of the zn-range [2^31 + k 2^24, 2^31 + (k+1) 2^24),
   // the top bucket centred at M so that ln(C_127 / M) = 0 exactly.
   for (int k = 0; k < 128; ++k) {
@@ -122,14 +121,85 @@ void transform_table(float out[kTransformEntries][4]) {
     split(1.0 / C, out[k][0], out[k][1]);
     split(std::log1p((C - M) / M), out[k][2], out[k][3]);
   }
-  // trig buckets: a_j = (pi/2) j 2^23 / D, D = M / 4 (a_0 = 0 exactly)
-  const double D = 1073741772.0;
+  // trig buckets: a_j = (pi/2) j 2^23 / D (a_0 = 0 exactly)
   for (int j = 0; j < 65; ++j) {
     const double a = (M_PI / 2) * ((j * 8388608.0) / D);
     split(std::sin(a), out[128 + j][0], out[128 + j][1]);
     split(std::cos(a), out[128 + j][2], out[128 + j][3]);
   }
 }
+}  // namespace
+
+void transform_table(float out[kTransformEntries][4]) {
+  transform_table_for(4294967088.0, 1073741772.0, out);   // M = m1 + 1, D = M / 4
+}
+
+void transform_table_m32(float out[kTransformEntries][4]) {
+  transform_table_for(4294967296.0, 1073741824.0, out);   // M = 2^32, D = 2^30
+}
+
+// ---------------------------------------------------------------------------
+// MRG31k3p: x1[n] = (2^22 x1[n-2] + (2^7 + 1) x1[n-3]) mod m1,
+//           x2[n] = (2^15 x2[n-1] + (2^15 + 1) x2[n-3]) mod m2.
+// ---------------------------------------------------------------------------
+namespace g31 {
+namespace {
+
+const uint64_t kMod31[2] = {2147483647ull, 2147462579ull};
+
+void companion31(int c, uint64_t A[9]) {
+  const uint64_t row0[2][3] = {{0, 1ull << 22, (1ull << 7) + 1}, {1ull << 15, 0, (1ull << 15) + 1}};
+  for (int j = 0; j < 3; ++j) A[j] = row0[c][j];
+  A[3] = 1; A[4] = 0; A[5] = 0;
+  A[6] = 0; A[7] = 1; A[8] = 0;
+}
+
+struct Tables31 {
+  uint64_t pow2[2][kJumpBits][9];
+  Tables31() {
+    for (int c = 0; c < 2; ++c) {
+      companion31(c, pow2[c][0]);
+      for (int i = 1; i < kJumpBits; ++i)
+        mat_mul(pow2[c][i - 1], pow2[c][i - 1], kMod31[c], pow2[c][i]);
+    }
+  }
+};
+
+const Tables31& tables31() {
+  static const Tables31 t;
+  return t;
+}
+
+}  // namespace
+
+void jump_table_u32(uint32_t out[2][kJumpBits][9]) {
+  const Tables31& t = tables31();
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < kJumpBits; ++i)
+      for (int k = 0; k < 9; ++k) out[c][i][k] = (uint32_t)t.pow2[c][i][k];
+}
+
+bool state_valid(const uint32_t s[6]) {
+  for (int k = 0; k < 3; ++k)
+    if (s[k] >= kMod31[0] || s[3 + k] >= kMod31[1]) return false;
+  if ((s[0] | s[1] | s[2]) == 0) return false;
+  if ((s[3] | s[4] | s[5]) == 0) return false;
+  return true;
+}
+
+void jump_pow2_multiple(uint32_t s[6], uint64_t e, int base) {
+  const Tables31& t = tables31();
+  uint64_t x[2][3] = {{s[0], s[1], s[2]}, {s[3], s[4], s[5]}};
+  for (int j = 0; j < 64 && (e >> j); ++j)
+    if ((e >> j) & 1)
+      for (int c = 0; c < 2; ++c) mat_vec(t.pow2[c][base + j], x[c], kMod31[c]);
+  for (int k = 0; k < 3; ++k) {
+    s[k] = (uint32_t)x[0][k];
+    s[3 + k] = (uint32_t)x[1][k];
+  }
+}
+
+}  // namespace g31
 
 }  // namespace host
 }  // namespace mrg

@@ -25,5 +25,19 @@ bool norm_constant_ok(uint64_t delta);
 constexpr int kTransformEntries = 193;
 void transform_table(float out[kTransformEntries][4]);
 
+// The same tables for uniforms u = z' / 2^32 (M = 2^32, quarter turn D = 2^30):
+// the transforms of MRG31k3p, whose u = z / 2^31 is fed as z' = 2 z.
+void transform_table_m32(float out[kTransformEntries][4]);
+
+// MRG31k3p (L'Ecuyer and Touzin 2000), the paper's own generator (Sec. 2):
+// m1 = 2^31 - 1, m2 = 2^31 - 21069; streams 2^134 apart (Sec. 2.1).
+namespace g31 {
+constexpr int kJumpBits = 198;  // A^(2^i), i < 198: offsets < 2^134, stream index < 2^64
+constexpr int kStreamLog2 = 134;
+void jump_table_u32(uint32_t out[2][kJumpBits][9]);
+bool state_valid(const uint32_t s[6]);
+void jump_pow2_multiple(uint32_t s[6], uint64_t e, int base);
+}  // namespace g31
+
 }  // namespace host
 }  // namespace mrg

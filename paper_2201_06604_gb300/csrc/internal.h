@@ -53,6 +53,17 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st);
 
+// MRG31k3p (gen31_kernels.cuh): tables, stream creation (2^134 apart), the
+// advance cur <- A^k cur (k < 2^64) and materialised generation.
+cudaError_t upload_tables31(const uint32_t* tab, size_t bytes);
+cudaError_t upload_transform_table31(const float* tab, size_t bytes);
+cudaError_t launch_create31(const uint32_t seed[6], uint64_t n, const DevStreams& s,
+                            cudaStream_t st);
+cudaError_t launch_jump31(uint32_t* cur, uint64_t stride, uint64_t ns, uint64_t k,
+                          cudaStream_t st);
+cudaError_t launch_generate31(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                              void* out, uint64_t ld, const GenConfig& cfg, cudaStream_t st);
+
 // Applies the output transform to caller-provided raw draws z[i] in [1, m1]
 // (consecutive pairs for normals): out[i] as generate would write it.
 cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype, double rate,

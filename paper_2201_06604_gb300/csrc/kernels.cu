@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
 
 #include "batch_kernels.cuh"
 #include "serve_kernels.cuh"
+#include "gen31_kernels.cuh"
 
 namespace mrg {
 
@@ -428,9 +429,9 @@ cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, do
 
 namespace {
 
-template <int DIST, int DT, int VB>
+template <int DIST, int DT, int VB, bool G31>
 cudaError_t launch_gen_t(const GenArgs& a, const GenConfig& cfg, cudaStream_t st) {
-  auto kern = generate_kernel<DIST, DT, VB>;
+  auto kern = G31 ? generate31_kernel<DIST, DT, VB> : generate_kernel<DIST, DT, VB>;
   const int block = cfg.block;
   static thread_local int occ_cache[64][9] = {};
   int dev = 0;
@@ -453,20 +454,26 @@ cudaError_t launch_gen_t(const GenArgs& a, const GenConfig& cfg, cudaStream_t st
   return after_launch();
 }
 
-template <int DIST, int DT>
+template <int DIST, int DT, bool G31>
 cudaError_t launch_gen_dt(const GenArgs& a, int vb, const GenConfig& cfg, cudaStream_t st) {
   switch (vb) {
-    case 32: return launch_gen_t<DIST, DT, 32>(a, cfg, st);
-    case 16: return launch_gen_t<DIST, DT, 16>(a, cfg, st);
-    case 8: return launch_gen_t<DIST, DT, 8>(a, cfg, st);
-    default: return launch_gen_t<DIST, DT, 4>(a, cfg, st);
+    case 32: return launch_gen_t<DIST, DT, 32, G31>(a, cfg, st);
+    case 16: return launch_gen_t<DIST, DT, 16, G31>(a, cfg, st);
+    case 8: return launch_gen_t<DIST, DT, 8, G31>(a, cfg, st);
+    default: return launch_gen_t<DIST, DT, 4, G31>(a, cfg, st);
   }
 }
 
+template <bool G31>
+cudaError_t launch_generate_g(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                              void* out, uint64_t ld, const GenConfig& cfg_in, cudaStream_t st);
+
 }  // namespace
 
-cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
-                            void* out, uint64_t ld, const GenConfig& cfg_in, cudaStream_t st) {
+namespace {
+template <bool G31>
+cudaError_t launch_generate_g(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                              void* out, uint64_t ld, const GenConfig& cfg_in, cudaStream_t st) {
   if (s.n == 0 || n == 0) return cudaSuccess;
   GenConfig cfg = cfg_in;
   if (cfg.block <= 0 || cfg.block > 256 || cfg.block % 32) cfg.block = 256;
@@ -505,15 +512,41 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
   const int vmax = (cfg.vec_bytes == 4 || cfg.vec_bytes == 8 || cfg.vec_bytes == 16) ? cfg.vec_bytes : 32;
   const int vb = (int)std::min<uint64_t>(align, (uint64_t)vmax);
   switch (dist * 4 + dtype) {
-    case MRG_RAW * 4 + MRG_U32: return launch_gen_dt<MRG_RAW, MRG_U32>(a, vb, cfg, st);
-    case MRG_UNIFORM * 4 + MRG_F32: return launch_gen_dt<MRG_UNIFORM, MRG_F32>(a, vb, cfg, st);
-    case MRG_UNIFORM * 4 + MRG_F64: return launch_gen_dt<MRG_UNIFORM, MRG_F64>(a, vb, cfg, st);
-    case MRG_NORMAL * 4 + MRG_F32: return launch_gen_dt<MRG_NORMAL, MRG_F32>(a, vb, cfg, st);
-    case MRG_NORMAL * 4 + MRG_F64: return launch_gen_dt<MRG_NORMAL, MRG_F64>(a, vb, cfg, st);
-    case MRG_EXPONENTIAL * 4 + MRG_F32: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F32>(a, vb, cfg, st);
-    case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64>(a, vb, cfg, st);
+    case MRG_RAW * 4 + MRG_U32: return launch_gen_dt<MRG_RAW, MRG_U32, G31>(a, vb, cfg, st);
+    case MRG_UNIFORM * 4 + MRG_F32: return launch_gen_dt<MRG_UNIFORM, MRG_F32, G31>(a, vb, cfg, st);
+    case MRG_UNIFORM * 4 + MRG_F64: return launch_gen_dt<MRG_UNIFORM, MRG_F64, G31>(a, vb, cfg, st);
+    case MRG_NORMAL * 4 + MRG_F32: return launch_gen_dt<MRG_NORMAL, MRG_F32, G31>(a, vb, cfg, st);
+    case MRG_NORMAL * 4 + MRG_F64: return launch_gen_dt<MRG_NORMAL, MRG_F64, G31>(a, vb, cfg, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F32: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F32, G31>(a, vb, cfg, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_gen_dt<MRG_EXPONENTIAL, MRG_F64, G31>(a, vb, cfg, st);
     default: return cudaErrorInvalidValue;
   }
+}
+}  // namespace
+
+cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                            void* out, uint64_t ld, const GenConfig& cfg, cudaStream_t st) {
+  return launch_generate_g<false>(s, n, dist, dtype, rate, out, ld, cfg, st);
+}
+
+cudaError_t launch_generate31(const DevStreams& s, uint64_t n, int dist, int dtype, double rate,
+                              void* out, uint64_t ld, const GenConfig& cfg, cudaStream_t st) {
+  return launch_generate_g<true>(s, n, dist, dtype, rate, out, ld, cfg, st);
+}
+
+cudaError_t launch_create31(const uint32_t seed[6], uint64_t n, const DevStreams& s,
+                            cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  State sd{seed[0], seed[1], seed[2], seed[3], seed[4], seed[5]};
+  create31_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(sd, n, s.cur, s.start, s.sub, s.stride);
+  return after_launch();
+}
+
+cudaError_t launch_jump31(uint32_t* cur, uint64_t stride, uint64_t ns, uint64_t k,
+                          cudaStream_t st) {
+  if (ns == 0 || k == 0) return cudaSuccess;
+  jump31_kernel<<<grid_for(ns, 256, 8), 256, 0, st>>>(cur, stride, ns, k);
+  return after_launch();
 }
 
 int batch_grid() {
@@ -608,6 +641,10 @@ void preload_gen(int& bad) {
   bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 16>) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 8>) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 4>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 32>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 16>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 8>) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 4>) != cudaSuccess;
 }
 template <int DIST, int DT>
 void preload_tr(int& bad) {
@@ -639,6 +676,8 @@ cudaError_t preload_kernels() {
   preload_tr<MRG_EXPONENTIAL, MRG_F64>(bad);
   bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<MRG_RAW, MRG_U32>) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, create31_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, jump31_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, batch_kernel) != cudaSuccess;

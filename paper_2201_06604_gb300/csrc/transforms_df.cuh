@@ -47,11 +47,27 @@ constexpr int TAB_LOG = 0;
 constexpr int TAB_TRIG = 128;
 constexpr int TAB_ENTRIES = 193;
 
-// ln 2 and (pi/2)/D as float pairs.
+// ln 2 as a float pair.
 constexpr float LN2_HI = 0x1.62e430p-1f;    // RN32(ln 2)
 constexpr float LN2_LO = -0x1.05c610p-29f;  // RN32(ln 2 - LN2_HI)
-constexpr float PID_HI = 0x1.921fb6p-30f;   // RN32(pi / (2 D)), D = (m1 + 1) / 4
-constexpr float PID_LO = 0x1.15f92cp-55f;   // RN32(pi / (2 D) - PID_HI)
+
+// The modulus M of the uniform u = z / M that the transforms take, with the
+// constants of its reductions.  The tables of each M come from the host
+// (transform_table / transform_table_m32) and are passed in `tab`.
+struct UM32k3a {                                  // M = m1 + 1 of MRG32k3a
+  static constexpr uint32_t TOP_CK = 4294967088u; // centre of the top log bucket: M
+  static constexpr uint32_t D = 1073741772u;      // M / 4
+  static constexpr uint32_t QFIX = 52u;           // 2^30 - D
+  static constexpr float PID_HI = 0x1.921fb6p-30f;  // RN32(pi / (2 D))
+  static constexpr float PID_LO = 0x1.15f92cp-55f;  // RN32(pi / (2 D) - PID_HI)
+};
+struct UM2p32 {                                   // M = 2^32 (MRG31k3p: z' = 2 z)
+  static constexpr uint32_t TOP_CK = 0u;          // M mod 2^32: zn - M as a signed word
+  static constexpr uint32_t D = 1073741824u;      // 2^30
+  static constexpr uint32_t QFIX = 0u;
+  static constexpr float PID_HI = 0x1.921fb6p-30f;  // RN32(pi / 2^31)
+  static constexpr float PID_LO = -0x1.777a5cp-55f; // RN32(pi / 2^31 - PID_HI)
+};
 
 __device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
   float s = __fadd_rn(a, b);
@@ -91,13 +107,14 @@ __device__ __forceinline__ float small_int_to_float(int32_t v) {
   return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
 }
 
-// ln(z / M) for z in [1, m1].
-__device__ __forceinline__ df ln_u_df(uint32_t z, const float4* __restrict__ tab) {
+// ln(z / M) for z in [1, M - 1].
+template <class UM>
+__device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ tab) {
   uint32_t s;
   asm("bfind.shiftamt.u32 %0, %1;" : "=r"(s) : "r"(z));
   const uint32_t zn = z << s;
   const uint32_t k = (zn >> 24) & 127u;
-  const uint32_t ck = k == 127u ? 4294967088u : 0x80800000u + (k << 24);
+  const uint32_t ck = k == 127u ? UM::TOP_CK : 0x80800000u + (k << 24);
   const int32_t d = (int32_t)(zn - ck);                 // |d| < 2^24: exact in fp32
   const float4 T = tab[TAB_LOG + k];
   const df r = df_mul_f(df{T.x, T.y}, (float)d);        // r = d / C_k
@@ -126,18 +143,19 @@ __device__ __forceinline__ df df_sqrt(df x) {
   return fast_two_sum(r0, __fmul_rn(__fmul_rn(e, y), 0.5f));
 }
 
-// sin and cos of 2 pi z / M for z in [1, m1].
-__device__ __forceinline__ void sincos_turn_df(uint32_t z, const float4* __restrict__ tab, df& sn,
-                                               df& cs) {
-  constexpr uint32_t D = 1073741772u;  // M / 4
+// sin and cos of 2 pi z / M for z in [1, M - 1].
+template <class UM>
+__device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __restrict__ tab, df& sn,
+                                                 df& cs) {
+  constexpr uint32_t D = UM::D;  // M / 4
   uint32_t q = z >> 30;
-  uint32_t w = (z & 0x3FFFFFFFu) + 52u * q;  // z - q D  (q D = q 2^30 - 52 q)
-  if (w >= D) { w -= D; ++q; }                // z = q D + w, w in [0, D)
+  uint32_t w = (z & 0x3FFFFFFFu) + UM::QFIX * q;  // z - q D  (q D = q 2^30 - QFIX q)
+  if (w >= D) { w -= D; ++q; }                     // z = q D + w, w in [0, D)
   const bool refl = 2u * w > D;
   const uint32_t wr = refl ? D - w : w;       // [0, D/2]
   const uint32_t j = (wr + 0x400000u) >> 23;  // 0..64
   const float dwf = small_int_to_float((int32_t)(wr - (j << 23)));   // [-2^22, 2^22)
-  const df delta = df_mul_f(df{PID_HI, PID_LO}, dwf);
+  const df delta = df_mul_f(df{UM::PID_HI, UM::PID_LO}, dwf);
   const float dh = delta.hi;
   const float d2 = __fmul_rn(dh, dh);
   // sin(delta) = delta + delta^3 (-1/6 + delta^2 / 120)
@@ -181,14 +199,28 @@ __device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
 
 // Box-Muller on one pair: X, Y as df.
-__device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
-                                              df& x, df& y) {
-  const df l = ln_u_df(z1, tab);
+template <class UM>
+__device__ __forceinline__ void box_muller_df_m(uint32_t z1, uint32_t z2,
+                                                const float4* __restrict__ tab, df& x, df& y) {
+  const df l = ln_u_df_m<UM>(z1, tab);
   const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
   df sn, cs;
-  sincos_turn_df(z2, tab, sn, cs);
+  sincos_turn_df_m<UM>(z2, tab, sn, cs);
   x = df_mul(R, cs);
   y = df_mul(R, sn);
+}
+
+// The transforms of MRG32k3a's uniforms u = z / (m1 + 1).
+__device__ __forceinline__ df ln_u_df(uint32_t z, const float4* __restrict__ tab) {
+  return ln_u_df_m<UM32k3a>(z, tab);
+}
+__device__ __forceinline__ void sincos_turn_df(uint32_t z, const float4* __restrict__ tab, df& sn,
+                                               df& cs) {
+  sincos_turn_df_m<UM32k3a>(z, tab, sn, cs);
+}
+__device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
+                                              df& x, df& y) {
+  box_muller_df_m<UM32k3a>(z1, z2, tab, x, y);
 }
 
 }  // namespace mrg

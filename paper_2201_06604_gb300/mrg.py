@@ -107,6 +107,10 @@ def _load():
         "mrg_get_state": ([sp, u32p, vp], i32),
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+        "mrg31k3p_seed_check": ([u32p], i32),
+        "mrg31k3p_create_streams": ([u32p, u64, sp, u32p, vp], i32),
+        "mrg31k3p_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
+        "mrg31k3p_skip": ([sp, u64, vp], i32),
         "mrg_generate_config": ([sp, u64, i32, i32, ctypes.c_double, vp, u64,
                                  ctypes.POINTER(LaunchConfig), vp], i32),
         "mrg_tune_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, ctypes.c_uint32,
@@ -171,11 +175,21 @@ def seed_check(seed) -> bool:
     return lib.mrg_seed_check(_u32_array(seed)) == OK
 
 
+GENERATORS = ("mrg32k3a", "mrg31k3p")
+
+
 class Streams:
     """n streams on one device: three int32 tensors [6, n] holding the uint32
-    words of the current state, the stream start and the substream start."""
+    words of the current state, the stream start and the substream start.
+    `generator` is "mrg32k3a" (default) or "mrg31k3p" (the paper's own
+    generator; create + generate + skip and the state copies only)."""
 
-    def __init__(self, n: int, device=None, *, _tensors=None):
+    generator = "mrg32k3a"
+
+    def __init__(self, n: int, device=None, *, _tensors=None, generator: str = "mrg32k3a"):
+        if generator not in GENERATORS:
+            raise ValueError(f"generator must be one of {GENERATORS}")
+        self.generator = generator
         dev = torch.device(device) if device is not None else torch.device("cuda")
         if _tensors is None:
             self.buf = torch.empty((3, 6, max(n, 1)), dtype=torch.int32, device=dev)
@@ -206,7 +220,7 @@ class Streams:
         if a < 0 or m < 0 or a + m > self.n:
             raise IndexError("stream range out of bounds")
         v = Streams.__new__(Streams)
-        v.buf, v.n = self.buf, m
+        v.buf, v.n, v.generator = self.buf, m, self.generator
         v._c = _Streams(self.buf[0].data_ptr() + 4 * a, self.buf[1].data_ptr() + 4 * a,
                         self.buf[2].data_ptr() + 4 * a, m, self.buf.shape[2])
         v._parent = self
@@ -238,21 +252,24 @@ def get_base_creator():
         return tuple(_creator.seed)
 
 
-def create_streams(n: int, device=None, seed=None, stream=None) -> Streams:
+def create_streams(n: int, device=None, seed=None, stream=None,
+                   generator: str = "mrg32k3a") -> Streams:
     """Creates n streams on the device.  With seed=None the module's creator
     state is used and advanced by n streams (Sec. 2.1); an explicit seed
-    leaves the creator untouched."""
-    s = Streams(n, device)
+    leaves the creator untouched.  generator="mrg31k3p" creates streams of
+    the paper's own generator (2^134 apart; an explicit seed is required)."""
+    s = Streams(n, device, generator=generator)
     nxt = (ctypes.c_uint32 * 6)()
+    fn = lib.mrg31k3p_create_streams if generator == "mrg31k3p" else lib.mrg_create_streams
     with torch.cuda.device(s.device):
         if seed is None:
+            if generator != "mrg32k3a":
+                raise ValueError("the module's creator state is MRG32k3a's: pass a seed")
             with _creator.lock:
-                _check(lib.mrg_create_streams(_u32_array(_creator.seed), n, s.ptr(), nxt,
-                                              _stream_handle(stream)))
+                _check(fn(_u32_array(_creator.seed), n, s.ptr(), nxt, _stream_handle(stream)))
                 _creator.seed = list(nxt)
         else:
-            _check(lib.mrg_create_streams(_u32_array(seed), n, s.ptr(), nxt,
-                                          _stream_handle(stream)))
+            _check(fn(_u32_array(seed), n, s.ptr(), nxt, _stream_handle(stream)))
     s.next_seed = tuple(nxt)
     return s
 
@@ -277,10 +294,16 @@ def generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64, rate
         raise ValueError("out must be [>= n_streams, >= n] with unit column stride")
     if out.dtype != dt:
         raise ValueError(f"out dtype {out.dtype} != {dt}")
+    fn = lib.mrg31k3p_generate if streams.generator == "mrg31k3p" else lib.mrg_generate
     with torch.cuda.device(streams.device):
-        _check(lib.mrg_generate(streams.ptr(), n, d, code, float(rate), out.data_ptr(),
-                                out.stride(0), _stream_handle(stream)))
+        _check(fn(streams.ptr(), n, d, code, float(rate), out.data_ptr(), out.stride(0),
+                  _stream_handle(stream)))
     return out
+
+
+def _need_mrg32k3a(streams: Streams, what: str):
+    if streams.generator != "mrg32k3a":
+        raise ValueError(f"{what} is implemented for MRG32k3a streams only")
 
 
 def _gen_args(streams, n, dist, dtype, out):
@@ -310,6 +333,7 @@ def generate_config(streams: Streams, n: int, cfg, dist="uniform", dtype=torch.f
                     stream=None) -> torch.Tensor:
     """generate() with an explicit launch shape (dict or LaunchConfig with
     seg_len, block, vec_bytes, blocks_per_sm); same output for any shape."""
+    _need_mrg32k3a(streams, "generate_config")
     d, code, out = _gen_args(streams, n, dist, dtype, out)
     c = _config(cfg)
     with torch.cuda.device(streams.device):
@@ -323,6 +347,7 @@ def tune_generate(streams: Streams, n: int, dist="uniform", dtype=torch.float64,
                   stream=None):
     """Runs the library's autotuner for this generate call (states are not
     advanced) and returns (best shape dict, [(shape dict, ms), ...])."""
+    _need_mrg32k3a(streams, "tune_generate")
     d, code, out = _gen_args(streams, n, dist, dtype, out)
     res = (_TuneEntry * 64)()
     nres = ctypes.c_uint32()
@@ -361,6 +386,7 @@ def generate_host(streams: Streams, n: int, dist="uniform", dtype=torch.float64,
     """Like generate, but into a host tensor (pinned when allocated here); the
     device-to-host copy of one chunk of streams overlaps the generation of
     the next.  `scratch` is a device uint8 tensor (default 512 MiB)."""
+    _need_mrg32k3a(streams, "generate_host")
     d = _DIST[dist] if isinstance(dist, str) else int(dist)
     dt = torch.int32 if d == RAW else dtype
     code = _dtype_code(d, dt)
@@ -398,6 +424,12 @@ def transform(z: torch.Tensor, dist="normal", dtype=torch.float64, rate: float =
 
 
 def skip(streams: Streams, k: int, stream=None):
+    if streams.generator == "mrg31k3p":
+        if k < 0 or k >= 1 << 64:
+            raise ValueError("k must be in [0, 2^64) for MRG31k3p streams")
+        with torch.cuda.device(streams.device):
+            _check(lib.mrg31k3p_skip(streams.ptr(), k, _stream_handle(stream)))
+        return
     if k < 0 or k >= 1 << 128:
         raise ValueError("k must be in [0, 2^128)")
     with torch.cuda.device(streams.device):
@@ -405,6 +437,7 @@ def skip(streams: Streams, k: int, stream=None):
 
 
 def substream_next(streams: Streams, stream=None):
+    _need_mrg32k3a(streams, "substream_next")
     with torch.cuda.device(streams.device):
         _check(lib.mrg_substream_next(streams.ptr(), _stream_handle(stream)))
 
@@ -438,6 +471,7 @@ def set_state(streams: Streams, host, stream=None):
 
 
 def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream=None):
+    _need_mrg32k3a(streams, "fused_pi_normsum")
     if count is None:
         count = torch.empty(streams.n, dtype=torch.int64, device=streams.device)
     if sum_ is None:
@@ -476,6 +510,7 @@ class Batch:
 
     def __init__(self, streams: Streams, max_requests: int = 4096, max_tiles: int = 1 << 16,
                  stream=None):
+        _need_mrg32k3a(streams, "Batch")
         self.streams = streams
         self.max_requests = max_requests
         h = ctypes.c_void_p()
@@ -570,6 +605,7 @@ class Server:
 
     def __init__(self, streams: Streams, arena_bytes: int, max_slots: int = 4096,
                  ring_tiles: int = 1 << 16, idle_seconds: float = 30.0, sm_fraction: float = 0.5):
+        _need_mrg32k3a(streams, "Server")
         self.streams = streams
         self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=streams.device)
         h = ctypes.c_void_p()

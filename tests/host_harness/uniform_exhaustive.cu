@@ -4,11 +4,16 @@
 //     of the IEEE product (double)z * RN64(1/(m1+1)), and f32_bits_from_f64
 //     equals the bits of (float) of that product.
 //   mode "step" n seed: prints n outputs of mrg::step from a state.
+//   mode "uniform31": for every z in [1, 2^31 - 1], g31::uniform_bits64(z) and
+//     g31::uniform_bits32(z) equal the bits of (double)z * 2^-31 and of its
+//     rounding to float (MRG31k3p).
+//   mode "step31" n seed: prints n outputs of g31::step from a state.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
 #include "../../paper_2201_06604_gb300/csrc/mrg32k3a_core.cuh"
+#include "../../paper_2201_06604_gb300/csrc/mrg31k3p_core.cuh"
 
 static int check_uniform(unsigned lo, unsigned hi) {
   volatile double norm_v = 1.0 / 4294967088.0;
@@ -34,7 +39,37 @@ static int check_uniform(unsigned lo, unsigned hi) {
   return bad != 0;
 }
 
+static int check_uniform31() {
+  long long bad = 0;
+#pragma omp parallel for reduction(+ : bad) schedule(static, 1 << 16)
+  for (long long zz = 1; zz < (1ll << 31); ++zz) {
+    uint32_t z = (uint32_t)zz;
+    double d = (double)z * 0x1p-31;
+    float f = (float)d;
+    uint64_t want;
+    uint32_t wantf;
+    std::memcpy(&want, &d, 8);
+    std::memcpy(&wantf, &f, 4);
+    if (mrg::g31::uniform_bits64(z) != want || mrg::g31::uniform_bits32(z) != wantf) {
+      if (bad < 5) std::printf("mismatch z=%u\n", z);
+      ++bad;
+    }
+  }
+  std::printf("checked [1, 2^31 - 1]: %lld mismatches\n", bad);
+  return bad != 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc >= 2 && !std::strcmp(argv[1], "uniform31")) return check_uniform31();
+  if (argc >= 9 && !std::strcmp(argv[1], "step31")) {
+    long n = std::atol(argv[2]);
+    mrg::State c{(uint32_t)std::strtoul(argv[3], 0, 10), (uint32_t)std::strtoul(argv[4], 0, 10),
+                 (uint32_t)std::strtoul(argv[5], 0, 10), (uint32_t)std::strtoul(argv[6], 0, 10),
+                 (uint32_t)std::strtoul(argv[7], 0, 10), (uint32_t)std::strtoul(argv[8], 0, 10)};
+    for (long i = 0; i < n; ++i) std::printf("%u\n", mrg::g31::step(c));
+    std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
+    return 0;
+  }
   if (argc >= 2 && !std::strcmp(argv[1], "uniform")) {
     unsigned lo = argc > 2 ? (unsigned)std::strtoul(argv[2], 0, 10) : 1u;
     unsigned hi = argc > 3 ? (unsigned)std::strtoul(argv[3], 0, 10) : mrg::M1;
@@ -51,6 +86,6 @@ int main(int argc, char** argv) {
     std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
     return 0;
   }
-  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5\n");
+  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5\n");
   return 2;
 }

@@ -3,7 +3,9 @@ own header and checked on the CPU (no GPU needed):
 
 * the fp64 uniform built in integers equals the IEEE product z * norm for
   every z in [1, m1] (exhaustive), and the fp32 uniform equals its rounding;
-* the folded modular step reproduces the oracle's plain `%` recurrence.
+* the folded modular step reproduces the oracle's plain `%` recurrence;
+* the same for MRG31k3p, the paper's own generator: its exact fp64 uniform
+  z / 2^31 and fp32 rounding for every z, and its step against the oracle.
 """
 import os
 import shutil
@@ -24,10 +26,11 @@ def harness():
     if shutil.which("nvcc") is None:
         pytest.skip("nvcc not available")
     os.makedirs(os.path.dirname(BIN), exist_ok=True)
+    csrc = os.path.join(HERE, "..", "paper_2201_06604_gb300", "csrc")
     if not os.path.exists(BIN) or os.path.getmtime(BIN) < max(
             os.path.getmtime(SRC),
-            os.path.getmtime(os.path.join(HERE, "..", "paper_2201_06604_gb300", "csrc",
-                                          "mrg32k3a_core.cuh"))):
+            os.path.getmtime(os.path.join(csrc, "mrg32k3a_core.cuh")),
+            os.path.getmtime(os.path.join(csrc, "mrg31k3p_core.cuh"))):
         subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fopenmp",
                         "-Xcompiler", "-ffp-contract=off", "-o", BIN, SRC], check=True)
     return BIN
@@ -64,3 +67,25 @@ def test_step_extreme_states(harness):
         lines = r.stdout.split("\n")
         want, after = O.raw(np.array(st, np.uint32), n)
         assert [int(v) for v in lines[:n]] == [int(v) for v in want]
+
+
+def test_uniform31_bits_exhaustive(harness):
+    r = subprocess.run([harness, "uniform31"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "0 mismatches" in r.stdout
+
+
+def test_step31_matches_oracle(harness):
+    m1, m2 = O.MRG31K3P[0], O.MRG31K3P[1]
+    rng = np.random.default_rng(7)
+    states = [[12345] * 6, [m1 - 1] * 3 + [m2 - 1] * 3, [0, 0, 1, 0, 0, 1],
+              [m1 - 1, 0, 0, 0, m2 - 1, 0], [1, m1 - 1, m1 - 1, m2 - 1, 1, m2 - 1],
+              list(rng.integers(0, m1, 3)) + list(rng.integers(0, m2, 3))]
+    for st in states:
+        n = 5000
+        r = subprocess.run([harness, "step31", str(n), *map(str, st)], capture_output=True,
+                           text=True, timeout=120, check=True)
+        lines = r.stdout.split("\n")
+        want, after = O.raw(np.array(st, np.uint32), n, gen=O.MRG31K3P)
+        assert [int(v) for v in lines[:n]] == [int(v) for v in want], st
+        assert [int(v) for v in lines[n].split()] == [int(v) for v in after], st
