@@ -89,6 +89,19 @@ def lib():
                                                ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]
             L.orc_fused.argtypes = [P, _u32p, ctypes.c_uint64, ctypes.c_uint64, _i64p, _f64p,
                                     ctypes.c_int]
+            _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            L.orc_logfact_table.argtypes = [ctypes.c_uint64, _f64p]
+            L.orc_logfact_sum.argtypes = [_i32p, ctypes.c_uint32, ctypes.c_uint32, _f64p]
+            L.orc_logfact_sum.restype = ctypes.c_double
+            L.orc_hyper_inv.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_double, _f64p]
+            L.orc_hyper_inv.restype = ctypes.c_int64
+            L.orc_fisher.argtypes = [P, _u32p, ctypes.c_uint64, _i32p, ctypes.c_uint32,
+                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _f64p,
+                                     ctypes.c_void_p, ctypes.c_int]
+            L.orc_fisher.restype = ctypes.c_uint64
+            L.orc_fisher_tables.argtypes = [P, _u32p, _i32p, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint64, _f64p, _i32p]
             _lib = L
     return _lib
 
@@ -228,3 +241,66 @@ def fused(states, draws: int, nthreads: int = 1, gen=MRG32K3A):
     sm = np.zeros(max(ns, 1), np.float64)
     lib().orc_fused(_p(gen), states.reshape(-1), ns, draws, cnt, sm, nthreads)
     return cnt[:ns], sm[:ns], states
+
+
+# ---------------------------------------------------------------------------
+# Fisher's exact test by Monte Carlo (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def logfact_table(n: int) -> np.ndarray:
+    """log(k!) for k = 0..n (lgamma)."""
+    lf = np.zeros(n + 1, np.float64)
+    lib().orc_logfact_table(n, lf)
+    return lf
+
+
+def logfact_sum(table, lf=None) -> float:
+    """-sum log(n_ij!) of a table (the statistic of Sec. 4, logfactSum)."""
+    t = np.ascontiguousarray(table, dtype=np.int32)
+    if lf is None:
+        lf = logfact_table(int(t.max()))
+    return lib().orc_logfact_sum(t, t.shape[0], t.shape[1], lf)
+
+
+def hyper_inv(S: int, K: int, R: int, u: float, lf) -> int:
+    """Smallest x with u <= F(x), F the CDF of the number of marked items in
+    R draws without replacement from S items of which K are marked."""
+    return int(lib().orc_hyper_inv(S, K, R, float(u), lf))
+
+
+def fisher_threshold(table, lf=None) -> float:
+    """The observed statistic, widened by a relative 64 ulp so that tables
+    whose statistic equals it mathematically count as "at or below" it
+    whatever their summation rounding."""
+    return logfact_sum(table, lf) / (1.0 + 64.0 * np.finfo(np.float64).eps)
+
+
+def fisher(states, table, B: int, nthreads: int = 1, return_stats: bool = False,
+           gen=MRG32K3A):
+    """B simulated tables with the margins of `table`; replicate b uses
+    stream b mod len(states).  Returns (count of statistics <= threshold,
+    threshold, states after[, stats[B]])."""
+    t = np.ascontiguousarray(table, dtype=np.int32)
+    I, J = t.shape
+    if not (2 <= I <= 64 and 2 <= J <= 64):
+        raise ValueError("2 <= I, J <= 64")
+    lf = logfact_table(int(t.sum()))
+    thr = fisher_threshold(t, lf)
+    st = np.array(states, dtype=np.uint32, order="C", copy=True)
+    stats = np.zeros(max(B, 1), np.float64) if return_stats else None
+    cnt = lib().orc_fisher(_p(gen), st.reshape(-1), st.shape[0], t, I, J, B, thr, lf,
+                           stats.ctypes.data if return_stats else None, nthreads)
+    out = (int(cnt), thr, st)
+    return out + (stats[:B],) if return_stats else out
+
+
+def fisher_tables(state, table, B: int, gen=MRG32K3A):
+    """B random tables [B, I, J] with the margins of `table`, from one stream
+    (returns (tables, state after))."""
+    t = np.ascontiguousarray(table, dtype=np.int32)
+    I, J = t.shape
+    lf = logfact_table(int(t.sum()))
+    st = _state(state).copy()
+    out = np.zeros((max(B, 1), I, J), np.int32)
+    lib().orc_fisher_tables(_p(gen), st, t, I, J, B, lf, out.reshape(-1))
+    return out[:B], st

@@ -421,3 +421,156 @@ void orc_fused(const int64_t *p, uint32_t *states, uint64_t nstreams, uint64_t d
         store_state(s, states + 6 * i);
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Fisher's exact test by Monte Carlo (Sec. 4): statistic, random tables   */
+/* with the observed margins, and the count of simulated statistics at or  */
+/* below the observed one.                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* lf[k] = log(k!) for k = 0..n, from lgamma. */
+void orc_logfact_table(uint64_t n, double *lf)
+{
+    for (uint64_t k = 0; k <= n; ++k)
+        lf[k] = lgamma((double)k + 1.0);
+}
+
+/* The test statistic of a table (Sec. 4: "minus log-factorial of table"),
+ * -sum_{i,j} log(n_ij!), summed row by row, left to right. */
+double orc_logfact_sum(const int32_t *table, uint32_t I, uint32_t J, const double *lf)
+{
+    double t = 0.0;
+    for (uint32_t i = 0; i < I; ++i)
+        for (uint32_t j = 0; j < J; ++j)
+            t -= lf[table[(size_t)i * J + j]];
+    return t;
+}
+
+/* Probability that a draw of R items without replacement from a population
+ * of S items, K of which are marked, holds exactly x marked items. */
+static double hyper_pmf(int64_t S, int64_t K, int64_t R, int64_t x, const double *lf)
+{
+    double l = lf[K] - lf[x] - lf[K - x] + lf[S - K] - lf[R - x] - lf[S - K - R + x]
+               - (lf[S] - lf[R] - lf[S - R]);
+    return exp(l);
+}
+
+/* Standard inversion of that distribution's CDF with one uniform u: the
+ * smallest x of the support with u <= F(x), F accumulated from the bottom
+ * of the support (the largest x if rounding leaves F below u). */
+int64_t orc_hyper_inv(int64_t S, int64_t K, int64_t R, double u, const double *lf)
+{
+    int64_t lo = R - (S - K) > 0 ? R - (S - K) : 0;
+    int64_t hi = R < K ? R : K;
+    double F = 0.0;
+    for (int64_t x = lo; x < hi; ++x) {
+        F += hyper_pmf(S, K, R, x, lf);
+        if (u <= F)
+            return x;
+    }
+    return hi;
+}
+
+/* One random table with row sums r[I] and column sums c[J] (Sec. 4 step 2,
+ * Patefield's method as the paper describes it): entries sampled row by row,
+ * left to right, each from its distribution conditional on the entries
+ * already sampled -- the cell (i, j) holds x of the R units still to place
+ * in row i among the S units left in columns j..J-1 of rows i..I-1, of which
+ * C_j are in column j -- by inversion with one uniform; the last entry of a
+ * row and the whole last row follow from the margins.  (I-1)(J-1) uniforms
+ * per table.  Returns the table's statistic; `st` advances by those draws. */
+static double fisher_table(const gen_t *g, uint64_t s[6], const int32_t *r, const int32_t *c,
+                           uint32_t I, uint32_t J, const double *lf, int32_t *cell)
+{
+    double norm = 1.0 / (double)(g->m[0] + 1);
+    int64_t C[64];
+    int64_t rest = 0;
+    for (uint32_t j = 0; j < J; ++j) {
+        C[j] = c[j];
+        rest += c[j];
+    }
+    for (uint32_t i = 0; i + 1 < I; ++i) {
+        int64_t R = r[i];
+        int64_t S = rest;
+        for (uint32_t j = 0; j + 1 < J; ++j) {
+            double u = (double)gen_step(g, s) * norm;
+            int64_t x = orc_hyper_inv(S, C[j], R, u, lf);
+            cell[(size_t)i * J + j] = (int32_t)x;
+            S -= C[j];
+            C[j] -= x;
+            R -= x;
+        }
+        cell[(size_t)i * J + J - 1] = (int32_t)R;
+        C[J - 1] -= R;
+        rest -= r[i];
+    }
+    for (uint32_t j = 0; j < J; ++j)
+        cell[(size_t)(I - 1) * J + j] = (int32_t)C[j];
+    return orc_logfact_sum(cell, I, J, lf);
+}
+
+/* B replicates on nstreams streams: replicate b uses stream b mod nstreams,
+ * taking that stream's next (I-1)(J-1) uniforms (replicates of one stream in
+ * increasing b).  stats[b] (may be NULL) receives each statistic; the return
+ * value is the number of replicates with statistic <= threshold (Sec. 4
+ * step 3).  states advance in place.  2 <= I, J <= 64. */
+uint64_t orc_fisher(const int64_t *p, uint32_t *states, uint64_t nstreams, const int32_t *table,
+                    uint32_t I, uint32_t J, uint64_t B, double threshold, const double *lf,
+                    double *stats, int nthreads)
+{
+    int32_t r[64], c[64];
+    for (uint32_t i = 0; i < I; ++i) {
+        r[i] = 0;
+        for (uint32_t j = 0; j < J; ++j)
+            r[i] += table[(size_t)i * J + j];
+    }
+    for (uint32_t j = 0; j < J; ++j) {
+        c[j] = 0;
+        for (uint32_t i = 0; i < I; ++i)
+            c[j] += table[(size_t)i * J + j];
+    }
+    if (nthreads < 1)
+        nthreads = 1;
+    uint64_t count = 0;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 16) reduction(+ : count)
+    for (uint64_t sidx = 0; sidx < nstreams; ++sidx) {
+        gen_t g = unpack(p);
+        uint64_t s[6];
+        int32_t cell[64 * 64];
+        load_state(states + 6 * sidx, s);
+        for (uint64_t b = sidx; b < B; b += nstreams) {
+            double t = fisher_table(&g, s, r, c, I, J, lf, cell);
+            if (stats)
+                stats[b] = t;
+            if (t <= threshold)
+                ++count;
+        }
+        store_state(s, states + 6 * sidx);
+    }
+    return count;
+}
+
+/* B random tables from one stream (state advanced in place): tables
+ * [B][I][J] receives the cells, the return value is unused (0). */
+int orc_fisher_tables(const int64_t *p, uint32_t st[6], const int32_t *table, uint32_t I,
+                      uint32_t J, uint64_t B, const double *lf, int32_t *tables)
+{
+    gen_t g = unpack(p);
+    int32_t r[64], c[64];
+    for (uint32_t i = 0; i < I; ++i) {
+        r[i] = 0;
+        for (uint32_t j = 0; j < J; ++j)
+            r[i] += table[(size_t)i * J + j];
+    }
+    for (uint32_t j = 0; j < J; ++j) {
+        c[j] = 0;
+        for (uint32_t i = 0; i < I; ++i)
+            c[j] += table[(size_t)i * J + j];
+    }
+    uint64_t s[6];
+    load_state(st, s);
+    for (uint64_t b = 0; b < B; ++b)
+        fisher_table(&g, s, r, c, I, J, lf, tables + b * (size_t)I * J);
+    store_state(s, st);
+    return 0;
+}
