@@ -113,6 +113,16 @@ class ClockSampler:
 # Reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def load_table(name):
+    """A contingency table printed in the paper (test fixture, Sec. 4)."""
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return np.array(rows, np.int32)
+
+
 def cpu_oracle_sample(streams: int, draws: int, nthreads: int):
     """Times the oracle on `streams` streams x `draws` draws of every variant
     (same seed, same transforms).  Returns (draws/s, seconds, draws done)."""
@@ -519,6 +529,25 @@ def run_gpu(args):
                  "pi_estimate": 4.0 * cnt.sum().item() / pairs}
         del f_st, cnt, sm_
 
+    # Monte Carlo Fisher's exact test on the paper's two tables at the
+    # paper's replicate counts (one thread per stream, 2^20 streams)
+    fisher = None
+    if not args.skip_fisher:
+        fisher = {}
+        f_st = mrg.create_streams(1 << 20, device=dev, seed=seed)
+        for name, fname, B in (("month 12x12", "fisher_month.txt", 1 << 20),
+                               ("week 7x12", "fisher_week.txt", 10027008)):
+            table = load_table(fname)
+            mrg.fisher_sim(f_st, table, B)          # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = mrg.fisher_sim(f_st, table, B)
+            sec = time.perf_counter() - t0
+            fisher[name] = {"B": B, "seconds": sec, "tables_per_s": B / sec,
+                            "p_value": res["p_value"], "count": res["count"],
+                            "threshold": res["threshold"]}
+        del f_st
+
     # the paper's own generator (MRG31k3p) on the same materialised shape
     g31 = None
     if not args.skip_mrg31k3p:
@@ -556,6 +585,14 @@ def run_gpu(args):
         cpu = {"value": v, "unit": "draws/s", "cores": cores, "kind": "oracle",
                "sample": f"16384 of 65536 streams x 16384 draws x 5 variants ({tot} draws) in "
                          f"{sec:.2f} s, OpenMP over streams"}
+        if fisher is not None:
+            month = load_table("fisher_month.txt")
+            ost, _ = oracle.create_streams(tuple(W.PAPER_SEED), 4096)
+            t0 = time.perf_counter()
+            oracle.fisher(ost, month, 1 << 16, nthreads=cores)
+            fsec = time.perf_counter() - t0
+            cpu["fisher_month_tables_per_s"] = (1 << 16) / fsec
+            cpu["fisher_sample"] = f"month table, 65536 replicates on 4096 streams in {fsec:.2f} s"
 
     line = {
         "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": world, "steps": K,
@@ -575,6 +612,7 @@ def run_gpu(args):
         "e2e": e2e,
         "fused": fused,
         "mrg31k3p": g31,
+        "fisher": fisher,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
@@ -598,6 +636,7 @@ def main():
     ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-mrg31k3p", action="store_true")
+    ap.add_argument("--skip-fisher", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--streams", type=int, default=0, help="override the stream count (profiling)")

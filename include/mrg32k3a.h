@@ -180,6 +180,34 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- Monte Carlo Fisher's exact test (Sec. 4) ---------------------------- */
+
+/* Bytes of device scratch mrg_fisher_sim needs for a table whose entries sum
+ * to n_total: a 1 KiB header and the log-factorials 0..n_total (fp64). */
+uint64_t mrg_fisher_scratch_bytes(uint64_t n_total);
+
+/* Simulated p-value of Fisher's exact test for an I x J contingency table
+ * (host, int32, row-major, entries >= 0, total < 2^24, 2 <= I, J <= 64), as
+ * Sec. 4 describes it: B random tables with the observed margins, each
+ * sampled row by row, left to right, every cell drawn from its
+ * hypergeometric distribution conditional on the cells before it by
+ * inversion with one fp64 uniform (Patefield's method; (I-1)(J-1) draws per
+ * table), and the statistic -sum log(n_ij!) of each.  Replicate b runs on
+ * stream b mod s->n, taking that stream's next draws; each stream advances
+ * by the draws its replicates consumed, so later calls continue it.
+ * *count (host) receives the number of replicates whose statistic is at or
+ * below the observed one (with a relative allowance of 64 ulp, so that ties
+ * count whatever their rounding); the p-value is (1 + *count) / (B + 1).
+ * *threshold (host, may be NULL) receives that bound.  stats (device, B
+ * doubles, may be NULL) receives every replicate's statistic.  scratch:
+ * caller-owned device memory, 256-byte aligned, at least
+ * mrg_fisher_scratch_bytes(total) bytes.  Synchronises `stream`.  Errors:
+ * MRG_EINVAL (shape, entries, NULL pointers, scratch too small), MRG_ERANGE
+ * (total not below 2^24), MRG_ECUDA. */
+int mrg_fisher_sim(const mrg_streams *s, const int32_t *table, uint32_t I, uint32_t J,
+                   uint64_t B, void *scratch, uint64_t scratch_bytes, double *stats,
+                   uint64_t *count, double *threshold, void *stream);
+
 /* ---- MRG31k3p, the paper's own generator --------------------------------
  * The package of the paper is built on MRG31k3p (L'Ecuyer and Touzin 2000;
  * Sec. 2): x1[n] = (2^22 x1[n-2] + (2^7 + 1) x1[n-3]) mod (2^31 - 1),

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -143,6 +145,90 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   const uint64_t consumed = dist == MRG_NORMAL ? n + (n & 1) : n;
   e = mrg::launch_jump(s->cur, s->cur, nullptr, s->stride, s->n, consumed, 0, 0, cs(stream));
   if (e != cudaSuccess) return fail_cuda(e, "jump_kernel (advance)");
+  return MRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Monte Carlo Fisher's exact test (Sec. 4)
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+constexpr uint64_t kFisherHeader = 1024;  // count (8 B), rows, cols (4 B each, <= 64)
+
+// log(k!) for k = 0..n on the host (lgamma), grown on demand and kept.
+const std::vector<double>& host_logfact(uint64_t n) {
+  static std::mutex mu;
+  static std::vector<double> lf;
+  std::lock_guard<std::mutex> lk(mu);
+  for (uint64_t k = lf.size(); k <= n; ++k) lf.push_back(std::lgamma((double)k + 1.0));
+  return lf;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t mrg_fisher_scratch_bytes(uint64_t n_total) {
+  return kFisherHeader + 8 * (n_total + 1);
+}
+
+int mrg_fisher_sim(const mrg_streams* s, const int32_t* table, uint32_t I, uint32_t J,
+                   uint64_t B, void* scratch, uint64_t scratch_bytes, double* stats,
+                   uint64_t* count, double* threshold, void* stream) {
+  if (!streams_ok(s) || s->n == 0) return fail(MRG_EINVAL, "bad stream set");
+  if (!table || !count) return fail(MRG_EINVAL, "table/count is NULL");
+  if (I < 2 || J < 2 || I > mrg::kFisherMaxDim || J > mrg::kFisherMaxDim)
+    return fail(MRG_EINVAL, "table must be I x J with 2 <= I, J <= 64");
+  int32_t rows[mrg::kFisherMaxDim] = {}, cols[mrg::kFisherMaxDim] = {};
+  int64_t total = 0;
+  for (uint32_t i = 0; i < I; ++i)
+    for (uint32_t j = 0; j < J; ++j) {
+      const int32_t v = table[(size_t)i * J + j];
+      if (v < 0) return fail(MRG_EINVAL, "negative table entry");
+      rows[i] += v;
+      cols[j] += v;
+      total += v;
+      if (total >= (1 << 24)) return fail(MRG_ERANGE, "table total not below 2^24");
+    }
+  if (!scratch || reinterpret_cast<uintptr_t>(scratch) % 256 ||
+      scratch_bytes < mrg_fisher_scratch_bytes((uint64_t)total))
+    return fail(MRG_EINVAL, "scratch NULL, not 256-byte aligned or smaller than "
+                            "mrg_fisher_scratch_bytes(total)");
+  if (stats && reinterpret_cast<uintptr_t>(stats) % 8) return fail(MRG_EINVAL, "stats misaligned");
+  int rc = ensure_device();
+  if (rc) return rc;
+  const std::vector<double>& lf = host_logfact((uint64_t)total);
+  // the observed statistic, -sum log(n_ij!) row by row; "at or below" it is
+  // taken with a relative allowance of 64 ulp, so that a table whose
+  // statistic equals it mathematically counts whatever its rounding
+  double tobs = 0.0;
+  for (uint32_t i = 0; i < I; ++i)
+    for (uint32_t j = 0; j < J; ++j) tobs -= lf[table[(size_t)i * J + j]];
+  const double thr = tobs / (1.0 + 64.0 * DBL_EPSILON);
+  if (threshold) *threshold = thr;
+  char* sc = static_cast<char*>(scratch);
+  unsigned long long* d_count = reinterpret_cast<unsigned long long*>(sc);
+  int32_t* d_rows = reinterpret_cast<int32_t*>(sc + 256);
+  int32_t* d_cols = reinterpret_cast<int32_t*>(sc + 512);
+  double* d_lf = reinterpret_cast<double*>(sc + kFisherHeader);
+  cudaStream_t st = cs(stream);
+  cudaError_t e = cudaMemsetAsync(d_count, 0, 8, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rows, rows, 4 * I, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cols, cols, 4 * J, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_lf, lf.data(), 8 * ((uint64_t)total + 1), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_cuda(e, "copying the Fisher tables");
+  e = mrg::launch_fisher(dev(s), d_rows, d_cols, I, J, (int32_t)total, d_lf, B, thr, d_count,
+                         stats, st);
+  if (e != cudaSuccess) return fail_cuda(e, "fisher_kernel");
+  unsigned long long h = 0;
+  e = cudaMemcpyAsync(&h, d_count, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda(e, "reading the Fisher count");
+  *count = h;
   return MRG_OK;
 }
 

@@ -53,6 +53,15 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st);
 
+// Monte Carlo Fisher's exact test (fisher_kernels.cuh): B replicates on the
+// streams of s (replicate b on stream b mod s.n); rows/cols/lf/count in
+// device memory, *count accumulated (not reset), stats optional.
+constexpr uint32_t kFisherMaxDim = 64;
+cudaError_t launch_fisher(const DevStreams& s, const int32_t* rows, const int32_t* cols,
+                          uint32_t I, uint32_t J, int32_t total, const double* lf, uint64_t B,
+                          double threshold, unsigned long long* count, double* stats,
+                          cudaStream_t st);
+
 // MRG31k3p (gen31_kernels.cuh): tables, stream creation (2^134 apart), the
 // advance cur <- A^k cur (k < 2^64) and materialised generation.
 cudaError_t upload_tables31(const uint32_t* tab, size_t bytes);

@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
 #include "batch_kernels.cuh"
 #include "serve_kernels.cuh"
 #include "gen31_kernels.cuh"
+#include "fisher_kernels.cuh"
 
 namespace mrg {
 
@@ -534,6 +535,29 @@ cudaError_t launch_generate31(const DevStreams& s, uint64_t n, int dist, int dty
   return launch_generate_g<true>(s, n, dist, dtype, rate, out, ld, cfg, st);
 }
 
+cudaError_t launch_fisher(const DevStreams& s, const int32_t* rows, const int32_t* cols,
+                          uint32_t I, uint32_t J, int32_t total, const double* lf, uint64_t B,
+                          double threshold, unsigned long long* count, double* stats,
+                          cudaStream_t st) {
+  if (s.n == 0) return cudaSuccess;
+  FisherArgs a;
+  a.cur = s.cur;
+  a.stride = s.stride;
+  a.ns = s.n;
+  a.rows = rows;
+  a.cols = cols;
+  a.lf = lf;
+  a.I = I;
+  a.J = J;
+  a.B = B;
+  a.threshold = threshold;
+  a.count = count;
+  a.stats = stats;
+  a.total = total;
+  fisher_kernel<<<grid_for(s.n, 256, 8), 256, 0, st>>>(a, K1, K2);
+  return after_launch();
+}
+
 cudaError_t launch_create31(const uint32_t seed[6], uint64_t n, const DevStreams& s,
                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -677,6 +701,7 @@ cudaError_t preload_kernels() {
   bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<MRG_RAW, MRG_U32>) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, create31_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, fisher_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump31_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;

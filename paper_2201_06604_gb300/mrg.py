@@ -107,6 +107,10 @@ def _load():
         "mrg_get_state": ([sp, u32p, vp], i32),
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+        "mrg_fisher_scratch_bytes": ([u64], u64),
+        "mrg_fisher_sim": ([sp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
+                            u64, vp, u64, vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
+                            vp], i32),
         "mrg31k3p_seed_check": ([u32p], i32),
         "mrg31k3p_create_streams": ([u32p, u64, sp, u32p, vp], i32),
         "mrg31k3p_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
@@ -480,6 +484,33 @@ def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream
         _check(lib.mrg_fused_pi_normsum(streams.ptr(), draws, count.data_ptr(), sum_.data_ptr(),
                                         _stream_handle(stream)))
     return count, sum_
+
+
+def fisher_sim(streams: Streams, table, B: int, return_stats: bool = False, stream=None) -> dict:
+    """Monte Carlo Fisher's exact test (Sec. 4, fisher.sim): B random tables
+    with the margins of `table` (I x J integers), replicate b on stream
+    b mod streams.n.  Returns dict(p_value=(1+count)/(B+1), count, threshold,
+    B[, stats = device tensor of the B statistics])."""
+    _need_mrg32k3a(streams, "fisher_sim")
+    t = np.ascontiguousarray(np.asarray(table), dtype=np.int32)
+    if t.ndim != 2:
+        raise ValueError("table must be 2-D")
+    I, J = t.shape
+    total = int(t.sum())
+    nbytes = int(lib.mrg_fisher_scratch_bytes(total))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=streams.device)
+    stats = torch.empty(max(B, 1), dtype=torch.float64, device=streams.device) if return_stats else None
+    cnt, thr = ctypes.c_uint64(), ctypes.c_double()
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_fisher_sim(streams.ptr(), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  I, J, B, scratch.data_ptr(), nbytes,
+                                  stats.data_ptr() if return_stats else None, ctypes.byref(cnt),
+                                  ctypes.byref(thr), _stream_handle(stream)))
+    out = {"p_value": (1 + cnt.value) / (B + 1), "count": int(cnt.value),
+           "threshold": thr.value, "B": B}
+    if return_stats:
+        out["stats"] = stats[:B]
+    return out
 
 
 _DT_CODE = {"u32": U32, "f32": F32, "f64": F64}
