@@ -61,26 +61,64 @@ __device__ __noinline__ int32_t hyper_inv_exact(int32_t S, int32_t K, int32_t R,
   return hi;
 }
 
-// a / b for exact floats a, b (integers below 2^24) as a double-float.
-__device__ __forceinline__ df df_quot(float a, float b) {
-  const float h = __fdiv_rn(a, b);
-  const float r = __fmaf_rn(-h, b, a);     // exact remainder
-  return df{h, __fdiv_rn(r, b)};
+__device__ __forceinline__ double df_value(df v) { return (double)v.hi + (double)v.lo; }
+
+// x * y for floats as an exact double-float (FMA error-free product).
+__device__ __forceinline__ df two_prod(float x, float y) {
+  const float p = __fmul_rn(x, y);
+  return df{p, __fmaf_rn(x, y, -p)};
 }
 
-__device__ __forceinline__ double df_value(df v) { return (double)v.hi + (double)v.lo; }
+// (a1 a2) / (b1 b2) for exact floats (integers below 2^24) as a double-float:
+// exact numerator and denominator products, one reciprocal, one correction
+// step (relative error ~2^-45).
+__device__ __forceinline__ df df_ratio(float a1, float a2, float b1, float b2) {
+  const df num = two_prod(a1, a2), den = two_prod(b1, b2);
+  const float rc = __frcp_rn(den.hi);
+  const float q1 = __fmul_rn(num.hi, rc);
+  // num - q1 den, exactly enough: q1 den as a double-float
+  const df t = df_mul_f(den, q1);
+  const df r = df_add(num, df_neg(t));
+  return fast_two_sum(q1, __fmul_rn(r.hi, rc));
+}
+
+// exp(x) for x in [-80, 0] as a double-float (relative error ~2^-38): x = k ln 2
+// + r in fp64, exp(r / 256) by its Taylor series to the fifth power, squared
+// eight times, scaled by 2^k.
+__device__ __forceinline__ df df_exp(double x) {
+  const double k = rint(x * 1.4426950408889634);
+  const double r = (x - k * 0.6931471805599453) - k * 2.3190468138462996e-17;  // |r| < 0.35
+  const double rs = r * 0x1p-8;
+  const float rh = (float)rs;
+  const df t{rh, (float)(rs - (double)rh)};
+  // 1 + t + t^2/2 + t^3/6 + t^4/24 + t^5/120, |t| < 0.0014
+  df e = df_add(df{1.0f, 0.0f}, t);
+  df tp = df_mul(t, t);
+  e = df_add(e, df{tp.hi * 0.5f, tp.lo * 0.5f});
+  const float tf = t.hi;
+  const float tail = __fmul_rn(tp.hi, __fmul_rn(tf, __fmaf_rn(tf, __fmaf_rn(tf, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f)));
+  e = df_add(e, df{tail, 0.0f});
+#pragma unroll
+  for (int i = 0; i < 8; ++i) e = df_mul(e, e);
+  const float sc = __int_as_float((127 + (int)k) << 23);   // 2^k, k in [-115, 0]
+  return df{e.hi * sc, e.lo * sc};
+}
+
+// v <= u for a double-float v and a double u given as a double-float.
+__device__ __forceinline__ bool df_le(df v, df u) { return v.hi < u.hi || (v.hi == u.hi && v.lo <= u.lo); }
 
 // Smallest x with u <= F(x) for the number of marked items in R draws without
 // replacement from S items of which K are marked (0 <= K, R <= S), S < 2^24.
 //
-// Fast path: P(m) at the mode from the log-factorial table (fp64, one exp);
-// F(m) by summing the pmf down from m until the terms vanish against it;
-// then a walk down (u <= F(m)) or up (u > F(m)), the pmf following its ratio
-// recursion -- all in double-float arithmetic on the FP32 pipe (~2^-47
-// relative per operation; GB300's FP64 pipe is a small fraction of its FP32
-// rate).  The fast result is kept only if u lies more than 2^-32 from both
-// CDF values that bracket it, far beyond the rounding of either evaluation;
-// otherwise the exact fp64 path decides.  So the decision is the fp64 one.
+// Fast path: log P(m) at the mode from the log-factorial table (fp64: the
+// terms cancel down from ~S ln S), P(m) = exp of it, F(m) by summing the pmf
+// down from m until the terms vanish against it, then a walk down
+// (u <= F(m)) or up (u > F(m)), the pmf following its ratio recursion -- all
+// but the log sum in double-float arithmetic on the FP32 pipe (GB300's FP64
+// rate is a small fraction of its FP32 rate).  The fast result is kept only
+// if u lies at least 2^-32 from both CDF values that bracket it -- far beyond
+// the ~1e-11 error of either evaluation; otherwise the exact fp64 path
+// decides.  So the decision is the fp64 one.
 __device__ __forceinline__ int32_t hyper_inv(int32_t S, int32_t K, int32_t R, double u,
                                              const double* __restrict__ lf) {
   const int32_t lo = max(0, R - (S - K));
@@ -89,40 +127,41 @@ __device__ __forceinline__ int32_t hyper_inv(int32_t S, int32_t K, int32_t R, do
   const int32_t SKR = S - K - R;
   int32_t m = (int32_t)(((int64_t)(R + 1) * (K + 1)) / (S + 2));
   m = min(max(m, lo), hi);
-  const double pm64 = exp(hyper_logpmf(S, K, R, m, lf));
-  const float pm_hi = (float)pm64;
-  const df pm{pm_hi, (float)(pm64 - (double)pm_hi)};
-  // P(x - 1) / P(x) = [x / (K - x + 1)] [(SKR + x) / (R - x + 1)]
-  auto down = [&](int32_t x) {
-    return df_mul(df_quot((float)x, (float)(K - x + 1)),
-                  df_quot((float)(SKR + x), (float)(R - x + 1)));
-  };
-  // P(x + 1) / P(x) = [(K - x) / (x + 1)] [(R - x) / (SKR + x + 1)]
-  auto up = [&](int32_t x) {
-    return df_mul(df_quot((float)(K - x), (float)(x + 1)),
-                  df_quot((float)(R - x), (float)(SKR + x + 1)));
-  };
+  const df pm = df_exp(hyper_logpmf(S, K, R, m, lf));
+  const float uh = (float)u;
+  const df ud{uh, (float)(u - (double)uh)};
+  // P(x - 1) / P(x) = x (SKR + x) / ((K - x + 1) (R - x + 1)); the four
+  // integer factors are kept as floats (exact below 2^24) and stepped by one
   df F = pm, q = pm;
-  for (int32_t x = m; x > lo; --x) {
-    q = df_mul(q, down(x));
-    F = df_add(F, q);
-    if (q.hi <= F.hi * 0x1p-60f) break;
+  {
+    float a = (float)m, b = (float)(SKR + m), c = (float)(K - m + 1), d = (float)(R - m + 1);
+    for (int32_t x = m; x > lo; --x) {
+      q = df_mul(q, df_ratio(a, b, c, d));
+      F = df_add(F, q);
+      if (q.hi <= F.hi * 0x1p-60f) break;
+      a -= 1.0f; b -= 1.0f; c += 1.0f; d += 1.0f;
+    }
   }
   int32_t x = m;
   df px = pm, Fx = F;
-  if (df_value(F) >= u) {  // walk down while u <= F(x - 1) = F(x) - P(x)
+  if (df_le(ud, F)) {      // walk down while u <= F(x - 1) = F(x) - P(x)
+    float a = (float)m, b = (float)(SKR + m), c = (float)(K - m + 1), d = (float)(R - m + 1);
     while (x > lo) {
       const df Fprev = df_add(Fx, df_neg(px));
-      if (u > df_value(Fprev)) break;
-      px = df_mul(px, down(x));
+      if (!df_le(ud, Fprev)) break;
+      px = df_mul(px, df_ratio(a, b, c, d));
       Fx = Fprev;
       --x;
+      a -= 1.0f; b -= 1.0f; c += 1.0f; d += 1.0f;
     }
-  } else {                 // walk up while F(x) < u
-    while (x < hi && df_value(Fx) < u) {
-      px = df_mul(px, up(x));
+  } else {                 // walk up while F(x) < u:
+    // P(x + 1) / P(x) = (K - x) (R - x) / ((x + 1) (SKR + x + 1))
+    float a = (float)(K - m), b = (float)(R - m), c = (float)(m + 1), d = (float)(SKR + m + 1);
+    while (x < hi && !df_le(ud, Fx)) {
+      px = df_mul(px, df_ratio(a, b, c, d));
       ++x;
       Fx = df_add(Fx, px);
+      a -= 1.0f; b -= 1.0f; c += 1.0f; d += 1.0f;
     }
   }
   // bracket: F(x - 1) < u <= F(x); 0 below the support
