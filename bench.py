@@ -34,7 +34,7 @@ ES = {"f64": 8, "f32": 4, "u32": 4}
 # These kernels are bound by instruction issue (the FP64 pipe is not used and
 # the recurrence is integer multiply-add work), so the dominant kernel's
 # roofline is issue slots: 4 warp-instructions per cycle per SM.
-INSTR_PER_OUTPUT = {("raw", "u32"): 28.8, ("uniform", "f64"): 45.0, ("uniform", "f32"): 49.9,
+INSTR_PER_OUTPUT = {("raw", "u32"): 28.3, ("uniform", "f64"): 44.0, ("uniform", "f32"): 49.4,
                     ("normal", "f64"): 173.7, ("normal", "f32"): 145.4,
                     ("exponential", "f32"): 105.2, ("exponential", "f64"): 133.2}
 SM_COUNT = 152
@@ -452,6 +452,21 @@ def run_gpu(args):
     torch.cuda.synchronize()
     adv_ms = e0.elapsed_time(e1) / 20
 
+    # HBM write bandwidth measured live: a device fill of the whole output
+    # buffer (8 GiB), best of 5 (context for the write-bound variants; the
+    # roofline's peak stays the measured copy bandwidth)
+    write_gbs = None
+    if not args.quick:
+        fills = []
+        for _ in range(5):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            buf.fill_(0)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            fills.append(a0.elapsed_time(a1))
+        write_gbs = buf.numel() / (min(fills) / 1e3) / 1e9
+
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -464,6 +479,8 @@ def run_gpu(args):
         v = {"dist": d, "dtype": dt, "ms": t_kern, "draws_per_s": total_out / t_kern * 1e3,
              "algo_bytes": algo, "gbs": algo / t_kern / 1e6}
         v["hbm_frac"] = v["gbs"] / hbm
+        if write_gbs:
+            v["write_frac"] = v["gbs"] / write_gbs
         ipo = INSTR_PER_OUTPUT.get((d, dt))
         if ipo:
             v["issue_tinst_s"] = ipo * total_out / (t_kern * 1e-3) / 1e12
@@ -604,6 +621,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "outputs (4-8 GiB per variant) larger than L2; no flush"},
         "gbs": bytes_step * world / (per_step_ms / 1e3) / 1e9,
+        "hbm_write_gbs_measured": write_gbs,
         "roofline": roofline(dom, hbm, peak_kind, issue_peak, total_out),
         "variants": variants,
         "tuned": tuned or None,

@@ -266,9 +266,25 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
     TState st = to_offset(st0);
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
     char* gdst = a.out + (s * a.ld + off) * ES;
+    uint32_t i0 = 0;
+    if constexpr (DIST == MRG_RAW || DIST == MRG_UNIFORM) {
+      // Units that every lane of the warp stores whole: no bound checks, a
+      // pointer step (saves about one instruction per output).  Not for the
+      // transforms, whose larger bodies would then exist twice in the code.
+      const uint32_t nfull = __reduce_min_sync(0xffffffffu, cnt) / UE * UE;
+      char* p = gdst;
+#pragma unroll 2
+      for (; i0 < nfull; i0 += UE) {
+        uint32_t wv[UW];
+        produce<DIST, DT, UE>(st, wv, c, s_tab);
+#pragma unroll
+        for (int v = 0; v < UB / VS; ++v) store_vec<VS>(p + v * VS, wv + v * VW);
+        p += UB;
+      }
+    }
 
 #pragma unroll 2
-    for (uint32_t i = 0; i < cmax; i += UE) {
+    for (uint32_t i = i0; i < cmax; i += UE) {
       uint32_t wv[UW];
       produce<DIST, DT, UE>(st, wv, c, s_tab);
       if (i + UE <= cnt) {
