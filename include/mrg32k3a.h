@@ -180,6 +180,15 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- write-bandwidth calibration ---------------------------------------- */
+
+/* Fills out[0 .. n_words) (device, 32-byte aligned, n_words a multiple of 8)
+ * with `value` using the store pattern of the generate kernels (each lane
+ * writes whole 32-byte sectors): a write-only stream whose bandwidth is the
+ * ceiling the materialised generation is measured against.  Not part of the
+ * paper's method.  Errors: MRG_EINVAL, MRG_ECUDA. */
+int mrg_fill_u32(void *out, uint64_t n_words, uint32_t value, void *stream);
+
 /* ---- Monte Carlo Fisher's exact test (Sec. 4) ---------------------------- */
 
 /* Bytes of device scratch mrg_fisher_sim needs for a table whose entries sum

@@ -171,6 +171,17 @@ const std::vector<double>& host_logfact(uint64_t n) {
 
 extern "C" {
 
+int mrg_fill_u32(void* out, uint64_t n_words, uint32_t value, void* stream) {
+  if (n_words == 0) return MRG_OK;
+  if (!out || reinterpret_cast<uintptr_t>(out) % 32 || n_words % 8)
+    return fail(MRG_EINVAL, "out must be 32-byte aligned and n_words a multiple of 8");
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_fill(out, n_words / 8, value, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "fill_kernel");
+  return MRG_OK;
+}
+
 uint64_t mrg_fisher_scratch_bytes(uint64_t n_total) {
   return kFisherHeader + 8 * (n_total + 1);
 }

@@ -53,6 +53,9 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st);
 
+// out[0 .. 32 units) = the word v repeated (32-byte stores; out 32-byte aligned).
+cudaError_t launch_fill(void* out, uint64_t units, uint32_t v, cudaStream_t st);
+
 // Monte Carlo Fisher's exact test (fisher_kernels.cuh): B replicates on the
 // streams of s (replicate b on stream b mod s.n); rows/cols/lf/count in
 // device memory, *count accumulated (not reset), stats optional.

@@ -300,6 +300,19 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Write-only stream (calibration of the HBM write bandwidth the generate
+// kernels are held against): every lane stores 32-byte units, a warp 1 KiB
+// of consecutive memory per step.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) fill_kernel(char* out, uint64_t units, uint32_t v) {
+  const uint32_t w[8] = {v, v, v, v, v, v, v, v};
+  const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < units; i += step_all)
+    store_vec<32>(out + 32 * i, w);
+}
+
+// ---------------------------------------------------------------------------
 // Fused no-store consumer
 // ---------------------------------------------------------------------------
 
@@ -574,6 +587,12 @@ cudaError_t launch_fisher(const DevStreams& s, const int32_t* rows, const int32_
   return after_launch();
 }
 
+cudaError_t launch_fill(void* out, uint64_t units, uint32_t v, cudaStream_t st) {
+  if (units == 0) return cudaSuccess;
+  fill_kernel<<<grid_for(units, 256, 8), 256, 0, st>>>(static_cast<char*>(out), units, v);
+  return after_launch();
+}
+
 cudaError_t launch_create31(const uint32_t seed[6], uint64_t n, const DevStreams& s,
                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -718,6 +737,7 @@ cudaError_t preload_kernels() {
   bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, create31_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, fisher_kernel) != cudaSuccess;
+  bad |= cudaFuncGetAttributes(&a, fill_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump31_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
   bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;

@@ -107,6 +107,7 @@ def _load():
         "mrg_get_state": ([sp, u32p, vp], i32),
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
+        "mrg_fill_u32": ([vp, u64, ctypes.c_uint32, vp], i32),
         "mrg_fisher_scratch_bytes": ([u64], u64),
         "mrg_fisher_sim": ([sp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
                             u64, vp, u64, vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
@@ -484,6 +485,16 @@ def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream
         _check(lib.mrg_fused_pi_normsum(streams.ptr(), draws, count.data_ptr(), sum_.data_ptr(),
                                         _stream_handle(stream)))
     return count, sum_
+
+
+def fill_u32(t: torch.Tensor, value: int = 0, stream=None):
+    """Writes `value` into every 32-bit word of a device tensor (32-byte
+    aligned, size a multiple of 32 bytes) with the library's write-only
+    stream kernel."""
+    nbytes = t.numel() * t.element_size()
+    with torch.cuda.device(t.device):
+        _check(lib.mrg_fill_u32(t.data_ptr(), nbytes // 4, value, _stream_handle(stream)))
+    return t
 
 
 def fisher_sim(streams: Streams, table, B: int, return_stats: bool = False, stream=None) -> dict:

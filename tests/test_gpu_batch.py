@@ -237,3 +237,33 @@ def test_back_to_back_runs_without_sync(M):
             for q, a in zip(reqs, ref):
                 assert torch.equal(q["out"], a), (mode, q)
     b.close()
+
+
+def test_full_size_batch_sampled(M):
+    """The 4096-request workload (lengths log-uniform in [1e2, 1e6], mixed
+    variants, request r on stream r, substream 1) in one tuned batched launch:
+    sampled requests against the oracle, all of them against plain
+    single-stream generation."""
+    reqs = W.batched_requests(4096)
+    for q in reqs:
+        q["dist"] = {1: "uniform", 2: "normal", 3: "exponential"}[q["dist"]]
+        q["offset"] = 0
+    s = M.create_streams(len(reqs), seed=SEED)
+    start, _ = O.create_streams(SEED, len(reqs))
+    M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=len(reqs), max_tiles=1 << 17)
+    b.tune(reqs, reps=1)
+    b.run(reqs)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    for r in list(rng.choice(len(reqs), 24, replace=False)) + [int(np.argmax([q["n"] for q in reqs]))]:
+        q = reqs[r]
+        check_close(q["out"].cpu().numpy(), oracle_request(start, q), q)
+    # every request equals plain generation from the same position
+    dt = {"f32": torch.float32, "f64": torch.float64}
+    M.substream_next(s)
+    for r in range(0, len(reqs), 97):
+        q = reqs[r]
+        p = M.generate(s.view(r, 1), q["n"], q["dist"], dt[q["dtype"]])[0]
+        assert torch.equal(p, q["out"]), q
+    b.close()

@@ -130,3 +130,24 @@ def test_mrg32k3a_only_calls_refuse_mrg31k3p_streams(M):
         M.Batch(s)
     with pytest.raises(M.MrgError):                      # a word >= 2^31 - 1 is not a state
         M.create_streams(1, seed=(2147483647, 1, 1, 1, 1, 1), generator="mrg31k3p")
+
+
+@pytest.mark.parametrize("dist,dtype", [("uniform", torch.float64), ("normal", torch.float64),
+                                        ("uniform", torch.float32)])
+def test_materialised_full_size_sampled(M, dist, dtype):
+    from paper_2201_06604_gb300 import workloads as W
+    ns, n = W.MATERIALISED["streams"], W.MATERIALISED["draws"]
+    s = M.create_streams(ns, seed=SEED, generator="mrg31k3p")
+    out = M.generate(s, n, dist, dtype)
+    torch.cuda.synchronize()
+    sample = [0, 1, 31, 32, 4095, 40000, ns - 1]
+    st0, _ = O.create_streams(SEED, ns, gen=G)
+    got = out.index_select(0, torch.tensor(sample, device="cuda")).cpu().numpy()
+    ref, after = O.generate_streams(st0[sample], n, DISTS[dist], f32=dtype == torch.float32,
+                                    nthreads=8, gen=G)
+    if dist == "uniform":
+        assert np.array_equal(got, ref)
+    else:
+        assert np.abs(got - ref).max() <= 1e-12
+    assert np.array_equal(states(M, s)[sample], after)
+    del out

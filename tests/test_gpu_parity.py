@@ -308,3 +308,15 @@ def test_generate_host_matches_device(M, dist, dtype):
     assert np.array_equal(got[:, :n], want)
     assert (got[:, n:] == -1).all()
     assert np.array_equal(M.get_state(a), M.get_state(b))
+
+
+def test_fill_writes_every_word(M):
+    t = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    M.fill_u32(t[8:8 + 4096], 0x12345678)
+    torch.cuda.synchronize()
+    h = t.cpu().numpy()
+    assert (h[8:8 + 4096] == 0x12345678).all() and (h[:8] == 0).all() and (h[8 + 4096:] == 0).all()
+    with pytest.raises(M.MrgError):
+        M.fill_u32(t[1:9])                       # not 32-byte aligned
+    with pytest.raises(M.MrgError):
+        M.fill_u32(t[8:12])                      # not a whole 32-byte unit
