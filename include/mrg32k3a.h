@@ -180,6 +180,32 @@ int mrg_set_state(const mrg_streams *s, const uint32_t *host, void *stream);
 int mrg_fused_pi_normsum(const mrg_streams *s, uint64_t draws, int64_t *count, double *sum,
                          void *stream);
 
+/* ---- the paper's matrix layout (compatibility mode) --------------------- */
+
+#define MRG_GEN_MRG32K3A 0
+#define MRG_GEN_MRG31K3P 1
+
+/* runifGpu / rexpGpu with an explicit work-item grid (Sec. 2.2, Listing 1;
+ * Sec. 3.2): a gsize0 x gsize1 grid of work items (the paper's Nglobal) fills
+ * the nrow x ncol row-major matrix out (device; element (r, c) at
+ * out[r * ld + c]).  Work item (i0, i1) uses stream i0 * gsize1 + i1 of `s`
+ * (s->n >= gsize0 * gsize1) and visits rows i0, i0 + gsize0, ... and, in
+ * each, columns i1, i1 + gsize1, ... of the matrix padded to
+ * ceil(ncol / gsize1) * gsize1 columns, taking one draw per visited position
+ * and writing only the real columns; a vector of n values is the n x 1
+ * matrix.  This is the reading under which the paper's printed runifGpu and
+ * rexpGpu examples are reproduced (its text and listings disagree on the
+ * stream map and the padding).  generator: MRG_GEN_MRG32K3A or
+ * MRG_GEN_MRG31K3P (the paper's).  dist: MRG_RAW (MRG_U32), MRG_UNIFORM or
+ * MRG_EXPONENTIAL (MRG_F32 / MRG_F64); normals are refused (the paper pairs
+ * two work items' streams for them, tying values to the grid -- mrg_generate
+ * pairs draws within a stream).  Unlike mrg_generate the output depends on
+ * the grid, and each work item runs on one thread (no memory-bandwidth
+ * design).  Errors: MRG_EINVAL, MRG_ERANGE, MRG_ECUDA. */
+int mrg_generate_matrix(const mrg_streams *s, int generator, uint64_t nrow, uint64_t ncol,
+                        uint32_t gsize0, uint32_t gsize1, int dist, int dtype, double rate,
+                        void *out, uint64_t ld, void *stream);
+
 /* ---- write-bandwidth calibration ---------------------------------------- */
 
 /* Fills out[0 .. n_words) (device, 32-byte aligned, n_words a multiple of 8)

@@ -171,6 +171,38 @@ const std::vector<double>& host_logfact(uint64_t n) {
 
 extern "C" {
 
+int mrg_generate_matrix(const mrg_streams* s, int generator, uint64_t nrow, uint64_t ncol,
+                        uint32_t gsize0, uint32_t gsize1, int dist, int dtype, double rate,
+                        void* out, uint64_t ld, void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (generator != MRG_GEN_MRG32K3A && generator != MRG_GEN_MRG31K3P)
+    return fail(MRG_EINVAL, "unknown generator");
+  if (dist == MRG_NORMAL)
+    return fail(MRG_EINVAL, "normals are not generated in the matrix layout (the paper pairs "
+                            "two work items' streams there); use mrg_generate");
+  const bool pair_ok = (dist == MRG_RAW && dtype == MRG_U32) ||
+                       ((dist == MRG_UNIFORM || dist == MRG_EXPONENTIAL) &&
+                        (dtype == MRG_F32 || dtype == MRG_F64));
+  if (!pair_ok) return fail(MRG_EINVAL, "unsupported dist/dtype combination");
+  if (dist == MRG_EXPONENTIAL && !(rate >= 0x1p-64 && rate <= 0x1p64))
+    return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+  if (gsize0 == 0 || gsize1 == 0) return fail(MRG_EINVAL, "empty work-item grid");
+  if ((uint64_t)gsize0 * gsize1 > s->n) return fail(MRG_EINVAL, "fewer streams than work items");
+  if ((uint64_t)gsize0 * gsize1 > (1ull << 31)) return fail(MRG_ERANGE, "work-item grid too large");
+  if (nrow == 0 || ncol == 0) return MRG_OK;
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  if (ld < ncol) return fail(MRG_EINVAL, "ld < ncol");
+  if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
+    return fail(MRG_EINVAL, "out is not aligned to its element size");
+  if (nrow > (1ull << 40) || ld > (1ull << 40)) return fail(MRG_ERANGE, "size too large");
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaError_t e = mrg::launch_matrix(generator == MRG_GEN_MRG31K3P, s->cur, s->stride, nrow, ncol,
+                                     gsize0, gsize1, dist, dtype, rate, out, ld, cs(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "matrix_kernel");
+  return MRG_OK;
+}
+
 int mrg_fill_u32(void* out, uint64_t n_words, uint32_t value, void* stream) {
   if (n_words == 0) return MRG_OK;
   if (!out || reinterpret_cast<uintptr_t>(out) % 32 || n_words % 8)

@@ -53,6 +53,13 @@ cudaError_t launch_generate(const DevStreams& s, uint64_t n, int dist, int dtype
 cudaError_t launch_fused(const DevStreams& s, uint64_t pairs, int64_t* count, double* sum,
                          cudaStream_t st);
 
+// The paper's matrix layout (matrix_kernels.cuh): a g0 x g1 grid of work
+// items, item t on stream t, fills an nrow x ncol row-major matrix (leading
+// dimension ld); dist RAW / UNIFORM / EXPONENTIAL.
+cudaError_t launch_matrix(bool g31, uint32_t* cur, uint64_t stride, uint64_t nrow, uint64_t ncol,
+                          uint32_t g0, uint32_t g1, int dist, int dtype, double rate, void* out,
+                          uint64_t ld, cudaStream_t st);
+
 // out[0 .. 32 units) = the word v repeated (32-byte stores; out 32-byte aligned).
 cudaError_t launch_fill(void* out, uint64_t units, uint32_t v, cudaStream_t st);
 

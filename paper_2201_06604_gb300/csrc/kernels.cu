@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
 #include "serve_kernels.cuh"
 #include "gen31_kernels.cuh"
 #include "fisher_kernels.cuh"
+#include "matrix_kernels.cuh"
 
 namespace mrg {
 
@@ -585,6 +586,45 @@ cudaError_t launch_fisher(const DevStreams& s, const int32_t* rows, const int32_
   a.total = total;
   fisher_kernel<<<grid_for(s.n, 256, 8), 256, 0, st>>>(a, K1, K2);
   return after_launch();
+}
+
+namespace {
+template <bool G31, int DIST, int DT>
+cudaError_t launch_matrix_t(const MatrixArgs& a, cudaStream_t st) {
+  const uint64_t items = (uint64_t)a.g0 * a.g1;
+  matrix_kernel<G31, DIST, DT><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a, K1, K2);
+  return after_launch();
+}
+template <bool G31>
+cudaError_t launch_matrix_g(const MatrixArgs& a, int dist, int dtype, cudaStream_t st) {
+  switch (dist * 4 + dtype) {
+    case MRG_RAW * 4 + MRG_U32: return launch_matrix_t<G31, MRG_RAW, MRG_U32>(a, st);
+    case MRG_UNIFORM * 4 + MRG_F32: return launch_matrix_t<G31, MRG_UNIFORM, MRG_F32>(a, st);
+    case MRG_UNIFORM * 4 + MRG_F64: return launch_matrix_t<G31, MRG_UNIFORM, MRG_F64>(a, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F32: return launch_matrix_t<G31, MRG_EXPONENTIAL, MRG_F32>(a, st);
+    case MRG_EXPONENTIAL * 4 + MRG_F64: return launch_matrix_t<G31, MRG_EXPONENTIAL, MRG_F64>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+cudaError_t launch_matrix(bool g31, uint32_t* cur, uint64_t stride, uint64_t nrow, uint64_t ncol,
+                          uint32_t g0, uint32_t g1, int dist, int dtype, double rate, void* out,
+                          uint64_t ld, cudaStream_t st) {
+  MatrixArgs a;
+  a.cur = cur;
+  a.stride = stride;
+  a.nrow = nrow;
+  a.ncol = ncol;
+  a.npad = (ncol + g1 - 1) / g1 * g1;
+  a.g0 = g0;
+  a.g1 = g1;
+  a.out = static_cast<char*>(out);
+  a.ld = ld;
+  const double ir = dist == MRG_EXPONENTIAL ? -1.0 / rate : 0.0;
+  a.ir_hi = (float)ir;
+  a.ir_lo = (float)(ir - (double)a.ir_hi);
+  return g31 ? launch_matrix_g<true>(a, dist, dtype, st) : launch_matrix_g<false>(a, dist, dtype, st);
 }
 
 cudaError_t launch_fill(void* out, uint64_t units, uint32_t v, cudaStream_t st) {

@@ -108,6 +108,8 @@ def _load():
         "mrg_set_state": ([sp, u32p, vp], i32),
         "mrg_fused_pi_normsum": ([sp, u64, vp, vp, vp], i32),
         "mrg_fill_u32": ([vp, u64, ctypes.c_uint32, vp], i32),
+        "mrg_generate_matrix": ([sp, i32, u64, u64, ctypes.c_uint32, ctypes.c_uint32, i32, i32,
+                                 ctypes.c_double, vp, u64, vp], i32),
         "mrg_fisher_scratch_bytes": ([u64], u64),
         "mrg_fisher_sim": ([sp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
                             u64, vp, u64, vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
@@ -485,6 +487,26 @@ def fused_pi_normsum(streams: Streams, draws: int, count=None, sum_=None, stream
         _check(lib.mrg_fused_pi_normsum(streams.ptr(), draws, count.data_ptr(), sum_.data_ptr(),
                                         _stream_handle(stream)))
     return count, sum_
+
+
+def generate_matrix(streams: Streams, shape, nglobal=(2, 2), dist="uniform",
+                    dtype=torch.float64, rate: float = 1.0, out=None, stream=None) -> torch.Tensor:
+    """The paper's runifGpu / rexpGpu layout (Sec. 2.2): `shape` is n (a
+    vector) or (nrow, ncol); nglobal the work-item grid.  Returns a tensor of
+    that shape (row-major)."""
+    nrow, ncol = (int(shape), 1) if np.ndim(shape) == 0 else (int(shape[0]), int(shape[1]))
+    d = _DIST[dist] if isinstance(dist, str) else int(dist)
+    dt = torch.int32 if d == RAW else dtype
+    if out is None:
+        out = torch.empty((nrow, ncol), dtype=dt, device=streams.device)
+    if out.dim() != 2 or out.shape[0] < nrow or out.shape[1] < ncol or out.stride(1) != 1:
+        raise ValueError("out must be [>= nrow, >= ncol] with unit column stride")
+    gen = 1 if streams.generator == "mrg31k3p" else 0
+    with torch.cuda.device(streams.device):
+        _check(lib.mrg_generate_matrix(streams.ptr(), gen, nrow, ncol, int(nglobal[0]),
+                                       int(nglobal[1]), d, _dtype_code(d, dt), float(rate),
+                                       out.data_ptr(), out.stride(0), _stream_handle(stream)))
+    return out[:, 0] if np.ndim(shape) == 0 else out
 
 
 def fill_u32(t: torch.Tensor, value: int = 0, stream=None):
