@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -79,6 +80,12 @@ mrg::DevStreams dev(const mrg_streams* s) {
 
 inline cudaStream_t cs(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 
+// rows x leading dimension x element size stays addressable (< 2^62 bytes).
+bool extent_ok(uint64_t rows, uint64_t ld, uint64_t es) {
+  const unsigned __int128 bytes = (unsigned __int128)rows * ld * es;
+  return bytes < ((unsigned __int128)1 << 62);
+}
+
 }  // namespace
 
 namespace mrg {
@@ -136,7 +143,8 @@ int mrg_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, double r
   if (ld < n) return fail(MRG_EINVAL, "ld < n");
   if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
     return fail(MRG_EINVAL, "out is not aligned to its element size");
-  if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
+  if (n > (1ull << 62) || !extent_ok(s->n, ld, dtype == MRG_F64 ? 8 : 4))
+    return fail(MRG_ERANGE, "size too large");
   int rc = ensure_device();
   if (rc) return rc;
   const mrg::GenConfig cfg = mrg::generate_config_for(dist, dtype, s->n, n);
@@ -158,14 +166,21 @@ namespace {
 
 constexpr uint64_t kFisherHeader = 1024;  // count (8 B), rows, cols (4 B each, <= 64)
 
-// log(k!) for k = 0..n on the host (lgamma), grown on demand and kept.
-const std::vector<double>& host_logfact(uint64_t n) {
+// log(k!) for k = 0..n on the host (lgamma).  The table is shared and grown
+// by replacement: a caller keeps its own reference while it copies, so a
+// concurrent call that needs a longer table never frees one in use.
+std::shared_ptr<const std::vector<double>> host_logfact(uint64_t n) {
   static std::mutex mu;
-  static std::vector<double> lf;
+  static std::shared_ptr<const std::vector<double>> table;
   std::lock_guard<std::mutex> lk(mu);
-  for (uint64_t k = lf.size(); k <= n; ++k) lf.push_back(std::lgamma((double)k + 1.0));
-  return lf;
+  if (!table || table->size() <= n) {
+    auto grown = std::make_shared<std::vector<double>>(table ? *table : std::vector<double>{});
+    for (uint64_t k = grown->size(); k <= n; ++k) grown->push_back(std::lgamma((double)k + 1.0));
+    table = grown;
+  }
+  return table;
 }
+
 
 }  // namespace
 
@@ -194,7 +209,7 @@ int mrg_generate_matrix(const mrg_streams* s, int generator, uint64_t nrow, uint
   if (ld < ncol) return fail(MRG_EINVAL, "ld < ncol");
   if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
     return fail(MRG_EINVAL, "out is not aligned to its element size");
-  if (nrow > (1ull << 40) || ld > (1ull << 40)) return fail(MRG_ERANGE, "size too large");
+  if (!extent_ok(nrow, ld, dtype == MRG_F64 ? 8 : 4)) return fail(MRG_ERANGE, "size too large");
   int rc = ensure_device();
   if (rc) return rc;
   cudaError_t e = mrg::launch_matrix(generator == MRG_GEN_MRG31K3P, s->cur, s->stride, nrow, ncol,
@@ -243,7 +258,8 @@ int mrg_fisher_sim(const mrg_streams* s, const int32_t* table, uint32_t I, uint3
   if (stats && reinterpret_cast<uintptr_t>(stats) % 8) return fail(MRG_EINVAL, "stats misaligned");
   int rc = ensure_device();
   if (rc) return rc;
-  const std::vector<double>& lf = host_logfact((uint64_t)total);
+  const std::shared_ptr<const std::vector<double>> lfp = host_logfact((uint64_t)total);
+  const std::vector<double>& lf = *lfp;
   // the observed statistic, -sum log(n_ij!) row by row; "at or below" it is
   // taken with a relative allowance of 64 ulp, so that a table whose
   // statistic equals it mathematically counts whatever its rounding
@@ -322,7 +338,8 @@ int mrg31k3p_generate(const mrg_streams* s, uint64_t n, int dist, int dtype, dou
   if (ld < n) return fail(MRG_EINVAL, "ld < n");
   if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
     return fail(MRG_EINVAL, "out is not aligned to its element size");
-  if (n > (1ull << 62) || ld > (1ull << 62)) return fail(MRG_ERANGE, "size too large");
+  if (n > (1ull << 62) || !extent_ok(s->n, ld, dtype == MRG_F64 ? 8 : 4))
+    return fail(MRG_ERANGE, "size too large");
   int rc = ensure_device();
   if (rc) return rc;
   cudaError_t e = mrg::launch_generate31(dev(s), n, dist, dtype, rate, out, ld, mrg::GenConfig{},

@@ -95,7 +95,9 @@ int check_generate_args(const mrg_streams* s, uint64_t n, int dist, int dtype, d
   if (ld < n) return mrg::set_error(MRG_EINVAL, "ld < n");
   if (reinterpret_cast<uintptr_t>(out) % (dtype == MRG_F64 ? 8 : 4))
     return mrg::set_error(MRG_EINVAL, "out is not aligned to its element size");
-  if (n > (1ull << 62) || ld > (1ull << 62)) return mrg::set_error(MRG_ERANGE, "size too large");
+  const unsigned __int128 bytes = (unsigned __int128)s->n * ld * (dtype == MRG_F64 ? 8 : 4);
+  if (n > (1ull << 62) || bytes >= ((unsigned __int128)1 << 62))
+    return mrg::set_error(MRG_ERANGE, "size too large");
   return MRG_OK;
 }
 

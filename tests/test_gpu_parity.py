@@ -320,3 +320,13 @@ def test_fill_writes_every_word(M):
         M.fill_u32(t[1:9])                       # not 32-byte aligned
     with pytest.raises(M.MrgError):
         M.fill_u32(t[8:12])                      # not a whole 32-byte unit
+
+
+def test_unaddressable_extent_is_rejected(M):
+    # 4 streams with a row pitch of 2^60 fp64 elements would span 2^65 bytes:
+    # refused before any device work
+    s = M.create_streams(4, seed=SEED)
+    out = torch.empty(64, dtype=torch.float64, device="cuda")
+    rc = M.lib.mrg_generate(s.ptr(), 8, M.UNIFORM, M.F64, 1.0, out.data_ptr(), 1 << 60,
+                            torch.cuda.current_stream().cuda_stream)
+    assert rc == M.ERANGE
