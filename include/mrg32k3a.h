@@ -477,8 +477,12 @@ int mrg_server_create(const mrg_streams *s, void *arena, uint64_t arena_bytes,
  * The request's tiles enter the worker's ring in chunks, round-robin with the
  * other requests in flight, on this call and on every later submit and poll:
  * keep polling while requests are in flight.
+ * A request starts entering the ring, in arrival order, once the ring can
+ * hold all of its tiles beside the tiles still to come of the requests
+ * already started (so every started request can finish).
  * Errors: MRG_EBUSY (no free slot or arena memory -- retry after releasing
- * finished requests), MRG_EINVAL, MRG_ERANGE (larger than the arena),
+ * finished requests), MRG_EINVAL, MRG_ERANGE (larger than the arena, or more
+ * tiles than ring_tiles),
  * MRG_ETIMEOUT (the worker has stopped), MRG_ECUDA. */
 int mrg_server_submit(mrg_server *sv, const mrg_request *req, uint64_t *id, void **out);
 

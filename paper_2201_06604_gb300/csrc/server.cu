@@ -85,8 +85,10 @@ struct mrg_server {
     bool done;
   };
   std::unordered_map<uint64_t, Inflight> inflight;  // id -> state
-  std::multiset<uint64_t> ring_firsts;               // first ring positions of undone requests
-  std::deque<uint64_t> emit_queue;                   // ids with tiles still to emit
+  std::multiset<uint64_t> ring_firsts;               // first ring positions of started, undone requests
+  std::deque<uint64_t> start_queue;                  // admitted ids with no tile emitted yet (FIFO)
+  std::deque<uint64_t> emit_queue;                   // started ids with tiles still to emit
+  uint64_t reserved = 0;                             // tiles of started requests not yet emitted
   // feeder thread: keeps the ring's backlog topped up while tiles are pending
   std::thread feeder;
   std::atomic<bool> quit{false};
@@ -139,10 +141,30 @@ void arena_free(mrg_server* sv, uint64_t off, uint64_t size) {
   }
 }
 
-// Appends chunks of pending tiles to the ring, round-robin over requests,
-// while there is ring space, and publishes the new tail.
+// Starts admitted requests in arrival order, appends chunks of their tiles to
+// the ring round-robin while there is ring space, and publishes the new tail.
+//
+// A ring position is reused only once the request whose first tile lies at
+// or before it has completed.  A request therefore starts only when the ring
+// can hold all of its tiles together with every tile still to be emitted for
+// the requests already started -- otherwise large requests emitted round-robin
+// could fill the ring with their first chunks, none could emit its last tile,
+// none would complete, and nothing could move (observed under saturation
+// before this rule).  Started requests can always finish emitting, so the
+// oldest completes and frees the ring behind it.
 int pump(mrg_server* sv) {
-  const uint64_t ring_low = sv->ring_firsts.empty() ? sv->tail : *sv->ring_firsts.begin();
+  uint64_t ring_low = sv->ring_firsts.empty() ? sv->tail : *sv->ring_firsts.begin();
+  while (!sv->start_queue.empty()) {
+    const uint64_t id = sv->start_queue.front();
+    auto& f = sv->inflight[id];
+    if ((sv->tail - ring_low) + sv->reserved + f.ntiles > sv->ring_tiles) break;
+    sv->start_queue.pop_front();
+    sv->reserved += f.ntiles;
+    f.ring_first = sv->tail;              // its first tile lands at or after this position
+    sv->ring_firsts.insert(f.ring_first);
+    sv->emit_queue.push_back(id);
+    ring_low = *sv->ring_firsts.begin();
+  }
   uint64_t space = sv->ring_tiles - (sv->tail - ring_low);
   const uint64_t claimed = *reinterpret_cast<volatile unsigned long long*>(sv->head_h);
   const uint64_t backlog = sv->tail > claimed ? sv->tail - claimed : 0;
@@ -154,15 +176,12 @@ int pump(mrg_server* sv) {
     sv->emit_queue.pop_front();
     auto& f = sv->inflight[id];
     const uint64_t k = std::min<uint64_t>(std::min<uint64_t>(kChunk, f.ntiles - f.emitted), space);
-    if (f.emitted == 0) {
-      f.ring_first = sv->tail;
-      sv->ring_firsts.insert(sv->tail);
-    }
     for (uint64_t i = 0; i < k; ++i)
       sv->ring_h[(sv->tail + i) & (sv->ring_tiles - 1)] =
           mrg::ServeTileHost{f.slot, (uint32_t)(32 * (f.emitted + i)), (uint32_t)f.ntiles, f.seq};
     f.emitted += k;
     sv->tail += k;
+    sv->reserved -= k;
     space -= k;
     if (f.emitted < f.ntiles) sv->emit_queue.push_back(id);
     if (turns == 0 && space > 0 && !sv->emit_queue.empty()) turns = sv->emit_queue.size();
@@ -232,8 +251,9 @@ void feeder_main(mrg_server* sv) {
     bool pending;
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      if (sv->running && !sv->emit_queue.empty()) pump(sv);
-      pending = !sv->emit_queue.empty();
+      const bool work = !sv->emit_queue.empty() || !sv->start_queue.empty();
+      if (sv->running && work) pump(sv);
+      pending = !sv->emit_queue.empty() || !sv->start_queue.empty();
     }
     if (!pending) ts.tv_nsec = 20000;   // idle: 20 us
     else ts.tv_nsec = 2000;
@@ -351,6 +371,8 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
   const uint64_t bytes = (q->n * (q->dtype == MRG_F64 ? 8 : 4) + kAlign - 1) / kAlign * kAlign;
   if (bytes > sv->arena_bytes || nseg > 0xFFFFFFFFull)
     return mrg::set_error(MRG_ERANGE, "request larger than the server's arena");
+  if (ntiles > sv->ring_tiles)
+    return mrg::set_error(MRG_ERANGE, "request has more tiles than the server's ring holds");
   // admission: a slot and output memory (tiles go to the ring in chunks)
   if (sv->free_slots.empty()) return mrg::set_error(MRG_EBUSY, "no free slot");
   uint64_t off = 0;
@@ -383,7 +405,7 @@ int mrg_server_submit(mrg_server* sv, const mrg_request* q, uint64_t* id, void**
     return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   }
   sv->inflight[seq64] = mrg_server::Inflight{slot, seq, off, bytes, ntiles, 0, 0, false};
-  sv->emit_queue.push_back(seq64);
+  sv->start_queue.push_back(seq64);
   rc = pump(sv);
   if (rc) return rc;
   *id = seq64;
@@ -460,6 +482,8 @@ int mrg_server_restart(mrg_server* sv) {
   }
   sv->ring_firsts.clear();
   sv->emit_queue.clear();
+  sv->start_queue.clear();
+  sv->reserved = 0;
   e = cudaMemset(sv->tiles_done_d, 0, sizeof(unsigned int) * sv->max_slots);
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   return launch_worker(sv);
@@ -471,7 +495,9 @@ int mrg_server_destroy(mrg_server* sv) {
   {
     std::unique_lock<std::mutex> lk(sv->mu);
     // let the feeder publish every admitted tile first (bounded by the ring)
-    for (int spin = 0; sv->running && !sv->emit_queue.empty() && spin < 200000; ++spin) {
+    for (int spin = 0;
+         sv->running && (!sv->emit_queue.empty() || !sv->start_queue.empty()) && spin < 200000;
+         ++spin) {
       lk.unlock();
       timespec ts{0, 10000};
       nanosleep(&ts, nullptr);

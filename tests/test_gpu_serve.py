@@ -199,3 +199,35 @@ def test_tiling_changes_no_output(M):
     with pytest.raises(M.MrgError):
         sv.set_tiling(dict(seg_min=8, seg_max=12, target_segments=1))
     sv.close()
+
+
+def test_saturation_with_a_small_ring_drains(M):
+    """Many large requests offered at once into a ring far smaller than their
+    tiles: requests start only when the ring can take all their tiles, so the
+    server keeps draining instead of filling the ring with first chunks.
+    Outputs equal the batch runner's."""
+    ns = 64
+    s = M.create_streams(ns, seed=SEED)
+    rng = np.random.default_rng(35)
+    reqs = [dict(stream=int(rng.integers(0, ns)), substream=int(k % 3), offset=0,
+                 n=int(rng.integers(1_200_000, 3_000_000)), dist=["uniform", "normal"][k % 2],
+                 dtype="f32", rate=1.0) for k in range(40)]
+    ref = [dict(q) for q in reqs]
+    M.alloc_outputs(ref)
+    b = M.Batch(s, max_requests=64, max_tiles=1 << 15)
+    # ring of 2048 tiles; each request takes ~290-730 tiles, more than one
+    # emission chunk, so several requests would be half-emitted at once
+    sv = M.Server(s, 1 << 30, max_slots=64, ring_tiles=2048, idle_seconds=10.0)
+    c = Client(sv)
+    got = c.submit_all(reqs)
+    c.wait([i for i, _ in got], timeout=60.0)
+    b.run(ref)
+    torch.cuda.current_stream().synchronize()
+    for (rid, out), r in zip(got, ref):
+        assert torch.equal(out.cpu(), r["out"].cpu()), r
+        sv.release(rid)
+    with pytest.raises(M.MrgError) as e:                      # more tiles than the ring
+        sv.submit(0, 100_000_000, "uniform", "f32")
+    assert e.value.code == M.ERANGE
+    sv.close()
+    b.close()
