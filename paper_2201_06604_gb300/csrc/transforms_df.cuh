@@ -179,21 +179,34 @@ __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __res
   cs = df{c0.hi * cs_, c0.lo * cs_};
 }
 
-// RN-ish conversion of a df to IEEE double bits, in integers (|error| <= 1 ulp
-// of the double).  Requires |hi| normal or zero and |lo| <= ulp(hi).
+// Conversion of a df to IEEE double bits, in integers (|error| <= 1 ulp of
+// the double).  Requires |hi| normal or zero and |lo| <= ulp(hi).
+//   * hi as a double: its exponent-and-significand bits moved up 29 places,
+//     the exponent rebiased by 1023 - 127 = 896 (one wide multiply-add);
+//   * lo in units of the double's last place at hi's binade, 2^(e - 179),
+//     rounded to an integer with the sign of lo relative to hi, added to the
+//     magnitude bits -- a carry or borrow moves the exponent;
+//   * when hi is a power of two and lo is negative the sum lies in the binade
+//     below, whose last place is half as large: lo counts twice there.
 __device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
   const uint32_t hb = __float_as_uint(v.hi);
   const uint32_t ah = hb & 0x7FFFFFFFu;
   if (ah == 0) return (uint64_t)(hb & 0x80000000u) << 32;   // +-0
-  const uint32_t eh = ah >> 23;                               // biased fp32 exponent
-  const uint32_t mh = (ah & 0x7FFFFFu) | 0x800000u;          // 24-bit significand
-  // lo in units of 2^(eh - 179) (the double's last place), sign relative to hi
-  const float scale = __uint_as_float(((306u - eh) << 23) ^ (hb & 0x80000000u));
-  const int32_t li = __float2int_rn(__fmul_rn(v.lo, scale));
-  uint64_t V = ((uint64_t)mh << 29) + (uint64_t)(int64_t)li;  // in [2^52 - 2^28, 2^53 + 2^28)
-  uint32_t e64 = eh + 895u;                                   // biased double exponent - 1
-  if (V < (1ull << 52)) { V <<= 1; --e64; }                   // hi a power of two, lo < 0
-  return ((uint64_t)(hb & 0x80000000u) << 32) | (((uint64_t)e64 << 52) + V);
+  uint64_t mag;
+  asm("mad.wide.u32 %0, %1, 536870912, 0x3800000000000000;" : "=l"(mag) : "r"(ah));  // ah 2^29 + 896 2^52
+  const uint32_t eh = ah >> 23;                              // biased fp32 exponent of hi
+  int32_t li;
+  if (__builtin_expect(eh >= 52, 1)) {                       // 2^(179 - eh) is a float
+    const float scale = __uint_as_float(((306u - eh) << 23) ^ (hb & 0x80000000u));
+    li = __float2int_rn(__fmul_rn(v.lo, scale));
+  } else {                                                   // |hi| < 2^-75: scale in two steps
+    const float s1 = __uint_as_float((127u + 64u) << 23);    // 2^64
+    const float s2 = __uint_as_float(((242u - eh) << 23) ^ (hb & 0x80000000u));  // 2^(115 - eh)
+    li = __float2int_rn(__fmul_rn(__fmul_rn(v.lo, s1), s2));
+  }
+  if (li < 0 && (ah & 0x7FFFFFu) == 0) li *= 2;
+  mag += (uint64_t)(int64_t)li;
+  return mag | ((uint64_t)(hb & 0x80000000u) << 32);
 }
 
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }

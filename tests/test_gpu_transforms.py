@@ -83,6 +83,11 @@ def test_normal_transform_accuracy(mrg, dtype):
     if dtype == torch.float64:
         print(f"fp64 normal: max abs err {err.max():.3e} over {z.size} values")
         assert err.max() <= 1e-12
+        nz = ref != 0
+        assert (got[~nz] == 0).all()                     # exact zeros stay exact
+        rel = (err[nz] / np.abs(ref[nz])).max()
+        print(f"fp64 normal: max rel err {rel:.3e}")
+        assert rel <= 1e-11
     else:
         ratio = (err / f32_ulp(ref)).max()
         print(f"fp32 normal: max err {ratio:.3f} ulp over {z.size} values")
@@ -100,6 +105,11 @@ def test_exponential_transform_accuracy(mrg, dtype, rate):
         tol = 1e-12 / min(rate, 1.0)
         print(f"fp64 exponential rate={rate}: max abs err {err.max():.3e} (tol {tol:.1e})")
         assert err.max() <= tol
+        # relative accuracy as well: an absolute bound cannot see wrong bits in
+        # values of 1e-20 and below (rate 2^64 with u near 1)
+        rel = (err / np.abs(ref)).max()
+        print(f"fp64 exponential rate={rate}: max rel err {rel:.3e}")
+        assert rel <= 4e-12
     else:
         ratio = (err / f32_ulp(ref)).max()
         print(f"fp32 exponential rate={rate}: max err {ratio:.3f} ulp")
