@@ -102,6 +102,24 @@ __device__ __forceinline__ df df_add(df x, df y) {
 
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
 
+// x + y when |x.hi| >= |y.hi| or x.hi = 0 (the order is known): the
+// error-free sum of the leading parts needs no magnitude test.
+__device__ __forceinline__ df df_add_ordered(df x, df y) {
+  const df s = fast_two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+// x * y for a df x and a small df y as (leading product, exact) + (the rest,
+// in fp32): the cross terms are below 2^-24 of the product, so their own
+// rounding stays below 2^-48 of it.
+__device__ __forceinline__ df df_mul_split(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df{p, e};  // not renormalised: p + e with |e| << |p|
+}
+
 // Small exact integer (|v| < 2^22) to float without the conversion unit.
 __device__ __forceinline__ float small_int_to_float(int32_t v) {
   return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
@@ -127,11 +145,14 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
   const float c3 = __fmul_rn(__fmul_rn(p2, rh), poly);
   df l1p = df_add(r, df{-0.5f * p2, __fmaf_rn(-0.5f, e2, c3)});
-  // -s ln2 + ln(C_k / M)
+  // -s ln2 + ln(C_k / M) + ln(1 + r): all three are <= 0 apart from the
+  // last, and |s ln2| >= ln 2 >= |ln(C_k / M)| when s > 0, while
+  // |ln(C_k / M)| >= |ln(1 + r)| outside the top bucket (where ln(C_k / M) = 0
+  // exactly): each sum's order is known.
   const float sf = small_int_to_float((int32_t)s);
   const float a = __fmul_rn(-sf, LN2_HI);
   const df sl = df{a, __fmaf_rn(-sf, LN2_LO, __fmaf_rn(-sf, LN2_HI, -a))};
-  return df_add(df_add(sl, df{T.z, T.w}), l1p);
+  return df_add_ordered(df_add_ordered(sl, df{T.z, T.w}), l1p);
 }
 
 // sqrt of a positive df (relative error ~2^-46).
@@ -167,9 +188,28 @@ __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __res
   const df cm1 = fast_two_sum(-0.5f * d2, __fmaf_rn(-0.5f, e2, cc));
   const float4 T = tab[TAB_TRIG + j];
   const df sj{T.x, T.y}, cj{T.z, T.w};
-  // sin(a + d) = sj + (sj (cos d - 1) + cj sin d);  cos(a + d) = cj + (cj (cos d - 1) - sj sin d)
-  df sp = df_add(sj, df_add(df_mul(sj, cm1), df_mul(cj, sd)));
-  df cp = df_add(cj, df_add(df_mul(cj, cm1), df_neg(df_mul(sj, sd))));
+  // sin(a + d) = sj + cj sin d + sj (cos d - 1);  cos(a + d) = cj - sj sin d + cj (cos d - 1).
+  // |sin d| <= 0.0062 and |cos d - 1| <= 2e-5, so each product is formed as
+  // its exact leading part plus fp32 cross terms, the leading parts are
+  // added largest first (the table value dominates, or is 0 for j = 0 where
+  // the result is the product itself), and the small remainders are summed
+  // in fp32: the error stays near 1e-15 against the 1.5e-13 an fp64 output
+  // of R cos(theta) allows.
+  const df ps = df_mul_split(cj, sd), pc = df_mul_split(sj, cm1);
+  const df qs = df_mul_split(sj, sd), qc = df_mul_split(cj, cm1);
+  df sp, cp;
+  {
+    const df u1 = fast_two_sum(sj.hi, ps.hi);
+    const df u2 = fast_two_sum(u1.hi, pc.hi);
+    const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(sj.lo, __fadd_rn(ps.lo, pc.lo)));
+    sp = fast_two_sum(u2.hi, lo);
+  }
+  {
+    const df u1 = fast_two_sum(cj.hi, -qs.hi);
+    const df u2 = fast_two_sum(u1.hi, qc.hi);
+    const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(cj.lo, __fsub_rn(qc.lo, qs.lo)));
+    cp = fast_two_sum(u2.hi, lo);
+  }
   // angle = (pi/2) q + phi, phi = reflected or not
   const bool swap = refl ^ (q & 1u);
   df s0 = swap ? cp : sp, c0 = swap ? sp : cp;
