@@ -35,8 +35,8 @@ ES = {"f64": 8, "f32": 4, "u32": 4}
 # the recurrence is integer multiply-add work), so the dominant kernel's
 # roofline is issue slots: 4 warp-instructions per cycle per SM.
 INSTR_PER_OUTPUT = {("raw", "u32"): 28.3, ("uniform", "f64"): 44.0, ("uniform", "f32"): 49.4,
-                    ("normal", "f64"): 150.9, ("normal", "f32"): 127.4,
-                    ("exponential", "f32"): 99.2, ("exponential", "f64"): 122.2}
+                    ("normal", "f64"): 150.9, ("normal", "f32"): 116.9,
+                    ("exponential", "f32"): 78.2, ("exponential", "f64"): 122.2}
 SM_COUNT = 152
 
 

@@ -195,7 +195,7 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
       const uint32_t z1 = step_fast(s, c.k1, c.k2);
       const uint32_t z2 = step_fast(s, c.k1, c.k2);
       df x, y;
-      box_muller_df(z1, z2, tab, x, y);
+      box_muller_df_m<UM32k3a, DT == MRG_F32>(z1, z2, tab, x, y);
       if constexpr (DT == MRG_F64) {
         put_f64(w + 4 * p, df_to_f64_bits(x));
         put_f64(w + 4 * p + 2, df_to_f64_bits(y));
@@ -207,7 +207,9 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
     for (int e = 0; e < UE; ++e) {
-      const df v = df_mul(ln_u_df(step_fast(s, c.k1, c.k2), tab), df{c.ir_hi, c.ir_lo});
+      const uint32_t z = step_fast(s, c.k1, c.k2);
+      const df l = DT == MRG_F64 ? ln_u_df(z, tab) : ln_u_lite(z, tab);
+      const df v = df_mul(l, df{c.ir_hi, c.ir_lo});
       if constexpr (DT == MRG_F64) put_f64(w + 2 * e, df_to_f64_bits(v));
       else w[e] = __float_as_uint(df_to_f32(v));
     }
@@ -362,11 +364,12 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
       const uint32_t z1 = z[2 * u];
       const uint32_t z2 = 2 * u + 1 < n ? z[2 * u + 1] : 1u;
       df x, y;
-      box_muller_df(z1, z2, s_tab, x, y);
+      box_muller_df_m<UM32k3a, DT == MRG_F32>(z1, z2, s_tab, x, y);
       if constexpr (DT == MRG_F64) { put_f64(w, df_to_f64_bits(x)); put_f64(w + 2, df_to_f64_bits(y)); }
       else { w[0] = __float_as_uint(df_to_f32(x)); w[1] = __float_as_uint(df_to_f32(y)); }
     } else if constexpr (DIST == MRG_EXPONENTIAL) {
-      const df v = df_mul(ln_u_df(z[u], s_tab), df{c.ir_hi, c.ir_lo});
+      const df v = df_mul(DT == MRG_F64 ? ln_u_df(z[u], s_tab) : ln_u_lite(z[u], s_tab),
+                          df{c.ir_hi, c.ir_lo});
       if constexpr (DT == MRG_F64) put_f64(w, df_to_f64_bits(v));
       else w[0] = __float_as_uint(df_to_f32(v));
     } else if constexpr (DT == MRG_F64) {

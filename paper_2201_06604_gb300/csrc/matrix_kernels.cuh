@@ -54,8 +54,8 @@ __global__ void __launch_bounds__(256) matrix_kernel(MatrixArgs a, uint64_t k1, 
         else *reinterpret_cast<uint32_t*>(dst) = G31 ? g31::uniform_bits32(z) : f32_bits_from_f64(b);
       } else {
         df l;
-        if constexpr (G31) l = ln_u_df_m<UM2p32>(2u * z, s_tab);
-        else l = ln_u_df(z, s_tab);
+        if constexpr (G31) l = DT == MRG_F64 ? ln_u_df_m<UM2p32>(2u * z, s_tab) : ln_u_lite_m<UM2p32>(2u * z, s_tab);
+        else l = DT == MRG_F64 ? ln_u_df(z, s_tab) : ln_u_lite(z, s_tab);
         const df v = df_mul(l, df{a.ir_hi, a.ir_lo});
         if constexpr (DT == MRG_F64) *reinterpret_cast<uint64_t*>(dst) = df_to_f64_bits(v);
         else *reinterpret_cast<float*>(dst) = df_to_f32(v);

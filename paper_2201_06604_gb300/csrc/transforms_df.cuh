@@ -155,6 +155,40 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   return df_add_ordered(df_add_ordered(sl, df{T.z, T.w}), l1p);
 }
 
+// ln(z / M) to ~2^-34 relative, for fp32 outputs (whose 2-ulp budget is
+// 2^-23): the same reduction and error-free leading parts as ln_u_df_m --
+// the product r = d / C_k kept with its rounding error (which alone would
+// be a whole fp32 ulp of the result near u = 1 - 2^-8), and the three terms
+// added largest first -- but the Taylor tail and the low parts in plain
+// fp32, renormalised once at the end.
+template <class UM>
+__device__ __forceinline__ df ln_u_lite_m(uint32_t z, const float4* __restrict__ tab) {
+  uint32_t s;
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(s) : "r"(z));
+  const uint32_t zn = z << s;
+  const uint32_t k = (zn >> 24) & 127u;
+  const uint32_t ck = k == 127u ? UM::TOP_CK : 0x80800000u + (k << 24);
+  const float df_ = (float)(int32_t)(zn - ck);          // |d| < 2^24: exact
+  const float4 T = tab[TAB_LOG + k];
+  const float rh = __fmul_rn(T.x, df_);
+  const float re = __fmaf_rn(T.y, df_, __fmaf_rn(T.x, df_, -rh));   // r = rh + re
+  // ln(1 + r) - r = r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 - r / 6))))
+  float poly = __fmaf_rn(rh, -1.0f / 6.0f, 0.2f);
+  poly = __fmaf_rn(rh, poly, -0.25f);
+  poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
+  poly = __fmaf_rn(rh, poly, -0.5f);
+  const float tail = __fmul_rn(__fmul_rn(rh, rh), poly);
+  const float sf = small_int_to_float((int32_t)s);
+  const float a = __fmul_rn(-sf, LN2_HI);
+  const float a_lo = __fmaf_rn(-sf, LN2_LO, __fmaf_rn(-sf, LN2_HI, -a));
+  const df u1 = fast_two_sum(a, T.z);        // |s ln 2| >= |ln(C_k / M)|, or s = 0
+  const df u2 = fast_two_sum(u1.hi, rh);     // |ln(C_k / M)| >= |r|, or both 0
+  const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(__fadd_rn(a_lo, T.w), __fadd_rn(re, tail)));
+  // renormalised: in the top bucket lo carries the Taylor tail, up to 2^-9 of
+  // hi, and df_sqrt's single correction step needs |lo| <= ulp(hi)
+  return fast_two_sum(u2.hi, lo);
+}
+
 // sqrt of a positive df (relative error ~2^-46).
 __device__ __forceinline__ df df_sqrt(df x) {
   float y = rsqrtf(x.hi);
@@ -251,11 +285,14 @@ __device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
 
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
 
-// Box-Muller on one pair: X, Y as df.
-template <class UM>
+// Box-Muller on one pair: X, Y as df.  LITE: the log to ~2^-34 (enough for
+// fp32 outputs), else to ~2^-46.
+template <class UM, bool LITE = false>
 __device__ __forceinline__ void box_muller_df_m(uint32_t z1, uint32_t z2,
                                                 const float4* __restrict__ tab, df& x, df& y) {
-  const df l = ln_u_df_m<UM>(z1, tab);
+  df l;
+  if constexpr (LITE) l = ln_u_lite_m<UM>(z1, tab);
+  else l = ln_u_df_m<UM>(z1, tab);
   const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
   df sn, cs;
   sincos_turn_df_m<UM>(z2, tab, sn, cs);
@@ -274,6 +311,9 @@ __device__ __forceinline__ void sincos_turn_df(uint32_t z, const float4* __restr
 __device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
                                               df& x, df& y) {
   box_muller_df_m<UM32k3a>(z1, z2, tab, x, y);
+}
+__device__ __forceinline__ df ln_u_lite(uint32_t z, const float4* __restrict__ tab) {
+  return ln_u_lite_m<UM32k3a>(z, tab);
 }
 
 }  // namespace mrg
