@@ -525,6 +525,7 @@ cudaError_t launch_generate_g(const DevStreams& s, uint64_t n, int dist, int dty
   L = (L + ce - 1) / ce * ce;                 // multiple of 8 (even: pairs stay aligned)
   const uint64_t ncap = (n + ce - 1) / ce * ce;
   L = std::min(L, ncap);
+  L = std::min<uint64_t>(L, 1ull << 31);      // a lane's count is a 32-bit word
   GenArgs a;
   a.cur = s.cur;
   a.stride = s.stride;
