@@ -100,24 +100,26 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
     for (int p = 0; p < UE / 2; ++p) {
       const uint32_t z1 = g31::step(s);
       const uint32_t z2 = g31::step(s);
-      df x, y;
-      box_muller_df_m<UM2p32, DT == MRG_F32>(2u * z1, 2u * z2, tab, x, y);
       if constexpr (DT == MRG_F64) {
+        df x, y;
+        box_muller_df_m<UM2p32>(2u * z1, 2u * z2, tab, x, y);
         put_f64(w + 4 * p, df_to_f64_bits(x));
         put_f64(w + 4 * p + 2, df_to_f64_bits(y));
       } else {
-        w[2 * p] = __float_as_uint(df_to_f32(x));
-        w[2 * p + 1] = __float_as_uint(df_to_f32(y));
+        float x, y;
+        box_muller_f32_m<UM2p32>(2u * z1, 2u * z2, tab, x, y);
+        w[2 * p] = __float_as_uint(x);
+        w[2 * p + 1] = __float_as_uint(y);
       }
     }
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
     for (int e = 0; e < UE; ++e) {
       const uint32_t z2 = 2u * g31::step(s);
-      const df l = DT == MRG_F64 ? ln_u_df_m<UM2p32>(z2, tab) : ln_u_lite_m<UM2p32>(z2, tab);
-      const df v = df_mul(l, df{c.ir_hi, c.ir_lo});
-      if constexpr (DT == MRG_F64) put_f64(w + 2 * e, df_to_f64_bits(v));
-      else w[e] = __float_as_uint(df_to_f32(v));
+      if constexpr (DT == MRG_F64)
+        put_f64(w + 2 * e, df_to_f64_bits(df_mul(ln_u_df_m<UM2p32>(z2, tab), df{c.ir_hi, c.ir_lo})));
+      else
+        w[e] = __float_as_uint(exp_f32_m<UM2p32>(z2, tab, c.ir_hi, c.ir_lo));
     }
   }
 }

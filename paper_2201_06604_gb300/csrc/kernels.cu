@@ -188,30 +188,32 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else if constexpr (DIST == MRG_UNIFORM) {
 #pragma unroll
     for (int e = 0; e < UE; ++e)
-      w[e] = f32_bits_from_f64(uniform_bits64_fast(step_fast(s, c.k1, c.k2)));
+      w[e] = uniform_bits32(step_fast(s, c.k1, c.k2));
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
       const uint32_t z1 = step_fast(s, c.k1, c.k2);
       const uint32_t z2 = step_fast(s, c.k1, c.k2);
-      df x, y;
-      box_muller_df_m<UM32k3a, DT == MRG_F32>(z1, z2, tab, x, y);
       if constexpr (DT == MRG_F64) {
+        df x, y;
+        box_muller_df(z1, z2, tab, x, y);
         put_f64(w + 4 * p, df_to_f64_bits(x));
         put_f64(w + 4 * p + 2, df_to_f64_bits(y));
       } else {
-        w[2 * p] = __float_as_uint(df_to_f32(x));
-        w[2 * p + 1] = __float_as_uint(df_to_f32(y));
+        float x, y;
+        box_muller_f32(z1, z2, tab, x, y);
+        w[2 * p] = __float_as_uint(x);
+        w[2 * p + 1] = __float_as_uint(y);
       }
     }
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
     for (int e = 0; e < UE; ++e) {
       const uint32_t z = step_fast(s, c.k1, c.k2);
-      const df l = DT == MRG_F64 ? ln_u_df(z, tab) : ln_u_lite(z, tab);
-      const df v = df_mul(l, df{c.ir_hi, c.ir_lo});
-      if constexpr (DT == MRG_F64) put_f64(w + 2 * e, df_to_f64_bits(v));
-      else w[e] = __float_as_uint(df_to_f32(v));
+      if constexpr (DT == MRG_F64)
+        put_f64(w + 2 * e, df_to_f64_bits(df_mul(ln_u_df(z, tab), df{c.ir_hi, c.ir_lo})));
+      else
+        w[e] = __float_as_uint(exp_f32(z, tab, c.ir_hi, c.ir_lo));
     }
   }
 }
@@ -363,19 +365,26 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
     if constexpr (DIST == MRG_NORMAL) {
       const uint32_t z1 = z[2 * u];
       const uint32_t z2 = 2 * u + 1 < n ? z[2 * u + 1] : 1u;
-      df x, y;
-      box_muller_df_m<UM32k3a, DT == MRG_F32>(z1, z2, s_tab, x, y);
-      if constexpr (DT == MRG_F64) { put_f64(w, df_to_f64_bits(x)); put_f64(w + 2, df_to_f64_bits(y)); }
-      else { w[0] = __float_as_uint(df_to_f32(x)); w[1] = __float_as_uint(df_to_f32(y)); }
+      if constexpr (DT == MRG_F64) {
+        df x, y;
+        box_muller_df(z1, z2, s_tab, x, y);
+        put_f64(w, df_to_f64_bits(x));
+        put_f64(w + 2, df_to_f64_bits(y));
+      } else {
+        float x, y;
+        box_muller_f32(z1, z2, s_tab, x, y);
+        w[0] = __float_as_uint(x);
+        w[1] = __float_as_uint(y);
+      }
     } else if constexpr (DIST == MRG_EXPONENTIAL) {
-      const df v = df_mul(DT == MRG_F64 ? ln_u_df(z[u], s_tab) : ln_u_lite(z[u], s_tab),
-                          df{c.ir_hi, c.ir_lo});
-      if constexpr (DT == MRG_F64) put_f64(w, df_to_f64_bits(v));
-      else w[0] = __float_as_uint(df_to_f32(v));
+      if constexpr (DT == MRG_F64)
+        put_f64(w, df_to_f64_bits(df_mul(ln_u_df(z[u], s_tab), df{c.ir_hi, c.ir_lo})));
+      else
+        w[0] = __float_as_uint(exp_f32(z[u], s_tab, c.ir_hi, c.ir_lo));
     } else if constexpr (DT == MRG_F64) {
       put_f64(w, uniform_bits64_fast(z[u]));
     } else {
-      w[0] = f32_bits_from_f64(uniform_bits64_fast(z[u]));
+      w[0] = uniform_bits32(z[u]);
     }
     for (int e = 0; e < PER; ++e) {
       const uint64_t i = u * PER + e;

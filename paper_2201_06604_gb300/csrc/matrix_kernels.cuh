@@ -47,18 +47,16 @@ __global__ void __launch_bounds__(256) matrix_kernel(MatrixArgs a, uint64_t k1, 
       if constexpr (DIST == MRG_RAW) {
         *reinterpret_cast<uint32_t*>(dst) = z;
       } else if constexpr (DIST == MRG_UNIFORM) {
-        uint64_t b;
-        if constexpr (G31) b = g31::uniform_bits64(z);
-        else b = uniform_bits64_fast(z);
-        if constexpr (DT == MRG_F64) *reinterpret_cast<uint64_t*>(dst) = b;
-        else *reinterpret_cast<uint32_t*>(dst) = G31 ? g31::uniform_bits32(z) : f32_bits_from_f64(b);
+        if constexpr (DT == MRG_F64)
+          *reinterpret_cast<uint64_t*>(dst) = G31 ? g31::uniform_bits64(z) : uniform_bits64_fast(z);
+        else
+          *reinterpret_cast<uint32_t*>(dst) = G31 ? g31::uniform_bits32(z) : uniform_bits32(z);
+      } else if constexpr (DT == MRG_F64) {
+        const df l = G31 ? ln_u_df_m<UM2p32>(2u * z, s_tab) : ln_u_df(z, s_tab);
+        *reinterpret_cast<uint64_t*>(dst) = df_to_f64_bits(df_mul(l, df{a.ir_hi, a.ir_lo}));
       } else {
-        df l;
-        if constexpr (G31) l = DT == MRG_F64 ? ln_u_df_m<UM2p32>(2u * z, s_tab) : ln_u_lite_m<UM2p32>(2u * z, s_tab);
-        else l = DT == MRG_F64 ? ln_u_df(z, s_tab) : ln_u_lite(z, s_tab);
-        const df v = df_mul(l, df{a.ir_hi, a.ir_lo});
-        if constexpr (DT == MRG_F64) *reinterpret_cast<uint64_t*>(dst) = df_to_f64_bits(v);
-        else *reinterpret_cast<float*>(dst) = df_to_f32(v);
+        *reinterpret_cast<float*>(dst) = G31 ? exp_f32_m<UM2p32>(2u * z, s_tab, a.ir_hi, a.ir_lo)
+                                             : exp_f32(z, s_tab, a.ir_hi, a.ir_lo);
       }
     }
   }

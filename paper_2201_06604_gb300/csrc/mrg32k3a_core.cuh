@@ -198,6 +198,29 @@ MRG_HD uint32_t f32_bits_from_f64(uint64_t d) {
   return (uint32_t)((d + 0x0FFFFFFFull + odd) >> 29) - (896u << 23);
 }
 
+// The same fp32 uniform straight from z, without forming the double.  With
+// zn, s and the significand S = zn 2^21 + RN(zn DELTA / 2^31) of the fp64
+// uniform above, the float keeps S rounded at bit 29.  Rounding half up
+// there is nearest-even for every z (the fp64 significands with a remainder
+// of exactly 2^28 all have an odd kept part), and both roundings nest into
+// one floor:
+//   floor((S + 2^28) / 2^29) = floor((zn 2^52 + zn DELTA + 2^59 + 2^30 - 1) / 2^60)
+//                            = floor((zn + h) / 2^8),   h = floor(t / 2^52),
+// with t = zn DELTA + 2^59 + 2^30 - 1 < 2^61 (one wide multiply-add).  The
+// float is ((125 - s) << 23) + that 24-bit significand, whose carry into
+// 2^24 steps the exponent.  When zn + h passes 2^32 the value rounds up to
+// 2^-s exactly (significand 2^24) -- for zn >= ZN_BIG, where the double
+// itself lies in the next binade, the float is 2^-s too.  Checked against
+// RN32 of the IEEE product for every z on the host.
+MRG_HD uint32_t uniform_bits32(uint32_t z) {
+  const uint32_t s = clz32(z);
+  const uint32_t zn = z << s;
+  const uint64_t t = (uint64_t)zn * (uint32_t)NORM_DELTA + ((1ull << 59) + (1ull << 30) - 1);
+  const uint32_t sum = zn + (uint32_t)(t >> 52);
+  const uint32_t m = sum < zn ? (1u << 24) : (sum >> 8);
+  return ((125u - s) << 23) + m;
+}
+
 // ---------------------------------------------------------------------------
 // Device fast paths: the same arithmetic written as PTX so that ptxas keeps
 // the multiply-adds on the IMAD pipe and the fold carries as predicated adds
@@ -236,12 +259,14 @@ __device__ __forceinline__ uint32_t step_fast(TState& s, uint64_t k1, uint64_t k
       : "=r"(p2) : "r"(s.b2), "r"(s.b0), "l"(k2));
   s.a2 = s.a1; s.a1 = s.a0; s.a0 = p1;
   s.b2 = s.b1; s.b1 = s.b0; s.b0 = p2;
-  // z: h = p1 + (22643 - p2) carries exactly when D >= 1; z = h + 209 c - 208
-  asm("{\n\t.reg .u32 q, h;\n\t"
+  // z: h = p1 + (22643 - p2) carries exactly when D >= 1, i.e. when h < p1;
+  // z = h + 209 c - 208 (the carry as a predicated add keeps it off the
+  // IMAD pipe, which the step's wide products already fill)
+  asm("{\n\t.reg .u32 q, h;\n\t.reg .pred c;\n\t"
       "sub.u32 q, 22643, %2;\n\t"
-      "add.cc.u32 h, %1, q;\n\t"
-      "addc.u32 q, 0, 0;\n\t"
-      "mad.lo.u32 h, q, 209, h;\n\t"
+      "add.u32 h, %1, q;\n\t"
+      "setp.lt.u32 c, h, %1;\n\t"
+      "@c add.u32 h, h, 209;\n\t"
       "sub.u32 %0, h, 208;\n\t}"
       : "=r"(z) : "r"(p1), "r"(p2));
   return z;

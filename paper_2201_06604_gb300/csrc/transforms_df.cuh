@@ -162,7 +162,7 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
 // added largest first -- but the Taylor tail and the low parts in plain
 // fp32, renormalised once at the end.
 template <class UM>
-__device__ __forceinline__ df ln_u_lite_m(uint32_t z, const float4* __restrict__ tab) {
+__device__ __forceinline__ df ln_u_lite_raw_m(uint32_t z, const float4* __restrict__ tab) {
   uint32_t s;
   asm("bfind.shiftamt.u32 %0, %1;" : "=r"(s) : "r"(z));
   const uint32_t zn = z << s;
@@ -184,32 +184,63 @@ __device__ __forceinline__ df ln_u_lite_m(uint32_t z, const float4* __restrict__
   const df u1 = fast_two_sum(a, T.z);        // |s ln 2| >= |ln(C_k / M)|, or s = 0
   const df u2 = fast_two_sum(u1.hi, rh);     // |ln(C_k / M)| >= |r|, or both 0
   const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(__fadd_rn(a_lo, T.w), __fadd_rn(re, tail)));
-  // renormalised: in the top bucket lo carries the Taylor tail, up to 2^-9 of
-  // hi, and df_sqrt's single correction step needs |lo| <= ulp(hi)
-  return fast_two_sum(u2.hi, lo);
+  return df{u2.hi, lo};  // not renormalised: in the top bucket |lo| reaches 2^-9 |hi|
 }
 
-// sqrt of a positive df (relative error ~2^-46).
-__device__ __forceinline__ df df_sqrt(df x) {
+// The same, renormalised (df_sqrt's single correction step needs
+// |lo| <= ulp(hi)).
+template <class UM>
+__device__ __forceinline__ df ln_u_lite_m(uint32_t z, const float4* __restrict__ tab) {
+  const df l = ln_u_lite_raw_m<UM>(z, tab);
+  return fast_two_sum(l.hi, l.lo);
+}
+
+// sqrt of a positive df (relative error ~2^-46) as r0 + c, not renormalised
+// (|c| is about 2^-23 r0 at most).
+__device__ __forceinline__ df df_sqrt_raw(df x) {
   float y = rsqrtf(x.hi);
   y = __fmul_rn(y, __fmaf_rn(-0.5f * x.hi, __fmul_rn(y, y), 1.5f));   // one Newton step
   const float r0 = __fmul_rn(x.hi, y);
   const float e = __fadd_rn(__fmaf_rn(-r0, r0, x.hi), x.lo);           // x - r0^2
-  return fast_two_sum(r0, __fmul_rn(__fmul_rn(e, y), 0.5f));
+  return df{r0, __fmul_rn(__fmul_rn(e, y), 0.5f)};
+}
+
+__device__ __forceinline__ df df_sqrt(df x) {
+  const df r = df_sqrt_raw(x);
+  return fast_two_sum(r.hi, r.lo);
+}
+
+// RN32 of a * b for a df a and b (unnormalised pairs allowed): the cross
+// terms in fp32, the leading product and the sum rounded once by the FMA
+// (the dropped a.lo b.lo and the cross terms' rounding are ~2^-46 of it).
+__device__ __forceinline__ float df_mul_to_f32(df a, float b_hi, float b_lo) {
+  return __fmaf_rn(a.hi, b_hi, __fmaf_rn(a.hi, b_lo, __fmul_rn(a.lo, b_hi)));
+}
+
+// The exact reduction of the angle 2 pi z / M, z in [1, M - 1]: quadrant q
+// (z = q D + w, w in [0, D)), reflection w -> D - w above D / 2, table
+// bucket j and the bucket residual dwf (an exact float in [-2^22, 2^22)).
+template <class UM>
+__device__ __forceinline__ void turn_reduce(uint32_t z, uint32_t& q, bool& refl, uint32_t& j,
+                                            float& dwf) {
+  constexpr uint32_t D = UM::D;  // M / 4
+  q = z >> 30;
+  uint32_t w = (z & 0x3FFFFFFFu) + UM::QFIX * q;  // z - q D  (q D = q 2^30 - QFIX q)
+  if (w >= D) { w -= D; ++q; }                     // z = q D + w, w in [0, D)
+  refl = 2u * w > D;
+  const uint32_t wr = refl ? D - w : w;       // [0, D/2]
+  j = (wr + 0x400000u) >> 23;                 // 0..64
+  dwf = small_int_to_float((int32_t)(wr - (j << 23)));
 }
 
 // sin and cos of 2 pi z / M for z in [1, M - 1].
 template <class UM>
 __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __restrict__ tab, df& sn,
                                                  df& cs) {
-  constexpr uint32_t D = UM::D;  // M / 4
-  uint32_t q = z >> 30;
-  uint32_t w = (z & 0x3FFFFFFFu) + UM::QFIX * q;  // z - q D  (q D = q 2^30 - QFIX q)
-  if (w >= D) { w -= D; ++q; }                     // z = q D + w, w in [0, D)
-  const bool refl = 2u * w > D;
-  const uint32_t wr = refl ? D - w : w;       // [0, D/2]
-  const uint32_t j = (wr + 0x400000u) >> 23;  // 0..64
-  const float dwf = small_int_to_float((int32_t)(wr - (j << 23)));   // [-2^22, 2^22)
+  uint32_t q, j;
+  bool refl;
+  float dwf;
+  turn_reduce<UM>(z, q, refl, j, dwf);
   const df delta = df_mul_f(df{UM::PID_HI, UM::PID_LO}, dwf);
   const float dh = delta.hi;
   const float d2 = __fmul_rn(dh, dh);
@@ -285,19 +316,93 @@ __device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
 
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
 
-// Box-Muller on one pair: X, Y as df.  LITE: the log to ~2^-34 (enough for
-// fp32 outputs), else to ~2^-46.
-template <class UM, bool LITE = false>
+// Box-Muller on one pair: X, Y as df (fp64 outputs).
+template <class UM>
 __device__ __forceinline__ void box_muller_df_m(uint32_t z1, uint32_t z2,
                                                 const float4* __restrict__ tab, df& x, df& y) {
-  df l;
-  if constexpr (LITE) l = ln_u_lite_m<UM>(z1, tab);
-  else l = ln_u_df_m<UM>(z1, tab);
+  const df l = ln_u_df_m<UM>(z1, tab);
   const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
   df sn, cs;
   sincos_turn_df_m<UM>(z2, tab, sn, cs);
   x = df_mul(R, cs);
   y = df_mul(R, sn);
+}
+
+// sin and cos of 2 pi z / M for fp32 outputs, to ~2^-40 relative: the same
+// reduction, table and Taylor terms as sincos_turn_df_m, but one exact
+// leading product per function (sin(a + d) = sj + cj sin d + sj (cos d - 1):
+// cj.hi d.hi exact, added to sj.hi error-free; the other terms, each below
+// 2^-7 of the result, summed in fp32) and cos d - 1 in plain fp32 (it
+// enters at most ~2e-5 of the result).  Returned without their signs, which
+// come back as the sign-bit masks sgn_s, sgn_c of quadrant q.
+//   error: sin in bucket 0 is the residual itself; elsewhere |sin| >= 0.006
+//   and the fp32 terms contribute ~2^-38 absolute; |cos| >= 0.7.
+template <class UM>
+__device__ __forceinline__ void sincos_turn_lite_m(uint32_t z, const float4* __restrict__ tab,
+                                                   df& sn, df& cs, uint32_t& sgn_s,
+                                                   uint32_t& sgn_c) {
+  uint32_t q, j;
+  bool refl;
+  float dwf;
+  turn_reduce<UM>(z, q, refl, j, dwf);
+  // delta = (pi / (2D)) dwf as dh + dl (dh exact leading product)
+  const float dh = __fmul_rn(UM::PID_HI, dwf);
+  const float dl = __fmaf_rn(UM::PID_LO, dwf, __fmaf_rn(UM::PID_HI, dwf, -dh));
+  const float d2 = __fmul_rn(dh, dh);
+  // sin d = dh + sdl,  sdl = dl + d^3 (-1/6 + d^2 / 120)
+  const float sdl = __fmaf_rn(__fmul_rn(dh, d2), __fmaf_rn(d2, 1.0f / 120.0f, -1.0f / 6.0f), dl);
+  // cos d - 1 = d^2 (-1/2 + d^2 (1/24 - d^2 / 720))
+  const float cm1 = __fmul_rn(d2, __fmaf_rn(d2, __fmaf_rn(d2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
+  const float4 T = tab[TAB_TRIG + j];
+  df sp, cp;
+  {  // sj + cj sin d + sj (cos d - 1); |sj.hi| >= |cj.hi dh| or sj = 0
+    const float p = __fmul_rn(T.z, dh);
+    float a = __fadd_rn(T.y, __fmaf_rn(T.z, dh, -p));
+    a = __fmaf_rn(T.x, cm1, a);
+    a = __fmaf_rn(T.z, sdl, a);
+    a = __fmaf_rn(T.w, dh, a);
+    const df u = fast_two_sum(T.x, p);
+    sp = df{u.hi, __fadd_rn(u.lo, a)};
+  }
+  {  // cj - sj sin d + cj (cos d - 1); |cj.hi| >= 0.7 > |sj.hi dh|
+    const float p = __fmul_rn(T.x, dh);
+    float a = __fsub_rn(T.w, __fmaf_rn(T.x, dh, -p));
+    a = __fmaf_rn(T.z, cm1, a);
+    a = __fmaf_rn(-T.x, sdl, a);
+    a = __fmaf_rn(-T.y, dh, a);
+    const df u = fast_two_sum(T.z, -p);
+    cp = df{u.hi, __fadd_rn(u.lo, a)};
+  }
+  const bool swap = refl ^ (q & 1u);
+  sn = swap ? cp : sp;
+  cs = swap ? sp : cp;
+  sgn_s = (q >> 1) << 31;                    // quadrants 2, 3
+  sgn_c = ((q ^ (q >> 1)) & 1u) << 31;       // quadrants 1, 2
+}
+
+// Box-Muller for fp32 outputs: R from the ~2^-34 log, sin and cos from the
+// lite reduction, each output rounded once (df_mul_to_f32) and then signed.
+// Accuracy ~2^-33 relative before the final rounding.
+template <class UM>
+__device__ __forceinline__ void box_muller_f32_m(uint32_t z1, uint32_t z2,
+                                                 const float4* __restrict__ tab, float& x,
+                                                 float& y) {
+  const df l = ln_u_lite_m<UM>(z1, tab);
+  const df R = df_sqrt_raw(df{-2.0f * l.hi, -2.0f * l.lo});
+  df sn, cs;
+  uint32_t sgn_s, sgn_c;
+  sincos_turn_lite_m<UM>(z2, tab, sn, cs, sgn_s, sgn_c);
+  x = __uint_as_float(__float_as_uint(df_mul_to_f32(R, cs.hi, cs.lo)) ^ sgn_c);
+  y = __uint_as_float(__float_as_uint(df_mul_to_f32(R, sn.hi, sn.lo)) ^ sgn_s);
+}
+
+// -ln(u) / rate for fp32 outputs: the ~2^-34 log times -1/rate (a float
+// pair), rounded once.
+template <class UM>
+__device__ __forceinline__ float exp_f32_m(uint32_t z, const float4* __restrict__ tab, float ir_hi,
+                                           float ir_lo) {
+  const df l = ln_u_lite_raw_m<UM>(z, tab);
+  return df_mul_to_f32(df{ir_hi, ir_lo}, l.hi, l.lo);
 }
 
 // The transforms of MRG32k3a's uniforms u = z / (m1 + 1).
@@ -314,6 +419,14 @@ __device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const fl
 }
 __device__ __forceinline__ df ln_u_lite(uint32_t z, const float4* __restrict__ tab) {
   return ln_u_lite_m<UM32k3a>(z, tab);
+}
+__device__ __forceinline__ void box_muller_f32(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
+                                               float& x, float& y) {
+  box_muller_f32_m<UM32k3a>(z1, z2, tab, x, y);
+}
+__device__ __forceinline__ float exp_f32(uint32_t z, const float4* __restrict__ tab, float ir_hi,
+                                         float ir_lo) {
+  return exp_f32_m<UM32k3a>(z, tab, ir_hi, ir_lo);
 }
 
 }  // namespace mrg

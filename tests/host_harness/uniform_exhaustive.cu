@@ -2,7 +2,8 @@
 // the CPU from the same header the kernels use (test infrastructure).
 //   mode "uniform": for every z in [1, m1], uniform_bits64(z) equals the bits
 //     of the IEEE product (double)z * RN64(1/(m1+1)), and f32_bits_from_f64
-//     equals the bits of (float) of that product.
+//     of it and uniform_bits32(z) (the fp32 uniform formed without the
+//     double) equal the bits of (float) of that product.
 //   mode "step" n seed: prints n outputs of mrg::step from a state.
 //   mode "uniform31": for every z in [1, 2^31 - 1], g31::uniform_bits64(z) and
 //     g31::uniform_bits32(z) equal the bits of (double)z * 2^-31 and of its
@@ -29,7 +30,7 @@ static int check_uniform(unsigned lo, unsigned hi) {
     uint32_t wantf;
     std::memcpy(&wantf, &f, 4);
     uint64_t got = mrg::uniform_bits64(z);
-    if (got != want || mrg::f32_bits_from_f64(got) != wantf) {
+    if (got != want || mrg::f32_bits_from_f64(got) != wantf || mrg::uniform_bits32(z) != wantf) {
       if (bad < 5) std::printf("mismatch z=%u got=%016llx want=%016llx\n", z,
                                (unsigned long long)got, (unsigned long long)want);
       ++bad;
