@@ -396,6 +396,28 @@ __device__ __forceinline__ void box_muller_f32_m(uint32_t z1, uint32_t z2,
   y = __uint_as_float(__float_as_uint(df_mul_to_f32(R, sn.hi, sn.lo)) ^ sgn_s);
 }
 
+// X + Y of one Box-Muller pair, R (cos + sin), as an unrounded float pair
+// for sums whose tolerance is relative to the sum of |X| and |Y| (~2^-30):
+// the ~2^-34 log and the lite sin/cos (absolute error ~2^-38), signed,
+// added error-free, times R with the exact leading product.  Absolute
+// error <= ~2^-34 per pair (R <= 6.7), whether or not cos and sin cancel.
+template <class UM>
+__device__ __forceinline__ df box_muller_sum_lite_m(uint32_t z1, uint32_t z2,
+                                                    const float4* __restrict__ tab) {
+  const df l = ln_u_lite_m<UM>(z1, tab);
+  const df R = df_sqrt_raw(df{-2.0f * l.hi, -2.0f * l.lo});
+  df sn, cs;
+  uint32_t sgn_s, sgn_c;
+  sincos_turn_lite_m<UM>(z2, tab, sn, cs, sgn_s, sgn_c);
+  const float ch = __uint_as_float(__float_as_uint(cs.hi) ^ sgn_c);
+  const float cl = __uint_as_float(__float_as_uint(cs.lo) ^ sgn_c);
+  const float sh = __uint_as_float(__float_as_uint(sn.hi) ^ sgn_s);
+  const float sl = __uint_as_float(__float_as_uint(sn.lo) ^ sgn_s);
+  const df t = two_sum(ch, sh);
+  const float tl = __fadd_rn(t.lo, __fadd_rn(cl, sl));
+  return df_mul_split(R, df{t.hi, tl});
+}
+
 // -ln(u) / rate for fp32 outputs: the ~2^-34 log times -1/rate (a float
 // pair), rounded once.
 template <class UM>

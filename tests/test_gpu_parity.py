@@ -240,6 +240,7 @@ def test_fused_small(M, ns, draws):
     assert np.array_equal(cnt, rc)
     x, _ = O.generate_streams(st0, draws + (draws & 1), O.NORMAL, nthreads=8)
     scale = np.abs(x).sum(axis=1)
+    print(f"fused sum: max error {(np.abs(sm - rs) / scale).max():.2e} of sum |x| (bar 1e-9)")
     assert (np.abs(sm - rs) <= 1e-9 * scale).all()
     assert np.array_equal(host_states(M, s), after)
 
