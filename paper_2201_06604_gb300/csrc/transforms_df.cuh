@@ -144,7 +144,8 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   poly = __fmaf_rn(rh, poly, -0.25f);
   poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
   const float c3 = __fmul_rn(__fmul_rn(p2, rh), poly);
-  df l1p = df_add(r, df{-0.5f * p2, __fmaf_rn(-0.5f, e2, c3)});
+  // |r| < 2^-7, so |r| >= r^2 / 2: the order of the sum is known
+  df l1p = df_add_ordered(r, df{-0.5f * p2, __fmaf_rn(-0.5f, e2, c3)});
   // -s ln2 + ln(C_k / M) + ln(1 + r): all three are <= 0 apart from the
   // last, and |s ln2| >= ln 2 >= |ln(C_k / M)| when s > 0, while
   // |ln(C_k / M)| >= |ln(1 + r)| outside the top bucket (where ln(C_k / M) = 0
