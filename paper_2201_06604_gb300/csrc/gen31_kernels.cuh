@@ -101,10 +101,10 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
       const uint32_t z1 = g31::step(s);
       const uint32_t z2 = g31::step(s);
       if constexpr (DT == MRG_F64) {
-        df x, y;
-        box_muller_df_m<UM2p32>(2u * z1, 2u * z2, tab, x, y);
-        put_f64(w + 4 * p, df_to_f64_bits(x));
-        put_f64(w + 4 * p + 2, df_to_f64_bits(y));
+        uint64_t x, y;
+        box_muller_f64_m<UM2p32>(2u * z1, 2u * z2, tab, x, y);
+        put_f64(w + 4 * p, x);
+        put_f64(w + 4 * p + 2, y);
       } else {
         float x, y;
         box_muller_f32_m<UM2p32>(2u * z1, 2u * z2, tab, x, y);

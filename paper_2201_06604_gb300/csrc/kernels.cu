@@ -195,10 +195,10 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
       const uint32_t z1 = step_fast(s, c.k1, c.k2);
       const uint32_t z2 = step_fast(s, c.k1, c.k2);
       if constexpr (DT == MRG_F64) {
-        df x, y;
-        box_muller_df(z1, z2, tab, x, y);
-        put_f64(w + 4 * p, df_to_f64_bits(x));
-        put_f64(w + 4 * p + 2, df_to_f64_bits(y));
+        uint64_t x, y;
+        box_muller_f64(z1, z2, tab, x, y);
+        put_f64(w + 4 * p, x);
+        put_f64(w + 4 * p + 2, y);
       } else {
         float x, y;
         box_muller_f32(z1, z2, tab, x, y);
@@ -378,10 +378,10 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
       const uint32_t z1 = z[2 * u];
       const uint32_t z2 = 2 * u + 1 < n ? z[2 * u + 1] : 1u;
       if constexpr (DT == MRG_F64) {
-        df x, y;
-        box_muller_df(z1, z2, s_tab, x, y);
-        put_f64(w, df_to_f64_bits(x));
-        put_f64(w + 2, df_to_f64_bits(y));
+        uint64_t x, y;
+        box_muller_f64(z1, z2, s_tab, x, y);
+        put_f64(w, x);
+        put_f64(w + 2, y);
       } else {
         float x, y;
         box_muller_f32(z1, z2, s_tab, x, y);

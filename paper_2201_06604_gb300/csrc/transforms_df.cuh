@@ -234,10 +234,11 @@ __device__ __forceinline__ void turn_reduce(uint32_t z, uint32_t& q, bool& refl,
   dwf = small_int_to_float((int32_t)(wr - (j << 23)));
 }
 
-// sin and cos of 2 pi z / M for z in [1, M - 1].
+// |sin| and |cos| of 2 pi z / M for z in [1, M - 1], with their signs as
+// the sign-bit masks sgn_s, sgn_c of the quadrant (0 or 0x80000000).
 template <class UM>
 __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __restrict__ tab, df& sn,
-                                                 df& cs) {
+                                                 df& cs, uint32_t& sgn_s, uint32_t& sgn_c) {
   uint32_t q, j;
   bool refl;
   float dwf;
@@ -276,13 +277,12 @@ __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __res
     const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(cj.lo, __fsub_rn(qc.lo, qs.lo)));
     cp = fast_two_sum(u2.hi, lo);
   }
-  // angle = (pi/2) q + phi, phi = reflected or not
+  // angle = (pi/2) q + phi, phi = reflected or not; sp, cp >= 0
   const bool swap = refl ^ (q & 1u);
-  df s0 = swap ? cp : sp, c0 = swap ? sp : cp;
-  const float ss = (q >= 2u) ? -1.0f : 1.0f;                 // sin sign: quadrants 2, 3
-  const float cs_ = (q == 1u || q == 2u) ? -1.0f : 1.0f;     // cos sign: quadrants 1, 2
-  sn = df{s0.hi * ss, s0.lo * ss};
-  cs = df{c0.hi * cs_, c0.lo * cs_};
+  sn = swap ? cp : sp;
+  cs = swap ? sp : cp;
+  sgn_s = (q >> 1) << 31;                    // quadrants 2, 3
+  sgn_c = ((q ^ (q >> 1)) & 1u) << 31;       // quadrants 1, 2
 }
 
 // Conversion of a df to IEEE double bits, in integers (|error| <= 1 ulp of
@@ -315,18 +315,37 @@ __device__ __forceinline__ uint64_t df_to_f64_bits(df v) {
   return mag | ((uint64_t)(hb & 0x80000000u) << 32);
 }
 
+// The same for a df with hi >= 0 (or -0) and hi = 0 or |hi| >= 2^-75, given
+// the sign to set as a sign-bit mask -- the magnitudes of Box-Muller
+// outputs: a nonzero normal is at least R_min sin(2 pi / M) ~ 2e-5 * 1.5e-9
+// = 3e-14.  A zero takes the sign too (as R times a negated zero does).
+__device__ __forceinline__ uint64_t df_abs_to_f64_bits(df v, uint32_t sgn) {
+  const uint32_t ah = __float_as_uint(v.hi) & 0x7FFFFFFFu;
+  const uint64_t sb = (uint64_t)sgn << 32;
+  if (ah == 0) return sb;
+  uint64_t mag;
+  asm("mad.wide.u32 %0, %1, 536870912, 0x3800000000000000;" : "=l"(mag) : "r"(ah));  // ah 2^29 + 896 2^52
+  const float scale = __uint_as_float((306u - (ah >> 23)) << 23);                // 2^(179 - eh)
+  int32_t li = __float2int_rn(__fmul_rn(v.lo, scale));
+  if (li < 0 && (ah & 0x7FFFFFu) == 0) li *= 2;
+  return (mag + (uint64_t)(int64_t)li) | sb;
+}
+
 __device__ __forceinline__ float df_to_f32(df v) { return __fadd_rn(v.hi, v.lo); }
 
-// Box-Muller on one pair: X, Y as df (fp64 outputs).
+// Box-Muller on one pair for fp64 outputs: R |cos| and R |sin| in
+// double-float, converted to double bits with the quadrant's signs.
 template <class UM>
-__device__ __forceinline__ void box_muller_df_m(uint32_t z1, uint32_t z2,
-                                                const float4* __restrict__ tab, df& x, df& y) {
+__device__ __forceinline__ void box_muller_f64_m(uint32_t z1, uint32_t z2,
+                                                 const float4* __restrict__ tab, uint64_t& x,
+                                                 uint64_t& y) {
   const df l = ln_u_df_m<UM>(z1, tab);
   const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
   df sn, cs;
-  sincos_turn_df_m<UM>(z2, tab, sn, cs);
-  x = df_mul(R, cs);
-  y = df_mul(R, sn);
+  uint32_t sgn_s, sgn_c;
+  sincos_turn_df_m<UM>(z2, tab, sn, cs, sgn_s, sgn_c);
+  x = df_abs_to_f64_bits(df_mul(R, cs), sgn_c);
+  y = df_abs_to_f64_bits(df_mul(R, sn), sgn_s);
 }
 
 // sin and cos of 2 pi z / M for fp32 outputs, to ~2^-40 relative: the same
@@ -432,13 +451,9 @@ __device__ __forceinline__ float exp_f32_m(uint32_t z, const float4* __restrict_
 __device__ __forceinline__ df ln_u_df(uint32_t z, const float4* __restrict__ tab) {
   return ln_u_df_m<UM32k3a>(z, tab);
 }
-__device__ __forceinline__ void sincos_turn_df(uint32_t z, const float4* __restrict__ tab, df& sn,
-                                               df& cs) {
-  sincos_turn_df_m<UM32k3a>(z, tab, sn, cs);
-}
-__device__ __forceinline__ void box_muller_df(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
-                                              df& x, df& y) {
-  box_muller_df_m<UM32k3a>(z1, z2, tab, x, y);
+__device__ __forceinline__ void box_muller_f64(uint32_t z1, uint32_t z2, const float4* __restrict__ tab,
+                                               uint64_t& x, uint64_t& y) {
+  box_muller_f64_m<UM32k3a>(z1, z2, tab, x, y);
 }
 __device__ __forceinline__ df ln_u_lite(uint32_t z, const float4* __restrict__ tab) {
   return ln_u_lite_m<UM32k3a>(z, tab);
