@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(256) generate31_kernel(GenArgs a) {
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
     char* gdst = a.out + (s * a.ld + off) * ES;
 
-#pragma unroll 2
+    constexpr int UNROLL = TABLES ? 1 : 2;  // as in generate_kernel
+#pragma unroll UNROLL
     for (uint32_t i = 0; i < cmax; i += UE) {
       uint32_t wv[UW];
       produce31<DIST, DT, UE>(st, wv, c, s_tab);

@@ -287,7 +287,11 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
       }
     }
 
-#pragma unroll 2
+    // the transforms' bodies are long enough on their own: unrolled once they
+    // keep fewer registers and more warps per SM (measured 3-5 % faster for
+    // fp32 normals and both exponentials)
+    constexpr int UNROLL = TABLES ? 1 : 2;
+#pragma unroll UNROLL
     for (uint32_t i = i0; i < cmax; i += UE) {
       uint32_t wv[UW];
       produce<DIST, DT, UE>(st, wv, c, s_tab);
