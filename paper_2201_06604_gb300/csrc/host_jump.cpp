@@ -127,6 +127,16 @@ void transform_table_for(double M, double D, float out[kTransformEntries][4]) {
     split(std::sin(a), out[128 + j][0], out[128 + j][1]);
     split(std::cos(a), out[128 + j][2], out[128 + j][3]);
   }
+  // ln(C_k / (M 2^s)) = ln(C_k / M) - s ln 2 for every shift s and bucket k,
+  // as float pairs from entry 193 on (pair 128 s + k); one fused multiply-add
+  // (explicit, so that no compiler contracts it differently on another host)
+  float* ls = &out[193][0];
+  for (int sh = 0; sh < 32; ++sh)
+    for (int k = 0; k < 128; ++k) {
+      const double C = k == 127 ? M : 2147483648.0 + (2.0 * k + 1.0) * 8388608.0;
+      const double v = std::fma(-(double)sh, 0.6931471805599453094, std::log1p((C - M) / M));
+      split(v, ls[2 * (sh * 128 + k)], ls[2 * (sh * 128 + k) + 1]);
+    }
 }
 }  // namespace
 

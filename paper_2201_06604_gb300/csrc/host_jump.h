@@ -21,8 +21,10 @@ bool norm_constant_ok(uint64_t delta);
 
 // Tables of the double-float transforms (layout in transforms_df.cuh):
 // entries [0, 128): 1/C_k and ln(C_k / M) for the log buckets;
-// entries [128, 193): sin and cos of the bucket angles a_j.
-constexpr int kTransformEntries = 193;
+// entries [128, 193): sin and cos of the bucket angles a_j;
+// entries [193, 2241): ln(C_k / (M 2^s)) for every shift s < 32 and bucket k,
+// as 4096 float pairs.
+constexpr int kTransformEntries = 193 + 2048;
 void transform_table(float out[kTransformEntries][4]);
 
 // The same tables for uniforms u = z' / 2^32 (M = 2^32, quarter turn D = 2^30):

@@ -762,23 +762,39 @@ static_assert(sizeof(VariantRange) == sizeof(VariantRangeHost), "variant range l
 static_assert(kCounterStride == kBatchCounterStride, "claim counter spacing");
 
 namespace {
+// Loads one kernel now (see preload_kernels).  Kernels that copy the
+// transform tables (~36 KB of shared memory a block) prefer the largest
+// shared-memory carveout: an SM whose split a smaller configuration fixed
+// could otherwise hold none of their blocks beside a resident serving
+// worker, and they would wait for it to exit.
+template <class K>
+void load_fn(K* f, int& bad) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, f) != cudaSuccess) {
+    bad = 1;
+    return;
+  }
+  if (a.sharedSizeBytes > 16384 &&
+      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    bad = 1;
+}
+
 template <int DIST, int DT>
 void preload_gen(int& bad) {
-  cudaFuncAttributes a;
-  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 32>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 16>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 8>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate_kernel<DIST, DT, 4>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 32>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 16>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 8>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, generate31_kernel<DIST, DT, 4>) != cudaSuccess;
+  load_fn(generate_kernel<DIST, DT, 32>, bad);
+  load_fn(generate_kernel<DIST, DT, 16>, bad);
+  load_fn(generate_kernel<DIST, DT, 8>, bad);
+  load_fn(generate_kernel<DIST, DT, 4>, bad);
+  load_fn(generate31_kernel<DIST, DT, 32>, bad);
+  load_fn(generate31_kernel<DIST, DT, 16>, bad);
+  load_fn(generate31_kernel<DIST, DT, 8>, bad);
+  load_fn(generate31_kernel<DIST, DT, 4>, bad);
 }
 template <int DIST, int DT>
 void preload_tr(int& bad) {
-  cudaFuncAttributes a;
-  bad |= cudaFuncGetAttributes(&a, transform_kernel<DIST, DT>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<DIST, DT>) != cudaSuccess;
+  load_fn(transform_kernel<DIST, DT>, bad);
+  load_fn(batch_variant_kernel<DIST, DT>, bad);
 }
 }  // namespace
 
@@ -788,7 +804,6 @@ void preload_tr(int& bad) {
 // until it is stopped.
 cudaError_t preload_kernels() {
   int bad = 0;
-  cudaFuncAttributes a;
   preload_gen<MRG_RAW, MRG_U32>(bad);
   preload_gen<MRG_UNIFORM, MRG_F32>(bad);
   preload_gen<MRG_UNIFORM, MRG_F64>(bad);
@@ -802,16 +817,16 @@ cudaError_t preload_kernels() {
   preload_tr<MRG_NORMAL, MRG_F64>(bad);
   preload_tr<MRG_EXPONENTIAL, MRG_F32>(bad);
   preload_tr<MRG_EXPONENTIAL, MRG_F64>(bad);
-  bad |= cudaFuncGetAttributes(&a, batch_variant_kernel<MRG_RAW, MRG_U32>) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, create_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, create31_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, fisher_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, fill_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, jump31_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, jump_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, fused_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, batch_kernel) != cudaSuccess;
-  bad |= cudaFuncGetAttributes(&a, serve_kernel) != cudaSuccess;
+  load_fn(batch_variant_kernel<MRG_RAW, MRG_U32>, bad);
+  load_fn(create_kernel, bad);
+  load_fn(create31_kernel, bad);
+  load_fn(fisher_kernel, bad);
+  load_fn(fill_kernel, bad);
+  load_fn(jump31_kernel, bad);
+  load_fn(jump_kernel, bad);
+  load_fn(fused_kernel, bad);
+  load_fn(batch_kernel, bad);
+  load_fn(serve_kernel, bad);
   return bad ? cudaErrorInvalidDeviceFunction : cudaSuccess;
 }
 

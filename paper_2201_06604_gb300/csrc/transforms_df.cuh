@@ -12,15 +12,18 @@
 //     X = R cos Theta, Y = R sin Theta;
 //   exponential (Sec. 3.2): E = -ln(u) / rate.
 //
-// ln u (relative error ~2^-46 over the whole range):
+// ln u (relative error ~2^-46 outside the top bucket; inside it, where
+// ln u is ln(1 + r) itself, the Taylor terms from r^3 on (up to 2^-17.6 |r|)
+// are summed in fp32, which bounds it at ~2^-40 -- 1e-12 relative, measured):
 //   z = zn 2^-s with zn in [2^31, 2^32); bucket k = the 7 bits after the
 //   leading one; C_k = the bucket centre 2^31 + (2k+1) 2^23, except the top
 //   bucket whose centre is M itself.  With d = zn - C_k (exact, |d| < 2^24)
 //   and r = d / C_k (|r| <= 2^-8):
-//     ln u = -s ln 2 + ln(C_k / M) + ln(1 + r),
-//   ln(1 + r) by its Taylor series to r^6.  For z >= 2^31 in the top bucket
-//   the first two terms are exactly zero, so ln u = ln(1 + r) keeps its
-//   relative accuracy as u -> 1.
+//     ln u = ln(C_k / (M 2^s)) + ln(1 + r),
+//   the first term from a table over all 32 shifts s and 128 buckets k (a
+//   float pair each), ln(1 + r) by its Taylor series to r^6.  For z >= 2^31
+//   in the top bucket the table term is exactly zero, so ln u = ln(1 + r)
+//   keeps its relative accuracy as u -> 1.
 // sin / cos of 2 pi z / M (absolute error ~2^-47, relative near zeros):
 //   exact integer reduction z = q D + w, D = M / 4, w in [0, D); reflection
 //   w -> D - w above D/2 (swapping sin and cos); bucket j = (w + 2^22) >> 23
@@ -40,16 +43,21 @@ struct df {
   float hi, lo;
 };
 
-// Table layout (float4 entries), built on the host (host_jump.cpp):
+// Table layout (float4 entries), built on the host (host_jump.cpp) and
+// copied to shared memory by every block that transforms (35.9 KB):
 //   [0, 128)   log:  (1/C_k).hi, (1/C_k).lo, ln(C_k/M).hi, ln(C_k/M).lo
 //   [128, 193) trig: sin(a_j).hi, sin(a_j).lo, cos(a_j).hi, cos(a_j).lo
+//   [193, 2241) as 4096 float pairs: ln(C_k / (M 2^s)).hi, .lo at pair
+//              128 s + k (one load replaces -s ln 2 and its error-free sum)
 constexpr int TAB_LOG = 0;
 constexpr int TAB_TRIG = 128;
-constexpr int TAB_ENTRIES = 193;
+constexpr int TAB_LS = 193;
+constexpr int TAB_ENTRIES = 193 + 2048;
 
-// ln 2 as a float pair.
-constexpr float LN2_HI = 0x1.62e430p-1f;    // RN32(ln 2)
-constexpr float LN2_LO = -0x1.05c610p-29f;  // RN32(ln 2 - LN2_HI)
+// ln(C_k / (M 2^s)) as a float pair.
+__device__ __forceinline__ float2 log_ck_shift(const float4* __restrict__ tab, uint32_t s, uint32_t k) {
+  return reinterpret_cast<const float2*>(tab + TAB_LS)[(s << 7) | k];
+}
 
 // The modulus M of the uniform u = z / M that the transforms take, with the
 // constants of its reductions.  The tables of each M come from the host
@@ -146,14 +154,11 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   const float c3 = __fmul_rn(__fmul_rn(p2, rh), poly);
   // |r| < 2^-7, so |r| >= r^2 / 2: the order of the sum is known
   df l1p = df_add_ordered(r, df{-0.5f * p2, __fmaf_rn(-0.5f, e2, c3)});
-  // -s ln2 + ln(C_k / M) + ln(1 + r): all three are <= 0 apart from the
-  // last, and |s ln2| >= ln 2 >= |ln(C_k / M)| when s > 0, while
-  // |ln(C_k / M)| >= |ln(1 + r)| outside the top bucket (where ln(C_k / M) = 0
-  // exactly): each sum's order is known.
-  const float sf = small_int_to_float((int32_t)s);
-  const float a = __fmul_rn(-sf, LN2_HI);
-  const df sl = df{a, __fmaf_rn(-sf, LN2_LO, __fmaf_rn(-sf, LN2_HI, -a))};
-  return df_add_ordered(df_add_ordered(sl, df{T.z, T.w}), l1p);
+  // ln(C_k / (M 2^s)) + ln(1 + r): |ln(C_k / (M 2^s))| >= ln 2 when s > 0,
+  // and |ln(C_k / M)| >= |ln(1 + r)| outside the top bucket (where the table
+  // term is exactly 0), so the order of the sum is known.
+  const float2 L = log_ck_shift(tab, s, k);
+  return df_add_ordered(df{L.x, L.y}, l1p);
 }
 
 // ln(z / M) to ~2^-34 relative, for fp32 outputs (whose 2-ulp budget is
@@ -179,13 +184,10 @@ __device__ __forceinline__ df ln_u_lite_raw_m(uint32_t z, const float4* __restri
   poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
   poly = __fmaf_rn(rh, poly, -0.5f);
   const float tail = __fmul_rn(__fmul_rn(rh, rh), poly);
-  const float sf = small_int_to_float((int32_t)s);
-  const float a = __fmul_rn(-sf, LN2_HI);
-  const float a_lo = __fmaf_rn(-sf, LN2_LO, __fmaf_rn(-sf, LN2_HI, -a));
-  const df u1 = fast_two_sum(a, T.z);        // |s ln 2| >= |ln(C_k / M)|, or s = 0
-  const df u2 = fast_two_sum(u1.hi, rh);     // |ln(C_k / M)| >= |r|, or both 0
-  const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(__fadd_rn(a_lo, T.w), __fadd_rn(re, tail)));
-  return df{u2.hi, lo};  // not renormalised: in the top bucket |lo| reaches 2^-9 |hi|
+  const float2 L = log_ck_shift(tab, s, k);
+  const df u = fast_two_sum(L.x, rh);        // |ln(C_k / (M 2^s))| >= |r|, or both 0
+  const float lo = __fadd_rn(u.lo, __fadd_rn(L.y, __fadd_rn(re, tail)));
+  return df{u.hi, lo};  // not renormalised: in the top bucket |lo| reaches 2^-9 |hi|
 }
 
 // The same, renormalised (df_sqrt's single correction step needs
