@@ -190,7 +190,7 @@ __device__ __forceinline__ df ln_u_lite_raw_m(uint32_t z, const float4* __restri
   return df{u.hi, lo};  // not renormalised: in the top bucket |lo| reaches 2^-9 |hi|
 }
 
-// The same, renormalised (df_sqrt's single correction step needs
+// The same, renormalised (the square root's single correction step needs
 // |lo| <= ulp(hi)).
 template <class UM>
 __device__ __forceinline__ df ln_u_lite_m(uint32_t z, const float4* __restrict__ tab) {
@@ -206,11 +206,6 @@ __device__ __forceinline__ df df_sqrt_raw(df x) {
   const float r0 = __fmul_rn(x.hi, y);
   const float e = __fadd_rn(__fmaf_rn(-r0, r0, x.hi), x.lo);           // x - r0^2
   return df{r0, __fmul_rn(__fmul_rn(e, y), 0.5f)};
-}
-
-__device__ __forceinline__ df df_sqrt(df x) {
-  const df r = df_sqrt_raw(x);
-  return fast_two_sum(r.hi, r.lo);
 }
 
 // RN32 of a * b for a df a and b (unnormalised pairs allowed): the cross
@@ -267,17 +262,17 @@ __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __res
   const df ps = df_mul_split(cj, sd), pc = df_mul_split(sj, cm1);
   const df qs = df_mul_split(sj, sd), qc = df_mul_split(cj, cm1);
   df sp, cp;
+  // (left unnormalised, |lo| <~ 1.5 ulp(hi): their one use, df_mul by R,
+  // renormalises its product)
   {
     const df u1 = fast_two_sum(sj.hi, ps.hi);
     const df u2 = fast_two_sum(u1.hi, pc.hi);
-    const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(sj.lo, __fadd_rn(ps.lo, pc.lo)));
-    sp = fast_two_sum(u2.hi, lo);
+    sp = df{u2.hi, __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(sj.lo, __fadd_rn(ps.lo, pc.lo)))};
   }
   {
     const df u1 = fast_two_sum(cj.hi, -qs.hi);
     const df u2 = fast_two_sum(u1.hi, qc.hi);
-    const float lo = __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(cj.lo, __fsub_rn(qc.lo, qs.lo)));
-    cp = fast_two_sum(u2.hi, lo);
+    cp = df{u2.hi, __fadd_rn(__fadd_rn(u1.lo, u2.lo), __fadd_rn(cj.lo, __fsub_rn(qc.lo, qs.lo)))};
   }
   // angle = (pi/2) q + phi, phi = reflected or not; sp, cp >= 0
   const bool swap = refl ^ (q & 1u);
@@ -342,7 +337,7 @@ __device__ __forceinline__ void box_muller_f64_m(uint32_t z1, uint32_t z2,
                                                  const float4* __restrict__ tab, uint64_t& x,
                                                  uint64_t& y) {
   const df l = ln_u_df_m<UM>(z1, tab);
-  const df R = df_sqrt(df{-2.0f * l.hi, -2.0f * l.lo});
+  const df R = df_sqrt_raw(df{-2.0f * l.hi, -2.0f * l.lo});   // df_mul renormalises
   df sn, cs;
   uint32_t sgn_s, sgn_c;
   sincos_turn_df_m<UM>(z2, tab, sn, cs, sgn_s, sgn_c);
