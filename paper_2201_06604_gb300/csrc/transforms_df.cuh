@@ -143,7 +143,11 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   const uint32_t ck = k == 127u ? UM::TOP_CK : 0x80800000u + (k << 24);
   const int32_t d = (int32_t)(zn - ck);                 // |d| < 2^24: exact in fp32
   const float4 T = tab[TAB_LOG + k];
-  const df r = df_mul_f(df{T.x, T.y}, (float)d);        // r = d / C_k
+  // r = d / C_k as the exact leading product plus the rest (not
+  // renormalised: every use below takes both parts)
+  const float dfl = (float)d;
+  const float rp = __fmul_rn(T.x, dfl);
+  const df r{rp, __fmaf_rn(T.y, dfl, __fmaf_rn(T.x, dfl, -rp))};
   // ln(1 + r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6)
   const float rh = r.hi;
   const float p2 = __fmul_rn(rh, rh);
