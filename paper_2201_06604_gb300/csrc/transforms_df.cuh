@@ -14,7 +14,7 @@
 //
 // ln u (relative error ~2^-46 outside the top bucket; inside it, where
 // ln u is ln(1 + r) itself, the Taylor terms from r^3 on (up to 2^-17.6 |r|)
-// are summed in fp32, which bounds it at ~2^-40 -- 1e-12 relative, measured):
+// are summed in fp32, which bounds it at ~2^-40 -- 1.3e-12 relative, measured):
 //   z = zn 2^-s with zn in [2^31, 2^32); bucket k = the 7 bits after the
 //   leading one; C_k = the bucket centre 2^31 + (2k+1) 2^23, except the top
 //   bucket whose centre is M itself.  With d = zn - C_k (exact, |d| < 2^24)
