@@ -9,12 +9,16 @@
 //     g31::uniform_bits32(z) equal the bits of (double)z * 2^-31 and of its
 //     rounding to float (MRG31k3p).
 //   mode "step31" n seed: prints n outputs of g31::step from a state.
+//   mode "tables": prints the double-float transform tables the library
+//     uploads (host_jump.cpp, linked in), for M = m1 + 1 (table 0) and
+//     M = 2^32 (table 1), one float4 entry a line as hex floats.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
 #include "../../paper_2201_06604_gb300/csrc/mrg32k3a_core.cuh"
 #include "../../paper_2201_06604_gb300/csrc/mrg31k3p_core.cuh"
+#include "../../paper_2201_06604_gb300/csrc/host_jump.h"
 
 static int check_uniform(unsigned lo, unsigned hi) {
   volatile double norm_v = 1.0 / 4294967088.0;
@@ -60,7 +64,21 @@ static int check_uniform31() {
   return bad != 0;
 }
 
+static float g_tab[mrg::host::kTransformEntries][4];
+
+static int print_tables() {
+  for (int t = 0; t < 2; ++t) {
+    if (t == 0) mrg::host::transform_table(g_tab);
+    else mrg::host::transform_table_m32(g_tab);
+    for (int i = 0; i < mrg::host::kTransformEntries; ++i)
+      std::printf("%d %d %a %a %a %a\n", t, i, (double)g_tab[i][0], (double)g_tab[i][1],
+                  (double)g_tab[i][2], (double)g_tab[i][3]);
+  }
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc >= 2 && !std::strcmp(argv[1], "tables")) return print_tables();
   if (argc >= 2 && !std::strcmp(argv[1], "uniform31")) return check_uniform31();
   if (argc >= 9 && !std::strcmp(argv[1], "step31")) {
     long n = std::atol(argv[2]);
@@ -87,6 +105,6 @@ int main(int argc, char** argv) {
     std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
     return 0;
   }
-  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5\n");
+  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5 | tables\n");
   return 2;
 }

@@ -5,7 +5,10 @@ own header and checked on the CPU (no GPU needed):
   every z in [1, m1] (exhaustive), and the fp32 uniform equals its rounding;
 * the folded modular step reproduces the oracle's plain `%` recurrence;
 * the same for MRG31k3p, the paper's own generator: its exact fp64 uniform
-  z / 2^31 and fp32 rounding for every z, and its step against the oracle.
+  z / 2^31 and fp32 rounding for every z, and its step against the oracle;
+* every entry of the transform tables the library builds on the host (1/C_k,
+  ln(C_k / M), sin and cos of the bucket angles, ln(C_k / (M 2^s)) for all
+  shifts), as float pairs, against 50-digit values from mpmath.
 """
 import os
 import shutil
@@ -18,6 +21,7 @@ import oracle as O
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "host_harness", "uniform_exhaustive.cu")
+HOST_JUMP = os.path.join(HERE, "..", "paper_2201_06604_gb300", "csrc", "host_jump.cpp")
 BIN = os.path.join(HERE, "host_harness", "_build", "harness")
 
 
@@ -28,11 +32,12 @@ def harness():
     os.makedirs(os.path.dirname(BIN), exist_ok=True)
     csrc = os.path.join(HERE, "..", "paper_2201_06604_gb300", "csrc")
     if not os.path.exists(BIN) or os.path.getmtime(BIN) < max(
-            os.path.getmtime(SRC),
+            os.path.getmtime(SRC), os.path.getmtime(HOST_JUMP),
+            os.path.getmtime(os.path.join(csrc, "host_jump.h")),
             os.path.getmtime(os.path.join(csrc, "mrg32k3a_core.cuh")),
             os.path.getmtime(os.path.join(csrc, "mrg31k3p_core.cuh"))):
         subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fopenmp",
-                        "-Xcompiler", "-ffp-contract=off", "-o", BIN, SRC], check=True)
+                        "-Xcompiler", "-ffp-contract=off", "-o", BIN, SRC, HOST_JUMP], check=True)
     return BIN
 
 
@@ -89,3 +94,40 @@ def test_step31_matches_oracle(harness):
         want, after = O.raw(np.array(st, np.uint32), n, gen=O.MRG31K3P)
         assert [int(v) for v in lines[:n]] == [int(v) for v in want], st
         assert [int(v) for v in lines[n].split()] == [int(v) for v in after], st
+
+
+def test_transform_tables_against_high_precision(harness):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    r = subprocess.run([harness, "tables"], capture_output=True, text=True, timeout=120, check=True)
+    tabs = {0: {}, 1: {}}
+    for line in r.stdout.split("\n"):
+        if line:
+            f = line.split()
+            tabs[int(f[0])][int(f[1])] = [float.fromhex(v) for v in f[2:]]
+    bound = mp.mpf(2) ** -47           # a float pair holds ~48 bits
+
+    def close(hi, lo, want):
+        got = mp.mpf(hi) + mp.mpf(lo)
+        if want == 0:
+            return hi == 0 and lo == 0
+        return abs(got - want) <= bound * abs(want)
+
+    for t, M in ((0, O.MRG32K3A[0] + 1), (1, 1 << 32)):
+        tab = tabs[t]
+        D = M // 4
+        C = [M if k == 127 else (1 << 31) + (2 * k + 1) * (1 << 23) for k in range(128)]
+        for k in range(128):
+            e = tab[k]
+            assert close(e[0], e[1], mp.mpf(1) / C[k]), (t, k)
+            assert close(e[2], e[3], mp.log(mp.mpf(C[k]) / M)), (t, k)
+        for j in range(65):
+            a = mp.pi / 2 * j * (1 << 23) / D
+            e = tab[128 + j]
+            assert close(e[0], e[1], mp.sin(a)), (t, j)
+            assert close(e[2], e[3], mp.cos(a)), (t, j)
+        for s in range(32):
+            for k in range(128):
+                i = 128 * s + k
+                e = tab[193 + i // 2][2 * (i % 2):2 * (i % 2) + 2]
+                assert close(e[0], e[1], mp.log(mp.mpf(C[k]) / (mp.mpf(M) * 2 ** s))), (t, s, k)
