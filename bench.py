@@ -35,8 +35,8 @@ ES = {"f64": 8, "f32": 4, "u32": 4}
 # the recurrence is integer multiply-add work), so the dominant kernel's
 # roofline is issue slots: 4 warp-instructions per cycle per SM.
 INSTR_PER_OUTPUT = {("raw", "u32"): 27.4, ("uniform", "f64"): 43.0, ("uniform", "f32"): 37.5,
-                    ("normal", "f64"): 140.2, ("normal", "f32"): 88.6,
-                    ("exponential", "f32"): 63.8, ("exponential", "f64"): 109.7}
+                    ("normal", "f64"): 134.2, ("normal", "f32"): 88.6,
+                    ("exponential", "f32"): 63.8, ("exponential", "f64"): 106.7}
 SM_COUNT = 152
 
 
@@ -175,9 +175,9 @@ def run_reference(args):
 
 # DRAM bytes (read + write) per output of generate_kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 65536 streams x 4096 draws.
-TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.822, ("uniform", "f32"): 3.813,
-                      ("normal", "f64"): 7.818, ("normal", "f32"): 3.810,
-                      ("exponential", "f32"): 3.809}
+TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.824, ("uniform", "f32"): 3.814,
+                      ("normal", "f64"): 7.817, ("normal", "f32"): 3.809,
+                      ("exponential", "f32"): 3.810}
 
 
 def roofline(dom, hbm, peak_kind, issue_peak, total_out):
