@@ -491,9 +491,10 @@ def run_gpu(args):
     adv_ms = e0.elapsed_time(e1) / 20
 
     # HBM write bandwidth measured live: the library's write-only stream
-    # kernel (the generate kernels' store pattern) over the whole output
-    # buffer (8 GiB), best of 5 -- the write ceiling of the materialised
-    # variants; the roofline's peak stays the measured copy bandwidth
+    # kernel (each warp fills its own contiguous chunk, 1 KiB per store --
+    # the fastest write pattern measured) over the whole output buffer
+    # (8 GiB), best of 5 -- the write ceiling of the materialised variants;
+    # the roofline's peak stays the measured copy bandwidth
     write_gbs = None
     if not args.quick:
         fills = []

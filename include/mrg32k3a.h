@@ -209,10 +209,10 @@ int mrg_generate_matrix(const mrg_streams *s, int generator, uint64_t nrow, uint
 /* ---- write-bandwidth calibration ---------------------------------------- */
 
 /* Fills out[0 .. n_words) (device, 32-byte aligned, n_words a multiple of 8)
- * with `value` using the store pattern of the generate kernels (each lane
- * writes whole 32-byte sectors): a write-only stream whose bandwidth is the
- * ceiling the materialised generation is measured against.  Not part of the
- * paper's method.  Errors: MRG_EINVAL, MRG_ECUDA. */
+ * with `value`, every warp writing its own contiguous chunk 1 KiB per store
+ * instruction (the fastest write-only pattern measured): a write-only stream
+ * whose bandwidth is the ceiling the materialised generation is measured
+ * against.  Not part of the paper's method.  Errors: MRG_EINVAL, MRG_ECUDA. */
 int mrg_fill_u32(void *out, uint64_t n_words, uint32_t value, void *stream);
 
 /* ---- Monte Carlo Fisher's exact test (Sec. 4) ---------------------------- */

@@ -311,12 +311,14 @@ def test_generate_host_matches_device(M, dist, dtype):
     assert np.array_equal(M.get_state(a), M.get_state(b))
 
 
-def test_fill_writes_every_word(M):
-    t = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
-    M.fill_u32(t[8:8 + 4096], 0x12345678)
+@pytest.mark.parametrize("n", [8, 4096, 8 * 1000, 8 * 12345, 8 * (152 * 8 * 8 * 32 + 7), 1 << 24])
+def test_fill_writes_every_word(M, n):
+    # sizes below, at and above one 1 KiB chunk per warp, ragged chunk counts
+    t = torch.zeros(n + 64, dtype=torch.int32, device="cuda")
+    M.fill_u32(t[8:8 + n], 0x12345678)
     torch.cuda.synchronize()
     h = t.cpu().numpy()
-    assert (h[8:8 + 4096] == 0x12345678).all() and (h[:8] == 0).all() and (h[8 + 4096:] == 0).all()
+    assert (h[8:8 + n] == 0x12345678).all() and (h[:8] == 0).all() and (h[8 + n:] == 0).all()
     with pytest.raises(M.MrgError):
         M.fill_u32(t[1:9])                       # not 32-byte aligned
     with pytest.raises(M.MrgError):
