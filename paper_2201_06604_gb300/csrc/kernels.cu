@@ -309,11 +309,13 @@ __global__ void __launch_bounds__(256) generate_kernel(GenArgs a) {
 
 // ---------------------------------------------------------------------------
 // Write-only stream (calibration of the HBM write bandwidth the generate
-// kernels are held against): every warp fills its own contiguous chunk of
-// `chunk` 32-byte units front to back, 1 KiB per store instruction -- the
-// fastest write-only pattern measured on GB300 (~7.5 TB/s, against ~6.5 for
-// a grid-stride loop over 1 KiB units and ~4.2 for one 32-byte unit per lane
-// and row per instruction, the generate kernels' own pattern).
+// kernels are held against): one warp per 128 KiB chunk, filled front to
+// back at 1 KiB per store instruction, the grid covering the whole buffer
+// (warps in launch order, so the chunks being written at any moment are
+// neighbours) -- the fastest write-only pattern measured on GB300 (~7.5
+// TB/s, against ~6.5 for a persistent grid-stride loop over 1 KiB units and
+// ~4.2 for one 32-byte unit per lane and row per instruction, the generate
+// kernels' own pattern).
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) fill_kernel(char* out, uint64_t units, uint64_t chunk,
@@ -663,10 +665,10 @@ cudaError_t launch_matrix(bool g31, uint32_t* cur, uint64_t stride, uint64_t nro
 
 cudaError_t launch_fill(void* out, uint64_t units, uint32_t v, cudaStream_t st) {
   if (units == 0) return cudaSuccess;
-  const unsigned grid = grid_for(units, 256, 8);
-  const uint64_t warps = (uint64_t)grid * 8;
-  const uint64_t chunk = ((units + warps - 1) / warps + 31) / 32 * 32;   // whole KiB per warp
-  fill_kernel<<<grid, 256, 0, st>>>(static_cast<char*>(out), units, chunk, v);
+  constexpr uint64_t chunk = 4096;                       // 32-byte units: 128 KiB per warp
+  const uint64_t blocks = (units + 8 * chunk - 1) / (8 * chunk);
+  if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<char*>(out), units, chunk, v);
   return after_launch();
 }
 
