@@ -806,6 +806,11 @@ void preload_tr(int& bad) {
   load_fn(transform_kernel<DIST, DT>, bad);
   load_fn(batch_variant_kernel<DIST, DT>, bad);
 }
+template <int DIST, int DT>
+void preload_matrix(int& bad) {
+  load_fn(matrix_kernel<false, DIST, DT>, bad);
+  load_fn(matrix_kernel<true, DIST, DT>, bad);
+}
 }  // namespace
 
 // Loads every kernel of the library now.  With CUDA's lazy module loading a
@@ -828,6 +833,11 @@ cudaError_t preload_kernels() {
   preload_tr<MRG_EXPONENTIAL, MRG_F32>(bad);
   preload_tr<MRG_EXPONENTIAL, MRG_F64>(bad);
   load_fn(batch_variant_kernel<MRG_RAW, MRG_U32>, bad);
+  preload_matrix<MRG_RAW, MRG_U32>(bad);
+  preload_matrix<MRG_UNIFORM, MRG_F32>(bad);
+  preload_matrix<MRG_UNIFORM, MRG_F64>(bad);
+  preload_matrix<MRG_EXPONENTIAL, MRG_F32>(bad);
+  preload_matrix<MRG_EXPONENTIAL, MRG_F64>(bad);
   load_fn(create_kernel, bad);
   load_fn(create31_kernel, bad);
   load_fn(fisher_kernel, bad);
