@@ -397,7 +397,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    from paper_2201_06604_gb300 import mrg
+    from paper_2201_06604_gb300 import mrg, shard
     from paper_2201_06604_gb300 import workloads as W
 
     dev = torch.device("cuda", local_rank)
@@ -413,9 +413,7 @@ def run_gpu(args):
         variants_run = tuple(tuple(v.split(":")) for v in args.only.split(","))
     total_out = ns * n
     # Replicas: rank r owns streams [r ns, (r+1) ns) of the creator sequence.
-    seed = tuple(W.PAPER_SEED)
-    for _ in range(rank):
-        seed = mrg.create_streams(ns, device=dev, seed=seed).next_seed
+    seed = shard.rank_seed(W.PAPER_SEED, rank, ns)
     s = mrg.Streams(ns, dev)
     buf = torch.empty(total_out * 8, dtype=torch.uint8, device=dev)
     outs = {"f64": buf.view(torch.float64).view(ns, n),
@@ -473,11 +471,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches = mrg.launch_count() - launches0
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(t_start.elapsed_time(t_end), dev)
     per_step_ms = ms / K
 
     # advance kernel cost (mrg_skip runs the same jump kernel the generate
@@ -530,7 +524,7 @@ def run_gpu(args):
 
     draws_step = total_out * len(variants_run)
     bytes_step = sum(total_out * ES[dt] for _, dt in variants_run)
-    value = draws_step * world / (per_step_ms / 1e3)
+    value = shard.whole_job_rate(draws_step, world, per_step_ms)
 
     # e2e through the public API with host buffers: every variant generated
     # into pinned host memory by mrg_generate_host (chunked; the copy of one

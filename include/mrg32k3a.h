@@ -88,6 +88,15 @@ const char *mrg_version(void);
  * zero.  Returns MRG_OK or MRG_EINVAL. */
 int mrg_seed_check(const uint32_t seed[6]);
 
+/* The creator state after n_streams streams: seed advanced n_streams * 2^127
+ * steps -- the next_seed of mrg_create_streams -- computed on the host,
+ * creating no stream and touching no device (Sec. 2.1: each new stream jumps
+ * ahead from the previous one).  For example the seed of a shard whose
+ * streams start n_streams into the creator's sequence.  out (host) receives
+ * the six words; it may alias seed.  Errors: MRG_EINVAL (seed invalid, seed
+ * or out NULL), MRG_ERANGE (n_streams > 2^63). */
+int mrg_creator_advance(const uint32_t seed[6], uint64_t n_streams, uint32_t out[6]);
+
 /* Creates n streams from the creator state `seed` (Sec. 2.1 setBaseCreator /
  * createStreamsGpu): stream i starts i * 2^127 steps after seed, exactly as if
  * the streams had been created one after another.  Writes cur = start = sub
@@ -259,6 +268,10 @@ int mrg_fisher_sim(const mrg_streams *s, const int32_t *table, uint32_t I, uint3
 
 /* x1 words < 2^31 - 1, x2 words < 2^31 - 21069, neither triple all zero. */
 int mrg31k3p_seed_check(const uint32_t seed[6]);
+
+/* mrg_creator_advance for MRG31k3p: seed advanced n_streams * 2^134 steps,
+ * on the host.  Errors: as mrg_creator_advance. */
+int mrg31k3p_creator_advance(const uint32_t seed[6], uint64_t n_streams, uint32_t out[6]);
 
 /* mrg_create_streams for MRG31k3p: stream i starts i * 2^134 steps after
  * seed (Sec. 2.1, createStreamsGpu); next_seed (may be NULL) receives the

@@ -108,6 +108,18 @@ int mrg_seed_check(const uint32_t seed[6]) {
   return MRG_OK;
 }
 
+int mrg_creator_advance(const uint32_t seed[6], uint64_t n_streams, uint32_t out[6]) {
+  int rc = mrg_seed_check(seed);
+  if (rc) return rc;
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  if (n_streams > (1ull << 63)) return fail(MRG_ERANGE, "too many streams");
+  uint32_t t[6];
+  std::memcpy(t, seed, sizeof t);
+  mrg::host::jump_pow2_multiple(t, n_streams, mrg::STREAM_LOG2);
+  std::memcpy(out, t, sizeof t);
+  return MRG_OK;
+}
+
 int mrg_create_streams(const uint32_t seed[6], uint64_t n, const mrg_streams* s,
                        uint32_t next_seed[6], void* stream) {
   int rc = mrg_seed_check(seed);
@@ -300,6 +312,18 @@ int mrg31k3p_seed_check(const uint32_t seed[6]) {
   if (!mrg::host::g31::state_valid(seed))
     return fail(MRG_EINVAL, "invalid MRG31k3p seed: need x1 words < 2^31 - 1, x2 words < "
                             "2^31 - 21069, no all-zero triple");
+  return MRG_OK;
+}
+
+int mrg31k3p_creator_advance(const uint32_t seed[6], uint64_t n_streams, uint32_t out[6]) {
+  int rc = mrg31k3p_seed_check(seed);
+  if (rc) return rc;
+  if (!out) return fail(MRG_EINVAL, "out is NULL");
+  if (n_streams > (1ull << 63)) return fail(MRG_ERANGE, "too many streams");
+  uint32_t t[6];
+  std::memcpy(t, seed, sizeof t);
+  mrg::host::g31::jump_pow2_multiple(t, n_streams, mrg::host::g31::kStreamLog2);
+  std::memcpy(out, t, sizeof t);
   return MRG_OK;
 }
 

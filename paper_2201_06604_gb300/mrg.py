@@ -97,6 +97,8 @@ def _load():
         "mrg_version": ([], ctypes.c_char_p),
         "mrg_seed_check": ([u32p], i32),
         "mrg_create_streams": ([u32p, u64, sp, u32p, vp], i32),
+        "mrg_creator_advance": ([u32p, u64, u32p], i32),
+        "mrg31k3p_creator_advance": ([u32p, u64, u32p], i32),
         "mrg_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
         "mrg_skip": ([sp, u64, u64, vp], i32),
         "mrg_transform": ([vp, u64, i32, i32, ctypes.c_double, vp, vp], i32),
@@ -252,6 +254,18 @@ def set_base_creator(seed=DEFAULT_SEED):
         raise MrgError(EINVAL, "invalid seed")
     with _creator.lock:
         _creator.seed = [int(v) for v in seed]
+
+
+def creator_advance(seed, n_streams: int, generator: str = "mrg32k3a") -> tuple:
+    """The creator state after n_streams streams (seed advanced n_streams *
+    2^127 steps for MRG32k3a, 2^134 for MRG31k3p), on the host: the seed of
+    a shard whose streams start n_streams into the creator's sequence."""
+    if generator not in GENERATORS:
+        raise ValueError(f"generator must be one of {GENERATORS}")
+    out = (ctypes.c_uint32 * 6)()
+    fn = lib.mrg31k3p_creator_advance if generator == "mrg31k3p" else lib.mrg_creator_advance
+    _check(fn(_u32_array(seed), int(n_streams), out))
+    return tuple(int(v) for v in out)
 
 
 def get_base_creator():
