@@ -1,0 +1,122 @@
+"""The C ABI's documented argument errors, decided on the host before any
+device work (no GPU needed): every case below must be refused by the
+entry point's validation, which runs before the library touches a device.
+
+The stream descriptors here carry non-null placeholder addresses that are
+never dereferenced -- so the module runs only where no CUDA device exists
+(on a machine with one, a validation regression must not become a launch).
+"""
+import ctypes
+
+import pytest
+import torch
+
+from paper_2201_06604_gb300 import mrg
+
+pytestmark = pytest.mark.skipif(torch.cuda.is_available(),
+                                reason="placeholder device addresses: host-only checks")
+
+L = mrg.lib
+GOOD = (12345,) * 6
+FAKE = 0x100000                                  # 1 MiB: aligned, never dereferenced
+
+
+def seed(v):
+    return (ctypes.c_uint32 * 6)(*v)
+
+
+def fake_streams(n=16, stride=16):
+    return mrg._Streams(FAKE, FAKE, FAKE, n, stride)
+
+
+def test_create_streams_errors():
+    nxt = (ctypes.c_uint32 * 6)()
+    assert L.mrg_create_streams(seed((0, 0, 0, 1, 2, 3)), 1, None, nxt, None) == mrg.EINVAL
+    assert L.mrg_create_streams(seed(GOOD), (1 << 63) + 1, None, nxt, None) == mrg.ERANGE
+    assert L.mrg_create_streams(seed(GOOD), 5, None, nxt, None) == mrg.EINVAL
+    s = fake_streams(n=4, stride=4)
+    assert L.mrg_create_streams(seed(GOOD), 5, ctypes.byref(s), nxt, None) == mrg.EINVAL
+    assert b"exceeds" in L.mrg_last_error()
+    # n = 0 creates nothing and only reports the creator (no device work)
+    assert L.mrg_create_streams(seed(GOOD), 0, None, nxt, None) == mrg.OK
+    assert tuple(nxt) == GOOD
+
+
+def test_generate_errors():
+    s = fake_streams()
+    sp = ctypes.byref(s)
+    g = L.mrg_generate
+    assert g(None, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 8, None) == mrg.EINVAL
+    bad = mrg._Streams(FAKE, None, FAKE, 16, 16)
+    assert g(ctypes.byref(bad), 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 8, None) == mrg.EINVAL
+    narrow = mrg._Streams(FAKE, FAKE, FAKE, 16, 8)                 # stride < n
+    assert g(ctypes.byref(narrow), 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.NORMAL, mrg.U32, 1.0, FAKE, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.RAW, mrg.F64, 1.0, FAKE, 8, None) == mrg.EINVAL
+    for rate in (0.0, -1.0, 2.0 ** -65, 2.0 ** 65, float("nan")):
+        assert g(sp, 8, mrg.EXPONENTIAL, mrg.F64, rate, FAKE, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.UNIFORM, mrg.F64, 1.0, None, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 7, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE + 4, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.UNIFORM, mrg.F32, 1.0, FAKE + 2, 8, None) == mrg.EINVAL
+    assert g(sp, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 1 << 61, None) == mrg.ERANGE
+    assert g(sp, (1 << 62) + 1, mrg.RAW, mrg.U32, 1.0, FAKE, (1 << 62) + 1, None) == mrg.ERANGE
+    # an empty request is a no-op
+    assert g(sp, 0, mrg.UNIFORM, mrg.F64, 1.0, None, 0, None) == mrg.OK
+
+
+def test_transform_and_matrix_errors():
+    t = L.mrg_transform
+    assert t(FAKE, 8, mrg.RAW, mrg.U32, 1.0, FAKE, None) == mrg.EINVAL
+    assert t(FAKE, 8, mrg.EXPONENTIAL, mrg.F32, 0.0, FAKE, None) == mrg.EINVAL
+    assert t(None, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, None) == mrg.EINVAL
+    assert t(FAKE + 2, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE, None) == mrg.EINVAL
+    assert t(FAKE, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE + 4, None) == mrg.EINVAL
+    assert t(None, 0, mrg.UNIFORM, mrg.F64, 1.0, None, None) == mrg.OK
+    s = fake_streams(n=16, stride=16)
+    sp = ctypes.byref(s)
+    m = L.mrg_generate_matrix
+    assert m(sp, 7, 4, 4, 2, 2, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 4, None) == mrg.EINVAL
+    assert m(sp, 0, 4, 4, 2, 2, mrg.NORMAL, mrg.F64, 1.0, FAKE, 4, None) == mrg.EINVAL
+    assert m(sp, 0, 4, 4, 0, 2, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 4, None) == mrg.EINVAL
+    assert m(sp, 0, 4, 4, 8, 4, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 4, None) == mrg.EINVAL  # 32 > 16 streams
+    assert m(sp, 0, 4, 4, 2, 2, mrg.UNIFORM, mrg.F64, 1.0, FAKE, 3, None) == mrg.EINVAL  # ld < ncol
+
+
+def test_fill_and_fisher_errors():
+    assert L.mrg_fill_u32(FAKE + 16, 8, 0, None) == mrg.EINVAL
+    assert L.mrg_fill_u32(FAKE, 12, 0, None) == mrg.EINVAL
+    assert L.mrg_fill_u32(None, 8, 0, None) == mrg.EINVAL
+    assert L.mrg_fill_u32(None, 0, 0, None) == mrg.OK
+    assert L.mrg_fisher_scratch_bytes(100) == 1024 + 8 * 101
+    s = fake_streams()
+    sp = ctypes.byref(s)
+    cnt = ctypes.c_uint64()
+    f = L.mrg_fisher_sim
+
+    def table(vals):
+        return (ctypes.c_int32 * len(vals))(*vals)
+
+    ok2x2 = table([3, 1, 1, 3])
+    scratch = FAKE
+    nbytes = L.mrg_fisher_scratch_bytes(8)
+    assert f(sp, ok2x2, 1, 4, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
+    assert f(sp, ok2x2, 2, 65, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
+    assert f(sp, table([3, -1, 1, 3]), 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None,
+             None) == mrg.EINVAL
+    big = table([1 << 23, 1 << 23, 1, 1])
+    assert f(sp, big, 2, 2, 100, scratch, 1 << 30, None, ctypes.byref(cnt), None,
+             None) == mrg.ERANGE
+    assert f(sp, ok2x2, 2, 2, 100, scratch, nbytes - 8, None, ctypes.byref(cnt), None,
+             None) == mrg.EINVAL                                        # scratch too small
+    assert f(sp, None, 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
+
+
+def test_mrg31k3p_errors():
+    nxt = (ctypes.c_uint32 * 6)()
+    assert L.mrg31k3p_create_streams(seed((2147483647, 1, 1, 1, 1, 1)), 1, None, nxt,
+                                     None) == mrg.EINVAL
+    assert L.mrg31k3p_create_streams(seed(GOOD), 3, None, nxt, None) == mrg.EINVAL
+    s = fake_streams()
+    assert L.mrg31k3p_generate(ctypes.byref(s), 8, mrg.NORMAL, mrg.U32, 1.0, FAKE, 8,
+                               None) == mrg.EINVAL
