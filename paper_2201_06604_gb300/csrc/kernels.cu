@@ -3,8 +3,14 @@
 //   create_kernel    stream i = A^(i 2^127) seed, one thread per stream
 //                    (Sec. 2.1: equal to creating the streams one after another)
 //   jump_kernel      x <- A^k x for every stream (skip, substreams, advance)
-//   generate_kernel  the recurrence in registers + transform + staged store
+//   generate_kernel  the recurrence in registers + transform + 32-byte stores
 //   fused_kernel     no-store consumer: quarter-circle count and normal sum
+//   transform_kernel the transforms of caller-provided raw draws
+//   fill_kernel      write-only stream (the write ceiling generate is held to)
+//   matrix_kernel    the paper's work-item matrix layout (matrix_kernels.cuh)
+//   fisher_kernel    Monte Carlo Fisher's exact test (fisher_kernels.cuh)
+//   batch / serve    batched and served requests (batch_kernels.cuh,
+//                    serve_kernels.cuh); MRG31k3p kernels in gen31_kernels.cuh
 //
 // Work decomposition of generate: every stream's n outputs are cut into
 // segments of L draws; a lane owns one (stream, segment) pair, jumps to the
@@ -14,10 +20,12 @@
 // offset whenever ns >= 32 and the jump's table reads are warp-uniform.
 // Each lane's outputs are contiguous in its row, so a lane stores whole
 // 32-byte sectors with one 256-bit st.global per 32 bytes: the L2 receives
-// full-sector writes and nothing is staged in shared memory.  (A staged
-// variant -- per-lane shared-memory rows drained by cp.async.bulk -- was
-// measured slower: its shared memory capped occupancy at 3 blocks per SM,
-// and the recurrence is bound by integer issue, not by the store path.)
+// full-sector writes and nothing is staged in shared memory.  (Staged
+// variants -- per-lane shared-memory rows drained by cp.async.bulk, or lane
+// quads transposed through shared memory to store 128 contiguous bytes per
+// row -- were measured slower: the first capped occupancy at 3 blocks per
+// SM, the second added address arithmetic to the IMAD pipe that bounds the
+// recurrence.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
