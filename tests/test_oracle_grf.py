@@ -37,6 +37,14 @@ def test_half_integer_shapes_closed_forms(shape, closed):
     assert np.allclose(got, var * closed(x), rtol=1e-12, atol=0)
 
 
+def test_far_tail_stays_positive():
+    # kappa = 1/2 at x = 700: variance e^-700, far below any covariance that
+    # matters but representable -- the oracle must not underflow to 0 early
+    x = 700.0
+    got = grf.matern(np.array([x / 2.0]), 0.5, 1.0, 1.3)[0]      # x = sqrt(4) d / phi
+    assert got > 0 and got == pytest.approx(1.3 * np.exp(-x), rel=1e-12)
+
+
 @pytest.mark.parametrize("shape", [0.6, 1.25, 2.15, 3.0])
 def test_variance_on_diagonal_and_continuity(shape):
     assert grf.matern(np.array([0.0]), shape, 50e3, 2.0)[0] == 2.0
