@@ -28,6 +28,8 @@ METRIC = "MRG32k3a draws/s & GB/s vs HBM peak; batched/plain speedup; p99 latenc
 VARIANTS = (("uniform", "f64"), ("uniform", "f32"), ("normal", "f64"), ("normal", "f32"),
             ("exponential", "f32"))
 ES = {"f64": 8, "f32": 4, "u32": 4}
+DTYPE_NOTE = ("exact 32-bit integer recurrence; uniforms formed in integers; normals and "
+              "exponentials in double-float (fp32 pairs); fp64 and fp32 outputs")
 
 # Warp-level instructions issued per output by generate_kernel, measured with
 # ncu (smsp__inst_executed.sum x 32 / outputs) on 16384 streams x 4096 draws.
@@ -37,7 +39,6 @@ ES = {"f64": 8, "f32": 4, "u32": 4}
 INSTR_PER_OUTPUT = {("raw", "u32"): 27.4, ("uniform", "f64"): 43.0, ("uniform", "f32"): 37.5,
                     ("normal", "f64"): 134.2, ("normal", "f32"): 88.6,
                     ("exponential", "f32"): 63.8, ("exponential", "f64"): 106.7}
-SM_COUNT = 152
 
 
 def env_rank():
@@ -158,7 +159,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "draws/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32+fp64/fp32",
+            "dtype_note": DTYPE_NOTE, "data": "synthetic",
             "config": {"workload": "materialised generation, 65536 streams x 16384 draws x 5 "
                                    "variants (fp64/fp32 uniform, fp64/fp32 normal, fp32 Exp(1))",
                        "sample": sample},
@@ -180,20 +182,26 @@ TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.824, ("uniform", "f32"): 3.814,
                       ("exponential", "f32"): 3.810}
 
 
-def roofline(dom, hbm, peak_kind, issue_peak, total_out):
+def roofline(dom, hbm, peak_kind, issue_peak, total_out, sm_count):
+    """The dominant kernel against the HBM roofline: algorithmic bytes (8 or 4
+    B written per draw + 24 B of state read per stream) per launch over its
+    CUDA-event duration, against the measured copy bandwidth.  The issue-slot
+    fraction (instructions per output from ncu x outputs / duration, against
+    4 warp-instructions per cycle per SM) sits beside it: it is what holds
+    the transform kernels below the HBM line on a part with weak FP64."""
     key = (dom["dist"], dom["dtype"])
     traffic = TRAFFIC_PER_OUTPUT.get(key)
     traffic = traffic * total_out if traffic else None
-    if "issue_tinst_s" in dom and dom["hbm_frac"] < 0.5:
-        return {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>", "bound": "alu",
-                "achieved": dom["issue_tinst_s"], "peak": issue_peak, "unit": "Tinst/s",
-                "frac": dom["issue_tinst_s"] / issue_peak, "traffic": traffic,
-                "peak_source": "issue slots: 4 warp-instructions/cycle/SM x 152 SMs x "
-                               "sm_max_mhz (MEASURED_PEAKS.json) x 32 threads",
-                "hbm_gbs": dom["gbs"], "hbm_frac": dom["hbm_frac"]}
-    return {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>", "bound": "hbm",
-            "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["hbm_frac"],
-            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs"}
+    out = {"kernel": f"generate_kernel<{dom['dist']},{dom['dtype']}>", "bound": "hbm",
+           "achieved": dom["gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["hbm_frac"],
+           "traffic": traffic, "algo_bytes_per_launch": dom["algo_bytes"],
+           "ms_per_launch": dom["ms"], "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+    if "issue_tinst_s" in dom:
+        out.update({"issue_achieved_tinst_s": dom["issue_tinst_s"], "issue_peak_tinst_s": issue_peak,
+                    "issue_frac": dom["issue_tinst_s"] / issue_peak,
+                    "issue_peak_source": f"4 warp-instructions/cycle/SM x {sm_count} SMs x "
+                                         "sm_max_mhz (MEASURED_PEAKS.json) x 32 threads"})
+    return out
 
 
 def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3, tune=True):
@@ -251,6 +259,21 @@ def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3, tune=True):
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) / reps
     identical = all(torch.equal(a, q["out"]) for a, q in zip(outs_b, plain))
+    # plain launches issued from the library's own host loop
+    # (mrg_batch_run_plain: per request one position jump + one generate
+    # launch): launch against launch, without the interpreter in between
+    plain_c = [dict(q) for q in reqs]
+    buf_c = mrg.alloc_outputs(plain_c, device=dev)
+    prepared_c = b.prepare(plain_c)
+    b.run_plain(prepared_c)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        b.run_plain(prepared_c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain_c = e0.elapsed_time(e1) / reps
+    identical_c = all(torch.equal(a, q["out"]) for a, q in zip(outs_b, plain_c))
     draws = sum(q["n"] + (q["n"] & 1 if q["dist"] == "normal" else 0) for q in reqs)
     nbytes = sum(q["n"] * (8 if q["dtype"] == "f64" else 4) for q in reqs)
     res = {"workload": f"{nst} requests, n log-uniform [1e2, 1e6], mixed dist/dtype, "
@@ -258,11 +281,12 @@ def run_batched(mrg, W, dev, stream, seed, quick=False, reps=3, tune=True):
            "draws": draws, "bytes": nbytes, "tiles": b.last_tiles, "tiling": tiling,
            "untuned_ms": t_default, "untuned_tiles": tiles_default,
            "batched_ms_python_marshalling": t_python,
-           "batched_ms": t_batch, "plain_ms": t_plain, "speedup": t_plain / t_batch,
+           "batched_ms": t_batch, "plain_ms_c": t_plain_c, "speedup_c": t_plain_c / t_batch,
+           "plain_ms_python": t_plain, "speedup_python": t_plain / t_batch,
            "batched_draws_per_s": draws / (t_batch / 1e3), "batched_gbs": nbytes / (t_batch / 1e3) / 1e9,
-           "plain_launches": 2 * nst, "identical_output": bool(identical)}
+           "plain_launches": 2 * nst, "identical_output": bool(identical and identical_c)}
     b.close()
-    del buf_b, buf_p
+    del buf_b, buf_p, buf_c
     return res
 
 
@@ -504,7 +528,8 @@ def run_gpu(args):
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    issue_peak = 4 * SM_COUNT * sm_max_mhz * 1e6 * 32 / 1e12   # thread-instr/s, in T
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = 4 * sm_count * sm_max_mhz * 1e6 * 32 / 1e12   # thread-instr/s, in T
     variants = []
     for i, (d, dt) in enumerate(variants_run):
         t_call = float(np.mean([ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K)]))
@@ -648,7 +673,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+fp64/fp32", "dtype_note": DTYPE_NOTE,
         "data": "synthetic (paper default seed 12345x6)",
         "config": {"workload": f"materialised generation: {ns} streams x {n} draws x 5 variants "
                                "(fp64/fp32 uniform, fp64/fp32 normal, fp32 Exp(1)) + stream creation",
@@ -656,7 +681,7 @@ def run_gpu(args):
                    "l2": "outputs (4-8 GiB per variant) larger than L2; no flush"},
         "gbs": bytes_step * world / (per_step_ms / 1e3) / 1e9,
         "hbm_write_gbs_measured": write_gbs,
-        "roofline": roofline(dom, hbm, peak_kind, issue_peak, total_out),
+        "roofline": roofline(dom, hbm, peak_kind, issue_peak, total_out, sm_count),
         "variants": variants,
         "tuned": tuned or None,
         "gpu_launches": int(launches),

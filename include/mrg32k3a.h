@@ -241,8 +241,9 @@ uint64_t mrg_fisher_scratch_bytes(uint64_t n_total);
  * by the draws its replicates consumed, so later calls continue it.
  * *count (host) receives the number of replicates whose statistic is at or
  * below the observed one (with a relative allowance of 64 ulp, so that ties
- * count whatever their rounding); the p-value is (1 + *count) / (B + 1).
- * *threshold (host, may be NULL) receives that bound.  stats (device, B
+ * count whatever their rounding).  *p_value (host, may be NULL) receives the
+ * simulated p-value (1 + *count) / (B + 1) (Sec. 4).  *threshold (host, may
+ * be NULL) receives that bound.  stats (device, B
  * doubles, may be NULL) receives every replicate's statistic.  scratch:
  * caller-owned device memory, 256-byte aligned, at least
  * mrg_fisher_scratch_bytes(total) bytes.  Synchronises `stream`.  Errors:
@@ -250,7 +251,7 @@ uint64_t mrg_fisher_scratch_bytes(uint64_t n_total);
  * (total not below 2^24), MRG_ECUDA. */
 int mrg_fisher_sim(const mrg_streams *s, const int32_t *table, uint32_t I, uint32_t J,
                    uint64_t B, void *scratch, uint64_t scratch_bytes, double *stats,
-                   uint64_t *count, double *threshold, void *stream);
+                   uint64_t *count, double *threshold, double *p_value, void *stream);
 
 /* ---- MRG31k3p, the paper's own generator --------------------------------
  * The package of the paper is built on MRG31k3p (L'Ecuyer and Touzin 2000;
@@ -441,16 +442,31 @@ uint64_t mrg_batch_last_tiles(const mrg_batch *b);
 /* Frees the batch object (synchronises its last run). */
 int mrg_batch_destroy(mrg_batch *b);
 
-/* mrg_batch_run for callers that cannot allocate device memory -- code that
- * runs inside a CUDA graph capture, plug-ins whose host application owns the
- * device-memory budget, loops that cannot afford cudaMalloc's implicit
- * synchronisation.  It allocates nothing: the request table, tile table and
+/* The requests of a batch run one by one with the plain kernels, from a host
+ * loop: for each request, one jump kernel sets its stream's `cur` to
+ * start * A^(substream * 2^76 + offset) and one generate kernel writes its n
+ * values -- two launches per request, the launch-by-launch way a caller
+ * without mrg_batch_run would serve the same requests (Sec. 2.1 streams and
+ * substreams, Sec. 2.2 generation).  Same outputs as mrg_batch_run.  Leaves
+ * the `cur` of every requested stream at the start of its last request.
+ * Requests are validated as mrg_batch_run validates them, before any launch.
+ * Errors: as mrg_batch_run. */
+int mrg_batch_run_plain(const mrg_streams *s, const mrg_request *reqs, uint32_t nreq,
+                        void *stream);
+
+/* mrg_batch_run for callers that cannot allocate device memory -- plug-ins
+ * whose host application owns the device-memory budget through its own
+ * allocator, loops that cannot afford cudaMalloc's implicit synchronisation.
+ * It allocates nothing: the request table, tile table and
  * claim counter live in a fixed device array of 192.25 KiB inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  Limits per call: 1024 requests and 16384 tiles (a tile holds up to
  * 32 segments of one request; a request of n draws takes about
- * ceil(n / 65536) tiles, at least one); larger calls fail with MRG_ERANGE and
- * run nothing.  The first call on a device does the set-up (the library's
+ * ceil(n / 65536) tiles, at least one); larger calls, and a request of 2^32
+ * or more segments, fail with MRG_ERANGE and run nothing.  Requests are
+ * validated exactly as mrg_batch_run validates them.  Tiles run in one
+ * persistent kernel for all output variants, longest segments first; the
+ * per-variant kernels of mrg_batch_run are faster on large mixed batches.  The first call on a device does the set-up (the library's
  * tables and the device address of the array), so make it before any stream
  * capture.  All calls share the array: calls whose work overlaps on the GPU
  * (different CUDA streams, or several host threads) race; calls ordered on

@@ -247,7 +247,7 @@ uint64_t mrg_fisher_scratch_bytes(uint64_t n_total) {
 
 int mrg_fisher_sim(const mrg_streams* s, const int32_t* table, uint32_t I, uint32_t J,
                    uint64_t B, void* scratch, uint64_t scratch_bytes, double* stats,
-                   uint64_t* count, double* threshold, void* stream) {
+                   uint64_t* count, double* threshold, double* p_value, void* stream) {
   if (!streams_ok(s) || s->n == 0) return fail(MRG_EINVAL, "bad stream set");
   if (!table || !count) return fail(MRG_EINVAL, "table/count is NULL");
   if (I < 2 || J < 2 || I > mrg::kFisherMaxDim || J > mrg::kFisherMaxDim)
@@ -300,6 +300,9 @@ int mrg_fisher_sim(const mrg_streams* s, const int32_t* table, uint32_t I, uint3
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail_cuda(e, "reading the Fisher count");
   *count = h;
+  // the simulated p-value of Sec. 4: the observed table counts as one of
+  // B + 1 equally likely tables
+  if (p_value) *p_value = (1.0 + (double)h) / ((double)B + 1.0);
   return MRG_OK;
 }
 
@@ -563,6 +566,47 @@ int mrg_fused_pi_normsum(const mrg_streams* s, uint64_t draws, int64_t* count, d
 
 }  // extern "C"
 
+namespace mrg {
+
+// One request of a batch (mrg_batch_run, mrg_batch_run_static): checks it
+// against a stream set of ns streams and writes its device record under the
+// tiling (seg_min, seg_max, target); *tiles receives its warp-tile count.
+int prepare_request(const mrg_request& q, uint64_t ns, uint32_t seg_min, uint32_t seg_max,
+                    uint64_t target, BatchReqHost* h, uint64_t* tiles) {
+  const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
+                       ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
+                         q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
+  if (!pair_ok) return fail(MRG_EINVAL, "request with unsupported dist/dtype");
+  if (q.stream >= ns) return fail(MRG_EINVAL, "request stream index out of range");
+  if (q.substream >= (1ull << 51)) return fail(MRG_ERANGE, "substream index >= 2^51");
+  const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
+  if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
+    return fail(MRG_ERANGE, "offset + draws too large");
+  if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
+    return fail(MRG_EINVAL, "request output NULL or not 32-byte aligned");
+  if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
+    return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
+  const uint32_t L = tiled_seg_len(q.n, seg_min, seg_max, target);
+  const uint64_t nseg = (q.n + L - 1) / L;
+  if (nseg > 0xFFFFFFFFull) return fail(MRG_ERANGE, "request has more than 2^32 segments");
+  h->out = reinterpret_cast<uint64_t>(q.out);
+  h->n = q.n;
+  h->off = q.offset;
+  h->sub = q.substream;
+  h->stream = q.stream;
+  h->dist = (uint32_t)q.dist;
+  h->dtype = (uint32_t)q.dtype;
+  const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
+  h->ir_hi = (float)ir;
+  h->ir_lo = (float)(ir - (double)h->ir_hi);
+  h->L = L;
+  h->nseg = (uint32_t)nseg;
+  *tiles = (nseg + 31) / 32;
+  return MRG_OK;
+}
+
+}  // namespace mrg
+
 // Host staging of one run's tables (pinned).  A batch object has two, used in
 // turn, so that the tables of the next run are built while the GPU still
 // copies or runs the previous one.
@@ -625,37 +669,11 @@ int build_batch_tables(mrg_batch* b, BatchStaging& S, const mrg_request* reqs, u
                        const mrg_tiling& t, uint64_t* ntiles) {
   uint64_t nt = 0;
   for (uint32_t r = 0; r < nreq; ++r) {
-    const mrg_request& q = reqs[r];
-    const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
-                         ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
-                           q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
-    if (!pair_ok) return fail(MRG_EINVAL, "request with unsupported dist/dtype");
-    if (q.stream >= b->s.n) return fail(MRG_EINVAL, "request stream index out of range");
-    if (q.substream >= (1ull << 51)) return fail(MRG_ERANGE, "substream index >= 2^51");
-    const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
-    if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
-      return fail(MRG_ERANGE, "offset + draws too large");
-    if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
-      return fail(MRG_EINVAL, "request output NULL or not 32-byte aligned");
-    if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
-      return fail(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
-    const uint32_t L = mrg::tiled_seg_len(q.n, t.seg_min, t.seg_max, t.target_segments);
-    const uint64_t nseg = (q.n + L - 1) / L;
-    if (nseg > 0xFFFFFFFFull) return fail(MRG_ERANGE, "request has more than 2^32 segments");
-    mrg::BatchReqHost& h = S.reqs[r];
-    h.out = reinterpret_cast<uint64_t>(q.out);
-    h.n = q.n;
-    h.off = q.offset;
-    h.sub = q.substream;
-    h.stream = q.stream;
-    h.dist = (uint32_t)q.dist;
-    h.dtype = (uint32_t)q.dtype;
-    const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
-    h.ir_hi = (float)ir;
-    h.ir_lo = (float)(ir - (double)h.ir_hi);
-    h.L = L;
-    h.nseg = (uint32_t)nseg;
-    nt += (nseg + 31) / 32;
+    uint64_t tiles = 0;
+    const int rc = mrg::prepare_request(reqs[r], b->s.n, t.seg_min, t.seg_max, t.target_segments,
+                                        &S.reqs[r], &tiles);
+    if (rc) return rc;
+    nt += tiles;
     if (nt > b->max_tiles) return fail(MRG_ERANGE, "more tiles than the batch holds");
   }
   // Tile order: grouped by output variant (one persistent kernel per variant
@@ -677,7 +695,7 @@ int build_batch_tables(mrg_batch* b, BatchStaging& S, const mrg_request* reqs, u
   for (uint32_t r : order) {
     const int rv = rank(r);
     for (; v < rv; ++v) S.ranges[v + 1].begin = S.ranges[v + 1].end = k;
-    const uint64_t tiles = (S.reqs[r].nseg + 31) / 32;
+    const uint64_t tiles = ((uint64_t)S.reqs[r].nseg + 31) / 32;
     for (uint64_t j = 0; j < tiles; ++j) S.tiles[k++] = mrg::BatchTileHost{r, (uint32_t)(32 * j)};
     S.ranges[rv].end = k;
   }
@@ -886,6 +904,37 @@ int mrg_batch_destroy(mrg_batch* b) {
   if (!b) return MRG_OK;
   if (b->ran) cudaEventSynchronize(b->done);
   batch_free(b);
+  return MRG_OK;
+}
+
+int mrg_batch_run_plain(const mrg_streams* s, const mrg_request* reqs, uint32_t nreq,
+                        void* stream) {
+  if (!streams_ok(s)) return fail(MRG_EINVAL, "bad stream set");
+  if (nreq > 0 && !reqs) return fail(MRG_EINVAL, "reqs is NULL");
+  for (uint32_t r = 0; r < nreq; ++r) {  // the batch's own checks, nothing launched yet
+    mrg::BatchReqHost h;
+    uint64_t tiles = 0;
+    const int rc = mrg::prepare_request(reqs[r], s->n, 8, 2048, 32, &h, &tiles);
+    if (rc) return rc;
+  }
+  int rc = ensure_device();
+  if (rc) return rc;
+  cudaStream_t st = cs(stream);
+  for (uint32_t r = 0; r < nreq; ++r) {
+    const mrg_request& q = reqs[r];
+    if (q.n == 0) continue;
+    // cur of the request's stream <- start * A^(substream 2^76 + offset)
+    const unsigned __int128 e =
+        ((unsigned __int128)q.substream << mrg::SUBSTREAM_LOG2) + (unsigned __int128)q.offset;
+    cudaError_t ce = mrg::launch_jump(s->start + q.stream, s->cur + q.stream, nullptr, s->stride, 1,
+                                      (uint64_t)e, (uint64_t)(e >> 64), 0, st);
+    if (ce != cudaSuccess) return fail_cuda(ce, "jump_kernel (request position)");
+    const mrg::DevStreams one{s->cur + q.stream, s->start + q.stream, s->sub + q.stream, 1,
+                              s->stride};
+    const mrg::GenConfig cfg = mrg::generate_config_for(q.dist, q.dtype, 1, q.n);
+    ce = mrg::launch_generate(one, q.n, q.dist, q.dtype, q.rate, q.out, q.n, cfg, st);
+    if (ce != cudaSuccess) return fail_cuda(ce, "generate_kernel (plain request)");
+  }
   return MRG_OK;
 }
 

@@ -5,6 +5,8 @@
 
 #include <atomic>
 
+struct mrg_request;  // include/mrg32k3a.h
+
 namespace mrg {
 
 struct DevStreams {
@@ -144,6 +146,13 @@ inline uint32_t tiled_seg_len(uint64_t draws, uint32_t seg_min, uint32_t seg_max
   if (L > seg_max) L = seg_max;
   return (uint32_t)L;
 }
+
+// Checks one batched request against a stream set of ns streams and writes
+// its device record under the tiling (seg_min, seg_max, target); *tiles
+// receives its warp-tile count.  Returns MRG_OK or an MRG_E* code with the
+// error text set (capi.cu).  Both batch entry points validate through it.
+int prepare_request(const mrg_request& q, uint64_t ns, uint32_t seg_min, uint32_t seg_max,
+                    uint64_t target, BatchReqHost* h, uint64_t* tiles);
 
 // Range of one variant in a variant-grouped tile table (device mirror:
 // VariantRange in batch_kernels.cuh), and the spacing of the per-variant

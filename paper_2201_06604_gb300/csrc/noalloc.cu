@@ -1,17 +1,18 @@
 // noalloc.cu -- batched generation for callers that cannot allocate device
 // memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not a capturable operation), plug-ins hosted
-// by an application that owns the whole device-memory budget through its own
-// allocator, and latency-critical loops where cudaMalloc's implicit device
-// synchronisation is not acceptable.  mrg_batch_run_static serves them: it
+// Some callers cannot call cudaMalloc: plug-ins hosted by an application that
+// owns the whole device-memory budget through its own allocator (a cudaMalloc
+// behind its back can fail or push the host application out of memory), and
+// latency-critical loops where cudaMalloc's implicit device synchronisation
+// is not acceptable.  mrg_batch_run_static serves them: it
 // runs the same persistent batch kernel as mrg_batch_run, but its request
 // table, tile table and claim counter live in the fixed-size device array
 // below, which every GPU that loads the library holds until the process
 // exits.  Nothing in this file allocates memory, on the device or the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/mrg32k3a.h"
@@ -36,6 +37,7 @@ struct Staging {
   mrg::BatchHeaderHost hdr;
   mrg::BatchReqHost reqs[kMaxRequests];
   mrg::BatchTileHost tiles[kMaxTiles];
+  uint32_t order[kMaxRequests];  // request order of the tile table
 };
 Staging g_stage;
 std::mutex g_mu;
@@ -54,14 +56,9 @@ int set_up(int dev) {
   return MRG_OK;
 }
 
-// Same segment length rule as mrg_batch_run (whole 32-byte units, ~n/32).
-uint32_t seg_len(uint64_t draws) {
-  uint64_t L = (draws + 31) / 32;
-  L = (L + 7) / 8 * 8;
-  if (L < 8) L = 8;
-  if (L > 2048) L = 2048;
-  return (uint32_t)L;
-}
+// Tiling of the static path: segments of ~n/32 draws, 8..2048, whole 32-byte units.
+constexpr uint32_t kSegMin = 8, kSegMax = 2048;
+constexpr uint64_t kTargetSegments = 32;
 
 }  // namespace
 
@@ -72,48 +69,38 @@ extern "C" int mrg_batch_run_static(const mrg_streams* s, const mrg_request* req
   if (nreq > 0 && !reqs) return mrg::set_error(MRG_EINVAL, "reqs is NULL");
   if (nreq > kMaxRequests)
     return mrg::set_error(MRG_ERANGE, "more than 1024 requests in one static-scratch call");
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = MRG_OK;
+  uint64_t nt = 0;
+  for (uint32_t r = 0; r < nreq; ++r) {
+    uint64_t tiles = 0;
+    rc = mrg::prepare_request(reqs[r], s->n, kSegMin, kSegMax, kTargetSegments, &g_stage.reqs[r],
+                              &tiles);
+    if (rc) return rc;
+    nt += tiles;
+    if (nt > kMaxTiles)
+      return mrg::set_error(MRG_ERANGE, "more than 16384 tiles in one static-scratch call");
+  }
+  // Tiles of the longest segments first, so that the last tiles claimed by
+  // the persistent kernel are the shortest (a short tail); the sort works in
+  // the static staging and allocates nothing.
+  for (uint32_t r = 0; r < nreq; ++r) g_stage.order[r] = r;
+  std::stable_sort(g_stage.order, g_stage.order + nreq, [](uint32_t x, uint32_t y) {
+    return g_stage.reqs[x].L > g_stage.reqs[y].L;
+  });
+  uint64_t k = 0;
+  for (uint32_t i = 0; i < nreq; ++i) {
+    const uint32_t r = g_stage.order[i];
+    const uint64_t tiles = ((uint64_t)g_stage.reqs[r].nseg + 31) / 32;
+    for (uint64_t j = 0; j < tiles; ++j) g_stage.tiles[k++] = mrg::BatchTileHost{r, (uint32_t)(32 * j)};
+  }
+  if (nt == 0) return MRG_OK;
+  // The requests are valid: only now is the device touched.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) return mrg::set_error(MRG_ECUDA, "cudaGetDevice failed");
-  std::lock_guard<std::mutex> lk(g_mu);
-  int rc = set_up(dev);
+  rc = set_up(dev);
   if (rc) return rc;
-  uint64_t nt = 0;
-  for (uint32_t r = 0; r < nreq; ++r) {
-    const mrg_request& q = reqs[r];
-    const bool pair_ok = (q.dist == MRG_RAW && q.dtype == MRG_U32) ||
-                         ((q.dist == MRG_UNIFORM || q.dist == MRG_NORMAL ||
-                           q.dist == MRG_EXPONENTIAL) && (q.dtype == MRG_F32 || q.dtype == MRG_F64));
-    if (!pair_ok) return mrg::set_error(MRG_EINVAL, "request with unsupported dist/dtype");
-    if (q.stream >= s->n) return mrg::set_error(MRG_EINVAL, "request stream index out of range");
-    if (q.substream >= (1ull << 51)) return mrg::set_error(MRG_ERANGE, "substream index >= 2^51");
-    const uint64_t draws = q.dist == MRG_NORMAL ? q.n + (q.n & 1) : q.n;
-    if (q.offset > (1ull << 62) || draws > (1ull << 62) || q.offset + draws > (1ull << 62))
-      return mrg::set_error(MRG_ERANGE, "offset + draws too large");
-    if (q.n > 0 && (!q.out || reinterpret_cast<uintptr_t>(q.out) % 32))
-      return mrg::set_error(MRG_EINVAL, "request output NULL or not 32-byte aligned");
-    if (q.dist == MRG_EXPONENTIAL && !(q.rate >= 0x1p-64 && q.rate <= 0x1p64))
-      return mrg::set_error(MRG_EINVAL, "exponential rate must lie in [2^-64, 2^64]");
-    mrg::BatchReqHost& h = g_stage.reqs[r];
-    h.out = reinterpret_cast<uint64_t>(q.out);
-    h.n = q.n;
-    h.off = q.offset;
-    h.sub = q.substream;
-    h.stream = q.stream;
-    h.dist = (uint32_t)q.dist;
-    h.dtype = (uint32_t)q.dtype;
-    const double ir = q.dist == MRG_EXPONENTIAL ? -1.0 / q.rate : 0.0;
-    h.ir_hi = (float)ir;
-    h.ir_lo = (float)(ir - (double)h.ir_hi);
-    h.L = seg_len(q.n);
-    h.nseg = (uint32_t)((q.n + h.L - 1) / h.L);
-    const uint64_t tiles = (h.nseg + 31) / 32;
-    if (nt + tiles > kMaxTiles)
-      return mrg::set_error(MRG_ERANGE, "more than 16384 tiles in one static-scratch call");
-    for (uint64_t k = 0; k < tiles; ++k) g_stage.tiles[nt + k] = mrg::BatchTileHost{r, (uint32_t)(32 * k)};
-    nt += tiles;
-  }
-  if (nt == 0) return MRG_OK;
   // The claim counter must start at zero: the header is rewritten every call.
   g_stage.hdr.next_tile = 0;
   g_stage.hdr.ntiles = nt;

@@ -115,7 +115,7 @@ def _load():
         "mrg_fisher_scratch_bytes": ([u64], u64),
         "mrg_fisher_sim": ([sp, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_uint32,
                             u64, vp, u64, vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
-                            vp], i32),
+                            ctypes.POINTER(ctypes.c_double), vp], i32),
         "mrg31k3p_seed_check": ([u32p], i32),
         "mrg31k3p_create_streams": ([u32p, u64, sp, u32p, vp], i32),
         "mrg31k3p_generate": ([sp, u64, i32, i32, ctypes.c_double, vp, u64, vp], i32),
@@ -131,6 +131,7 @@ def _load():
         "mrg_tune_clear": ([], None),
         "mrg_batch_create": ([sp, ctypes.c_uint32, u64, ctypes.POINTER(vp), vp], i32),
         "mrg_batch_run": ([vp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
+        "mrg_batch_run_plain": ([sp, ctypes.POINTER(_Request), ctypes.c_uint32, vp], i32),
         "mrg_batch_last_tiles": ([vp], u64),
         "mrg_batch_set_tiling": ([vp, ctypes.POINTER(Tiling)], i32),
         "mrg_batch_get_tiling": ([vp, ctypes.POINTER(Tiling)], i32),
@@ -536,7 +537,7 @@ def fill_u32(t: torch.Tensor, value: int = 0, stream=None):
 def fisher_sim(streams: Streams, table, B: int, return_stats: bool = False, stream=None) -> dict:
     """Monte Carlo Fisher's exact test (Sec. 4, fisher.sim): B random tables
     with the margins of `table` (I x J integers), replicate b on stream
-    b mod streams.n.  Returns dict(p_value=(1+count)/(B+1), count, threshold,
+    b mod streams.n.  Returns dict(p_value (the library's (1+count)/(B+1)), count, threshold,
     B[, stats = device tensor of the B statistics])."""
     _need_mrg32k3a(streams, "fisher_sim")
     t = np.ascontiguousarray(np.asarray(table), dtype=np.int32)
@@ -547,13 +548,13 @@ def fisher_sim(streams: Streams, table, B: int, return_stats: bool = False, stre
     nbytes = int(lib.mrg_fisher_scratch_bytes(total))
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=streams.device)
     stats = torch.empty(max(B, 1), dtype=torch.float64, device=streams.device) if return_stats else None
-    cnt, thr = ctypes.c_uint64(), ctypes.c_double()
+    cnt, thr, pv = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
     with torch.cuda.device(streams.device):
         _check(lib.mrg_fisher_sim(streams.ptr(), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   I, J, B, scratch.data_ptr(), nbytes,
                                   stats.data_ptr() if return_stats else None, ctypes.byref(cnt),
-                                  ctypes.byref(thr), _stream_handle(stream)))
-    out = {"p_value": (1 + cnt.value) / (B + 1), "count": int(cnt.value),
+                                  ctypes.byref(thr), ctypes.byref(pv), _stream_handle(stream)))
+    out = {"p_value": pv.value, "count": int(cnt.value),
            "threshold": thr.value, "B": B}
     if return_stats:
         out["stats"] = stats[:B]
@@ -615,6 +616,14 @@ class Batch:
         arr, n = self._requests(requests)
         with torch.cuda.device(self.streams.device):
             _check(lib.mrg_batch_run(self._h, arr, n, _stream_handle(stream)))
+
+    def run_plain(self, requests, stream=None):
+        """The same requests served one by one from the library's host loop
+        (mrg_batch_run_plain: a position jump and a generate launch per
+        request); same outputs as run()."""
+        arr, n = self._requests(requests)
+        with torch.cuda.device(self.streams.device):
+            _check(lib.mrg_batch_run_plain(self.streams.ptr(), arr, n, _stream_handle(stream)))
 
     def set_tiling(self, tiling=None):
         """tiling: dict(seg_min, seg_max, target_segments) or None (default)."""

@@ -100,16 +100,16 @@ def test_fill_and_fisher_errors():
     ok2x2 = table([3, 1, 1, 3])
     scratch = FAKE
     nbytes = L.mrg_fisher_scratch_bytes(8)
-    assert f(sp, ok2x2, 1, 4, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
-    assert f(sp, ok2x2, 2, 65, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
-    assert f(sp, table([3, -1, 1, 3]), 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None,
+    assert f(sp, ok2x2, 1, 4, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None, None) == mrg.EINVAL
+    assert f(sp, ok2x2, 2, 65, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None, None) == mrg.EINVAL
+    assert f(sp, table([3, -1, 1, 3]), 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None,
              None) == mrg.EINVAL
     big = table([1 << 23, 1 << 23, 1, 1])
-    assert f(sp, big, 2, 2, 100, scratch, 1 << 30, None, ctypes.byref(cnt), None,
+    assert f(sp, big, 2, 2, 100, scratch, 1 << 30, None, ctypes.byref(cnt), None, None,
              None) == mrg.ERANGE
-    assert f(sp, ok2x2, 2, 2, 100, scratch, nbytes - 8, None, ctypes.byref(cnt), None,
+    assert f(sp, ok2x2, 2, 2, 100, scratch, nbytes - 8, None, ctypes.byref(cnt), None, None,
              None) == mrg.EINVAL                                        # scratch too small
-    assert f(sp, None, 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None) == mrg.EINVAL
+    assert f(sp, None, 2, 2, 100, scratch, nbytes, None, ctypes.byref(cnt), None, None, None) == mrg.EINVAL
 
 
 def test_mrg31k3p_errors():
@@ -120,3 +120,34 @@ def test_mrg31k3p_errors():
     s = fake_streams()
     assert L.mrg31k3p_generate(ctypes.byref(s), 8, mrg.NORMAL, mrg.U32, 1.0, FAKE, 8,
                                None) == mrg.EINVAL
+
+
+def _static_call(reqs):
+    f = L.mrg_batch_run_static
+    f.argtypes = [ctypes.POINTER(mrg._Streams), ctypes.POINTER(mrg._Request), ctypes.c_uint32,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    arr = (mrg._Request * len(reqs))(*reqs)
+    s = fake_streams()
+    return f(ctypes.byref(s), arr, len(reqs), None)
+
+
+def test_static_batch_refuses_requests_before_any_device_work():
+    # 2^43 + 2048 draws at 2048 draws per segment is 2^32 + 1 segments: more
+    # than a request record counts, refused (it once wrapped to one segment)
+    huge = mrg._Request(0, 0, 0, (1 << 43) + 2048, mrg.UNIFORM, mrg.F64, 1.0, FAKE)
+    assert _static_call([huge]) == mrg.ERANGE
+    assert b"2^32" in L.mrg_last_error()
+    # the same checks as mrg_batch_run: stream index, dist/dtype, alignment, rate
+    assert _static_call([mrg._Request(16, 0, 0, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE)]) == mrg.EINVAL
+    assert _static_call([mrg._Request(0, 0, 0, 8, mrg.RAW, mrg.F64, 1.0, FAKE)]) == mrg.EINVAL
+    assert _static_call([mrg._Request(0, 0, 0, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE + 16)]) == mrg.EINVAL
+    assert _static_call([mrg._Request(0, 1 << 51, 0, 8, mrg.UNIFORM, mrg.F64, 1.0, FAKE)]) == mrg.ERANGE
+    assert _static_call([mrg._Request(0, 0, 0, 8, mrg.EXPONENTIAL, mrg.F32, 0.0, FAKE)]) == mrg.EINVAL
+    # a request of 2^26 draws takes 1024 tiles (2048-draw segments, 32 per
+    # tile): 17 of them pass the 16384-tile limit
+    big = [mrg._Request(0, 0, 0, 1 << 26, mrg.UNIFORM, mrg.F32, 1.0, FAKE)] * 17
+    assert _static_call(big) == mrg.ERANGE
+    assert b"16384" in L.mrg_last_error()
+    # an empty call is a no-op that touches nothing
+    assert _static_call([mrg._Request(0, 0, 0, 0, mrg.UNIFORM, mrg.F64, 1.0, None)]) == mrg.OK

@@ -267,3 +267,26 @@ def test_full_size_batch_sampled(M):
         p = M.generate(s.view(r, 1), q["n"], q["dist"], dt[q["dtype"]])[0]
         assert torch.equal(p, q["out"]), q
     b.close()
+
+
+def test_plain_host_loop_matches_batch_and_oracle(M):
+    # mrg_batch_run_plain: the same requests, one position jump and one
+    # generate launch each from the library's host loop
+    ns = 200
+    s = M.create_streams(ns, seed=SEED)
+    start, _ = O.create_streams(SEED, ns)
+    reqs = make_requests(ns, 90, seed=17)
+    ref = [dict(q) for q in reqs]
+    buf_b = M.alloc_outputs(ref)
+    buf_p = M.alloc_outputs(reqs)
+    b = M.Batch(s, max_requests=128, max_tiles=4096)
+    b.run(ref)
+    b.run_plain(reqs)
+    torch.cuda.synchronize()
+    for q, r in zip(reqs, ref):
+        if q["n"] == 0:
+            continue
+        assert torch.equal(q["out"], r["out"]), q
+        check_close(q["out"].cpu().numpy(), oracle_request(start, q), q)
+    b.close()
+    del buf_b, buf_p

@@ -1,9 +1,10 @@
 """mrg_batch_run_static: batched generation for callers that cannot allocate
-device memory (inside a CUDA graph capture, under a host application that owns
-the device-memory budget, or where cudaMalloc's implicit synchronisation is
-not acceptable).  Its scratch lives in a fixed device array inside the
-library, so it must produce what mrg_batch_run produces, call after call,
-with no allocation.
+device memory (a plug-in under a host application that owns the
+device-memory budget through its own allocator, or a loop where cudaMalloc's
+implicit synchronisation is not acceptable).  Its scratch lives in a fixed
+device array inside the library, so it must produce what mrg_batch_run
+produces, call after call, and a call after the first must leave the
+device's free memory unchanged.
 
 This file is collected last on purpose: a failure here leaves every other
 test already run.  It passes alone in a fresh process and after the others.
@@ -98,3 +99,20 @@ def test_static_scratch_rejects_oversize(M):
                out=out)]
     assert run_static(M, s, ok) == M.OK
     torch.cuda.synchronize()
+
+
+def test_static_scratch_allocates_nothing(M):
+    ns = 64
+    s = M.create_streams(ns, seed=SEED)
+    reqs = requests(ns, 40, 23)
+    M.alloc_outputs(reqs)
+    assert run_static(M, s, reqs) == M.OK, M.lib.mrg_last_error()   # first call: set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    used0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert run_static(M, s, reqs) == M.OK, M.lib.mrg_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == used0
+    assert free1 == free0, (free0, free1)
