@@ -541,6 +541,98 @@ int mrg_server_restart(mrg_server *sv);
  * it and frees the server (the arena stays the caller's). */
 int mrg_server_destroy(mrg_server *sv);
 
+/* ---- Gaussian random fields by direct matrix decomposition ---------------
+ * Sec. 5, Algorithm 2: (1) the Matern covariance matrix of the locations,
+ * (2) Sigma = L D L^T with L unit lower triangular, (3) standard normals Z
+ * from the generator (mrg_generate with MRG_NORMAL), (4) U = L D^(1/2) Z.
+ * Matrices are row-major fp64 in device memory, matrix b of a batch at
+ * base + b * n * ld; a batch runs in parallel. */
+
+/* One parameter set of the Matern covariance of Sec. 5:
+ *   Sigma_ij = variance * 2^(1-shape) / Gamma(shape) * x^shape K_shape(x),
+ *   x = sqrt(8 shape) |d_ij| / range,
+ *   d_ij = diag(1, aniso_ratio) R(aniso_angle) (x_i - x_j),
+ *   R(t) = [[cos t, -sin t], [sin t, cos t]],
+ * and Sigma_ii = variance.  The printed normalising constant 2^(shape-1) is
+ * read as 2^(1-shape), the only one for which var(U_i) = variance (the
+ * paper's stated property).  Valid: 0 < shape <= 10, range > 0,
+ * variance > 0, aniso_ratio >= 1, finite angle (radians). */
+typedef struct mrg_matern_params {
+    double shape, range, variance, aniso_ratio, aniso_angle;
+} mrg_matern_params;
+
+/* Bytes of device scratch mrg_grf_matern_raster needs (a 4 KiB parameter
+ * block and one covariance value per cell offset and matrix). */
+uint64_t mrg_grf_matern_scratch_bytes(uint32_t batch, uint32_t nrow, uint32_t ncol);
+
+/* Algorithm 2 step 1 for a raster of nrow x ncol square cells of side
+ * `cell` (the paper's maternBatch on a raster): point k is the centre of the
+ * cell in column k mod ncol and row k div ncol, at ((c + 1/2) cell,
+ * (r + 1/2) cell).  Writes the full n x n covariance matrix (n = nrow ncol,
+ * leading dimension ld >= n) of every parameter set params[0 .. batch)
+ * (host) into cov (device, matrix b at cov + b n ld).  On a raster the
+ * covariance depends only on the cell offset, so each of the
+ * (2 nrow - 1)(2 ncol - 1) offsets is evaluated once (K by the trapezoidal
+ * rule on its integral representation, ~1e-13 relative) and the matrix is
+ * filled from that table.  scratch: device, 256-byte aligned, at least
+ * mrg_grf_matern_scratch_bytes bytes.  Synchronises `stream` once (the
+ * parameters are staged through it).  Errors: MRG_EINVAL (NULL, batch not in
+ * 1..64, bad parameters, ld < n, alignment, scratch too small), MRG_ERANGE
+ * (n > 2^20), MRG_ECUDA. */
+int mrg_grf_matern_raster(const mrg_matern_params *params, uint32_t batch, uint32_t nrow,
+                          uint32_t ncol, double cell, double *cov, uint64_t ld, void *scratch,
+                          uint64_t scratch_bytes, void *stream);
+
+/* Algorithm 2 step 1 for arbitrary locations xy (device, n x 2: x then y of
+ * each point): every entry evaluated on its own.  scratch: device, 256-byte
+ * aligned, >= 4096 bytes.  Synchronises `stream` once.  Errors: as
+ * mrg_grf_matern_raster. */
+int mrg_grf_matern_points(const mrg_matern_params *params, uint32_t batch, const double *xy,
+                          uint64_t n, double *cov, uint64_t ld, void *scratch,
+                          uint64_t scratch_bytes, void *stream);
+
+/* Bytes of device workspace mrg_grf_ldl needs for `batch` matrices of order n
+ * (the bf16 operand slices of one panel, ~4.2 KiB per row and matrix). */
+uint64_t mrg_grf_ldl_workspace_bytes(uint64_t n, uint32_t batch);
+
+/* Algorithm 2 step 2: Sigma = L D L^T in place for `batch` symmetric positive
+ * definite matrices (device, matrix b at a + b n lda; only the lower
+ * triangle is read).  On return the strict lower triangle holds L (its unit
+ * diagonal implied), the diagonal holds D, and d (device, batch x n) holds D
+ * too; the strict upper triangle is overwritten with scratch values.  A
+ * right-looking blocked factorisation with 128-column panels: each 128 x 128
+ * diagonal block is factored in double-float arithmetic by one CTA per
+ * matrix; the panel L_ik = A_ik L_kk^-T D^-1 and the trailing update
+ * A_ij -= L_ik D L_jk^T are fp64 products evaluated on the tensor cores
+ * (tcgen05) by an error-free split of every operand row into eight bf16
+ * slices of a 56-bit fixed-point form (the Ozaki scheme), summed exactly in
+ * integers and rounded once to fp64.  workspace: device, 1024-byte aligned,
+ * >= mrg_grf_ldl_workspace_bytes(n, batch).  info (host, batch entries, may
+ * be NULL): when given, the call synchronises `stream` and info[b] receives
+ * 0, or 1 + the index of the first pivot of matrix b that was not positive
+ * (its factor is then invalid); without it the call returns as soon as the
+ * kernels are enqueued.  Errors: MRG_EINVAL (NULL, batch not in 1..255,
+ * lda < n, alignment, workspace too small), MRG_ERANGE (n > 2^20),
+ * MRG_ETIMEOUT (a bounded tensor-core wait gave up; only reported with
+ * info), MRG_ECUDA. */
+int mrg_grf_ldl(double *a, uint64_t n, uint64_t lda, uint32_t batch, double *d, void *workspace,
+                uint64_t workspace_bytes, int32_t *info, void *stream);
+
+/* Bytes of device scratch mrg_grf_simulate needs (D^(1/2) Z). */
+uint64_t mrg_grf_simulate_scratch_bytes(uint64_t n, uint32_t nsim, uint32_t batch);
+
+/* Algorithm 2 step 4: U = L D^(1/2) Z for nsim columns of standard normals
+ * per matrix.  l (device): the factor written by mrg_grf_ldl (strict lower
+ * triangle read, unit diagonal implied); d (device, batch x n); z and u
+ * (device) are [batch][nsim][n]: simulation s of matrix b is the contiguous
+ * vector at z + (b nsim + s) n -- the layout of mrg_generate's normals on
+ * batch * nsim streams of n draws.  fp64 throughout.  scratch: device,
+ * >= mrg_grf_simulate_scratch_bytes.  Errors: MRG_EINVAL, MRG_ERANGE
+ * (n > 2^20 or nsim > 2^16), MRG_ECUDA. */
+int mrg_grf_simulate(const double *l, const double *d, uint64_t n, uint64_t lda, uint32_t batch,
+                     const double *z, uint32_t nsim, double *u, void *scratch,
+                     uint64_t scratch_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

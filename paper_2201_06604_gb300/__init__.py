@@ -5,13 +5,13 @@ The CUDA library is loaded on first use of a binding name, so that
 be imported on a machine where it is not built yet.  Every compute call goes
 through libmrg32k3a's kernels; there is no CPU path.
 """
-__all__ = ["mrg", "build", "workloads"]
+__all__ = ["mrg", "build", "workloads", "grf"]
 
 
 def __getattr__(name):
     import importlib
 
-    if name in ("mrg", "build", "workloads", "serve", "batch", "tune"):
+    if name in ("mrg", "build", "workloads", "serve", "batch", "tune", "grf"):
         return importlib.import_module(f".{name}", __name__)
     mod = importlib.import_module(".mrg", __name__)
     try:

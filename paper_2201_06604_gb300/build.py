@@ -20,7 +20,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr", "-I", INCLUDE]
-SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu", "server.cu", "tune.cu", "host_jump.cpp"]
+SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu", "server.cu", "tune.cu", "grf.cu",
+           "host_jump.cpp"]
 
 
 def _deps():

@@ -1,0 +1,334 @@
+// grf.cu -- C-ABI entry points and launchers of the Gaussian-random-field
+// path (Sec. 5, Algorithm 2): Matern covariance matrices, their batched
+// LDL^T factorisation on the tensor cores, and U = L D^(1/2) Z.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "../../include/mrg32k3a.h"
+#include "grf_kernels.cuh"
+#include "internal.h"
+
+namespace {
+
+using namespace mrg::grf;
+
+constexpr int kSlices = 8;             // bf16 slices per fp64 operand (56-bit fixed point)
+constexpr uint32_t kMaxBatch = 64;     // matrices per call (parameters travel by value)
+
+struct ParamBlock {
+  MaternParams p[kMaxBatch];
+};
+
+uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+// Per-matrix workspace layout of the factorisation (bytes, 1024-aligned parts).
+struct LdlLayout {
+  uint64_t img_a, img_w, img_x, exp_a, exp_w, exp_x, exp_eq, per_matrix, common;
+  explicit LdlLayout(uint64_t n) {
+    const uint64_t ta = (n + RB_A - 1) / RB_A;
+    img_a = 0;
+    img_w = img_a + ta * kSlices * SLICE_A;
+    img_x = img_w + 2 * ta * kSlices * SLICE_B;
+    exp_a = img_x + 2 * kSlices * SLICE_B;
+    exp_w = exp_a + align_up(ta * RB_A * 4, 1024);
+    exp_x = exp_w + align_up(ta * RB_A * 4, 1024);
+    exp_eq = exp_x + 1024;
+    per_matrix = exp_eq + align_up(n * 4, 1024);
+    common = 2048;   // status word, per-matrix info and equilibration flags (<= 255 matrices)
+  }
+  uint64_t bytes(uint32_t batch) const { return common + per_matrix * batch; }
+};
+
+int set_attrs_once() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return mrg::set_error(MRG_ECUDA, "cudaGetDevice failed");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return MRG_OK;
+  cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel<kSlices, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GemmSmem<kSlices>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ozaki_gemm_kernel<kSlices, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GemmSmem<kSlices>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ldl_diag_kernel<kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(NB * DG * sizeof(mrg::df)));
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+  done[dev] = true;
+  return MRG_OK;
+}
+
+int after(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, what);
+  mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
+  return MRG_OK;
+}
+
+int params_block(const mrg_matern_params* params, uint32_t batch, ParamBlock* pb) {
+  for (uint32_t b = 0; b < batch; ++b) {
+    const mrg_matern_params& q = params[b];
+    if (!(q.shape > 0.0 && q.shape <= 10.0) || !(q.range > 0.0) || !(q.variance > 0.0) ||
+        !(q.aniso_ratio >= 1.0) || !std::isfinite(q.aniso_angle) || !std::isfinite(q.range) ||
+        !std::isfinite(q.variance) || !std::isfinite(q.aniso_ratio))
+      return mrg::set_error(MRG_EINVAL, "Matern parameters: need 0 < shape <= 10, range > 0, "
+                                        "variance > 0, aniso_ratio >= 1, finite angle");
+    MaternParams& p = pb->p[b];
+    p.kappa = q.shape;
+    p.var = q.variance;
+    p.norm = std::exp2(1.0 - q.shape) / std::tgamma(q.shape);
+    p.scale = std::sqrt(8.0 * q.shape) / q.range;
+    p.c = std::cos(q.aniso_angle);
+    p.s = std::sin(q.aniso_angle);
+    p.omega = q.aniso_ratio;
+  }
+  return MRG_OK;
+}
+
+// Copies the parameter block to the head of the caller's scratch.
+int upload_params(const ParamBlock& pb, uint32_t batch, void* scratch, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(scratch, &pb, sizeof(MaternParams) * batch,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // pb lives on the caller's stack
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "copying the Matern parameters");
+  return MRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t mrg_grf_matern_scratch_bytes(uint32_t batch, uint32_t nrow, uint32_t ncol) {
+  return 4096 + (uint64_t)batch * (2ull * nrow - 1) * (2ull * ncol - 1) * 8;
+}
+
+int mrg_grf_matern_raster(const mrg_matern_params* params, uint32_t batch, uint32_t nrow,
+                          uint32_t ncol, double cell, double* cov, uint64_t ld, void* scratch,
+                          uint64_t scratch_bytes, void* stream) {
+  if (!params || !cov || !scratch) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  if (batch == 0 || batch > kMaxBatch) return mrg::set_error(MRG_EINVAL, "batch must be 1..64");
+  if (nrow == 0 || ncol == 0) return mrg::set_error(MRG_EINVAL, "empty raster");
+  const uint64_t n = (uint64_t)nrow * ncol;
+  if (n > (1u << 20)) return mrg::set_error(MRG_ERANGE, "more than 2^20 cells");
+  if (ld < n) return mrg::set_error(MRG_EINVAL, "ld < nrow * ncol");
+  if (!(cell > 0.0) || !std::isfinite(cell)) return mrg::set_error(MRG_EINVAL, "cell must be > 0");
+  if (reinterpret_cast<uintptr_t>(cov) % 8 || reinterpret_cast<uintptr_t>(scratch) % 256)
+    return mrg::set_error(MRG_EINVAL, "cov not 8-byte or scratch not 256-byte aligned");
+  if (scratch_bytes < mrg_grf_matern_scratch_bytes(batch, nrow, ncol))
+    return mrg::set_error(MRG_EINVAL, "scratch smaller than mrg_grf_matern_scratch_bytes");
+  ParamBlock pb;
+  int rc = params_block(params, batch, &pb);
+  if (rc) return rc;
+  rc = mrg::ensure_device_ready();
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  rc = upload_params(pb, batch, scratch, st);
+  if (rc) return rc;
+  const MaternParams* dprm = static_cast<const MaternParams*>(scratch);
+  double* table = reinterpret_cast<double*>(static_cast<char*>(scratch) + 4096);
+  const uint64_t per_t = (2ull * nrow - 1) * (2ull * ncol - 1);
+  const uint64_t nt = per_t * batch;
+  matern_offsets_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(dprm, batch, nrow, ncol, cell,
+                                                                       table);
+  rc = after(cudaSuccess, "matern_offsets_kernel");
+  if (rc) return rc;
+  const int grid = mrg::sm_count() * 8;
+  matern_fill_kernel<<<grid, 256, 0, st>>>(table, batch, nrow, ncol, cov, ld, n * ld);
+  return after(cudaSuccess, "matern_fill_kernel");
+}
+
+int mrg_grf_matern_points(const mrg_matern_params* params, uint32_t batch, const double* xy,
+                          uint64_t n, double* cov, uint64_t ld, void* scratch,
+                          uint64_t scratch_bytes, void* stream) {
+  if (!params || !xy || !cov || !scratch) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  if (batch == 0 || batch > kMaxBatch) return mrg::set_error(MRG_EINVAL, "batch must be 1..64");
+  if (n == 0) return MRG_OK;
+  if (n > (1u << 20)) return mrg::set_error(MRG_ERANGE, "more than 2^20 points");
+  if (ld < n) return mrg::set_error(MRG_EINVAL, "ld < n");
+  if (reinterpret_cast<uintptr_t>(cov) % 8 || reinterpret_cast<uintptr_t>(xy) % 8 ||
+      reinterpret_cast<uintptr_t>(scratch) % 256 || scratch_bytes < 4096)
+    return mrg::set_error(MRG_EINVAL, "misaligned pointer or scratch below 4096 bytes");
+  ParamBlock pb;
+  int rc = params_block(params, batch, &pb);
+  if (rc) return rc;
+  rc = mrg::ensure_device_ready();
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  rc = upload_params(pb, batch, scratch, st);
+  if (rc) return rc;
+  const int grid = mrg::sm_count() * 8;
+  matern_points_kernel<<<grid, 256, 0, st>>>(static_cast<const MaternParams*>(scratch), batch, xy,
+                                             n, cov, ld, n * ld);
+  return after(cudaSuccess, "matern_points_kernel");
+}
+
+uint64_t mrg_grf_ldl_workspace_bytes(uint64_t n, uint32_t batch) {
+  return LdlLayout(n).bytes(batch);
+}
+
+int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, void* workspace,
+                uint64_t workspace_bytes, int32_t* info, void* stream) {
+  if (!a || !d || !workspace) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  if (batch == 0 || batch > 255) return mrg::set_error(MRG_EINVAL, "batch must be 1..255");
+  if (n == 0) return MRG_OK;
+  if (n > (1u << 20)) return mrg::set_error(MRG_ERANGE, "n above 2^20");
+  if (lda < n) return mrg::set_error(MRG_EINVAL, "lda < n");
+  if (reinterpret_cast<uintptr_t>(a) % 8 || reinterpret_cast<uintptr_t>(d) % 8 ||
+      reinterpret_cast<uintptr_t>(workspace) % 1024)
+    return mrg::set_error(MRG_EINVAL, "a or d not 8-byte, or workspace not 1024-byte aligned");
+  const LdlLayout L(n);
+  if (workspace_bytes < L.bytes(batch))
+    return mrg::set_error(MRG_EINVAL, "workspace smaller than mrg_grf_ldl_workspace_bytes");
+  int rc = mrg::ensure_device_ready();
+  if (rc) return rc;
+  rc = set_attrs_once();
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  int* status = reinterpret_cast<int*>(ws);
+  int* dinfo = status + 1;
+  int* nonuniform = status + 256;
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.common, st);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "clearing the status words");
+  char* base = ws + L.common;
+  const uint64_t pm = L.per_matrix;
+  const uint64_t a_ms = n * lda;
+  int32_t* eq = reinterpret_cast<int32_t*>(base + L.exp_eq);
+  const dim3 egrid((unsigned)((n + 255) / 256), batch);
+  equil_exps_kernel<<<egrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform);
+  if ((rc = after(cudaSuccess, "equil_exps_kernel"))) return rc;
+  const dim3 agrid((unsigned)std::min<uint64_t>((n * (n + 1) / 2 + 255) / 256,
+                                                (uint64_t)mrg::sm_count() * 16), batch);
+  equil_apply_kernel<<<agrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, 1);
+  if ((rc = after(cudaSuccess, "equil_apply_kernel (scale)"))) return rc;
+  for (uint64_t k0 = 0; k0 < n; k0 += NB) {
+    const uint32_t kb = (uint32_t)std::min<uint64_t>(NB, n - k0);
+    const uint64_t t0 = k0 + kb, nt = n - t0;
+    DiagArgs dg;
+    dg.a = a;
+    dg.lda = lda;
+    dg.a_mstride = a_ms;
+    dg.d = d;
+    dg.d_mstride = n;
+    dg.k0 = (uint32_t)k0;
+    dg.kb = kb;
+    dg.img_x = reinterpret_cast<uint8_t*>(base + L.img_x);
+    dg.exp_x = reinterpret_cast<int32_t*>(base + L.exp_x);
+    dg.img_x_mstride = pm;
+    dg.exp_x_mstride = pm / 4;
+    dg.info = dinfo;
+    ldl_diag_kernel<kSlices><<<batch, 512, NB * DG * sizeof(mrg::df), st>>>(dg);
+    if ((rc = after(cudaSuccess, "ldl_diag_kernel"))) return rc;
+    if (nt == 0) break;
+    const uint32_t rows_pad = (uint32_t)align_up(nt, RB_A);
+    // panel operand: A_ik (rows t0.., columns k0.., kb wide)
+    SliceArgs sa;
+    sa.a = a + t0 * lda + k0;
+    sa.lda = lda;
+    sa.a_mstride = a_ms;
+    sa.rows = (uint32_t)nt;
+    sa.rows_pad = rows_pad;
+    sa.kb = kb;
+    sa.img_a = reinterpret_cast<uint8_t*>(base + L.img_a);
+    sa.exp_a = reinterpret_cast<int32_t*>(base + L.exp_a);
+    sa.img_a_mstride = pm;
+    sa.exp_a_mstride = pm / 4;
+    sa.img_b = nullptr;
+    sa.exp_b = nullptr;
+    sa.img_b_mstride = sa.exp_b_mstride = 0;
+    sa.colscale = nullptr;
+    sa.colscale_mstride = 0;
+    const dim3 sgrid(rows_pad / 8, batch);
+    slice_kernel<kSlices><<<sgrid, 256, 0, st>>>(sa);
+    if ((rc = after(cudaSuccess, "slice_kernel (panel)"))) return rc;
+    // L_ik = A_ik X^T, written over A_ik
+    GemmArgs gp;
+    gp.img_a = sa.img_a;
+    gp.exp_a = sa.exp_a;
+    gp.img_b = dg.img_x;
+    gp.exp_b = dg.exp_x;
+    gp.img_a_mstride = pm;
+    gp.exp_a_mstride = pm / 4;
+    gp.img_b_mstride = pm;
+    gp.exp_b_mstride = pm / 4;
+    gp.c = a + t0 * lda + k0;
+    gp.ldc = lda;
+    gp.c_mstride = a_ms;
+    gp.m = (uint32_t)nt;
+    gp.n = kb;
+    gp.tiles_n = (kb + BN - 1) / BN;
+    gp.status = status;
+    const dim3 pgrid((unsigned)((nt + BM - 1) / BM * gp.tiles_n), batch);
+    ozaki_gemm_kernel<kSlices, false><<<pgrid, 128, GemmSmem<kSlices>::TOTAL, st>>>(gp);
+    if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (panel)"))) return rc;
+    // trailing operands: L_ik (A role) and W = L_ik D_k (B role)
+    sa.img_b = reinterpret_cast<uint8_t*>(base + L.img_w);
+    sa.exp_b = reinterpret_cast<int32_t*>(base + L.exp_w);
+    sa.img_b_mstride = pm;
+    sa.exp_b_mstride = pm / 4;
+    sa.colscale = d + k0;
+    sa.colscale_mstride = n;
+    slice_kernel<kSlices><<<sgrid, 256, 0, st>>>(sa);
+    if ((rc = after(cudaSuccess, "slice_kernel (trailing)"))) return rc;
+    GemmArgs gt = gp;
+    gt.img_b = sa.img_b;
+    gt.exp_b = sa.exp_b;
+    gt.c = a + t0 * lda + t0;
+    gt.n = (uint32_t)nt;
+    gt.tiles_n = (uint32_t)((nt + BN - 1) / BN);
+    const uint64_t T = (nt + BM - 1) / BM;
+    const dim3 tgrid((unsigned)(T * (T - 1) + gt.tiles_n), batch);
+    ozaki_gemm_kernel<kSlices, true><<<tgrid, 128, GemmSmem<kSlices>::TOTAL, st>>>(gt);
+    if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (trailing)"))) return rc;
+  }
+  equil_apply_kernel<<<agrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, -1);
+  if ((rc = after(cudaSuccess, "equil_apply_kernel (unscale)"))) return rc;
+  if (info) {
+    int32_t h[256];
+    e = cudaMemcpyAsync(h, ws, 4 * (1 + batch), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
+    for (uint32_t b = 0; b < batch; ++b) info[b] = h[1 + b];
+    if (h[0]) return mrg::set_error(MRG_ETIMEOUT, "a tensor-core wait gave up (2 s)");
+  }
+  return MRG_OK;
+}
+
+uint64_t mrg_grf_simulate_scratch_bytes(uint64_t n, uint32_t nsim, uint32_t batch) {
+  return (uint64_t)batch * nsim * n * 8;
+}
+
+int mrg_grf_simulate(const double* l, const double* d, uint64_t n, uint64_t lda, uint32_t batch,
+                     const double* z, uint32_t nsim, double* u, void* scratch,
+                     uint64_t scratch_bytes, void* stream) {
+  if (!l || !d || !z || !u || !scratch) return mrg::set_error(MRG_EINVAL, "NULL argument");
+  if (batch == 0 || batch > 65535) return mrg::set_error(MRG_EINVAL, "batch must be 1..65535");
+  if (n == 0 || nsim == 0) return MRG_OK;
+  if (lda < n) return mrg::set_error(MRG_EINVAL, "lda < n");
+  if (n > (1u << 20) || nsim > (1u << 16)) return mrg::set_error(MRG_ERANGE, "n or nsim too large");
+  if ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(d) |
+       reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(u) |
+       reinterpret_cast<uintptr_t>(scratch)) % 8)
+    return mrg::set_error(MRG_EINVAL, "pointers must be 8-byte aligned");
+  if (scratch_bytes < mrg_grf_simulate_scratch_bytes(n, nsim, batch))
+    return mrg::set_error(MRG_EINVAL, "scratch smaller than mrg_grf_simulate_scratch_bytes");
+  int rc = mrg::ensure_device_ready();
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* y = static_cast<double*>(scratch);
+  const uint64_t tot = (uint64_t)batch * nsim * n;
+  scale_sqrt_d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, n, z, y, n, nsim, batch);
+  if ((rc = after(cudaSuccess, "scale_sqrt_d_kernel"))) return rc;
+  const dim3 grid((unsigned)((n + 7) / 8), batch);
+  lower_times_y_kernel<<<grid, 256, 0, st>>>(l, lda, n * lda, y, u, n, nsim, batch);
+  return after(cudaSuccess, "lower_times_y_kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,733 @@
+// grf_kernels.cuh -- Gaussian random fields by direct matrix decomposition
+// (Sec. 5, Algorithm 2) on GB300: Matern covariance matrices (step 1), their
+// LDL^T factorisation (step 2) and U = L D^(1/2) Z (step 4; Z comes from the
+// generator's normals, step 3).
+//
+// The factorisation is a right-looking blocked LDL^T with 128-column panels:
+//   1. the 128 x 128 diagonal block is factored (and its unit lower factor
+//      inverted) by one CTA per matrix in double-float arithmetic;
+//   2. the panel below it, L_ik = A_ik L_kk^-T D_k^-1, and
+//   3. the trailing update A_ij -= L_ik D_k L_jk^T
+// are fp64 matrix products with K = 128, computed on the tensor cores by an
+// error-free splitting of each fp64 operand into S bf16 slices (the Ozaki
+// scheme: Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012)), here in its fixed-point form:
+//   * every operand row i is scaled by 2^-e_i so that its entries lie in
+//     (-1/2, 1/2), rounded to a 7S-bit fixed-point integer X and cut into S
+//     balanced base-128 digits s_0 .. s_(S-1) (|s_p| <= 64, exact in bf16):
+//     a_ik ~ 2^e_i sum_p s_p 2^(-7(p+1)), error <= 2^(e_i - 7S - 1);
+//   * the digit products of one level l = p + q (p, q < S, l < S) are summed
+//     by tcgen05.mma into one fp32 TMEM accumulator; every product is an
+//     integer below 2^12 in magnitude, a level holds at most 8 x 128 of them,
+//     so each level sum is an exact integer of magnitude <= 2^22;
+//   * the S level sums are combined exactly in 128-bit integers (two
+//     64-bit words), T = sum_l acc_l 128^(S-1-l) (|T| < 2^69), and the
+//     product is T 2^(e_i + f_j - 7(S+1)), rounded once to fp64.
+// Levels l >= S are dropped: with S = 8 their weight is below 2^-63 of the
+// leading term, under the 2^-57 truncation of the operands themselves.
+#pragma once
+#include <stdint.h>
+
+#include "matern.cuh"
+#include "tc_sm100.cuh"
+#include "transforms_df.cuh"
+
+namespace mrg {
+namespace grf {
+
+constexpr int NB = 128;        // panel width (the K extent of every product)
+constexpr int BM = 128;        // output tile rows (MMA M)
+constexpr int BN = 64;         // output tile columns (MMA N)
+constexpr int RB_A = 128;      // rows per block of an A-role operand image
+constexpr int RB_B = 64;       // rows per block of a B-role operand image
+constexpr uint32_t SLICE_A = RB_A * NB * 2;  // bytes of one bf16 slice of an A block (32 KB)
+constexpr uint32_t SLICE_B = RB_B * NB * 2;  // (16 KB)
+constexpr uint64_t WAIT_NS = 2000000000ull;  // bound of every device wait (2 s)
+
+// Error flags a kernel records (bitwise or) in the caller's status word.
+constexpr int ERR_TIMEOUT = 1;
+
+// ---------------------------------------------------------------------------
+// Step 1: Matern covariance (Sec. 5).  Sigma_ij = var * corr(x), x =
+// sqrt(8 kappa) |d_ij| / phi, d_ij = diag(1, omega) R(theta) (x_i - x_j).
+// ---------------------------------------------------------------------------
+
+struct MaternParams {
+  double kappa, var, norm;       // norm = 2^(1-kappa) / Gamma(kappa)
+  double scale;                  // sqrt(8 kappa) / phi
+  double c, s, omega;            // cos theta, sin theta, anisotropy ratio
+};
+
+__device__ __forceinline__ double matern_cov_at(const MaternParams& p, double dx, double dy) {
+  const double u = p.c * dx - p.s * dy;
+  const double v = p.omega * (p.s * dx + p.c * dy);
+  const double x = p.scale * sqrt(u * u + v * v);
+  return p.var * matern_corr(x, p.kappa, p.norm);
+}
+
+// Raster of nrow x ncol square cells (row-major point order, point k at
+// column k mod ncol, row k div ncol): the covariance depends only on the
+// offset (dr, dc) between two cells, so it is evaluated once per offset,
+// dr in (-nrow, nrow), dc in (-ncol, ncol), table[(dr + nrow - 1) (2 ncol - 1)
+// + dc + ncol - 1].  One thread per (matrix, offset).
+__global__ void __launch_bounds__(256) matern_offsets_kernel(const MaternParams* __restrict__ prm,
+                                                             uint32_t batch, uint32_t nrow,
+                                                             uint32_t ncol, double cell,
+                                                             double* __restrict__ table) {
+  const uint64_t per = (uint64_t)(2 * nrow - 1) * (2 * ncol - 1);
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * batch) return;
+  const uint32_t b = (uint32_t)(t / per);
+  const uint64_t o = t - (uint64_t)b * per;
+  const int dr = (int)(o / (2 * ncol - 1)) - (int)(nrow - 1);
+  const int dc = (int)(o % (2 * ncol - 1)) - (int)(ncol - 1);
+  table[t] = matern_cov_at(prm[b], dc * cell, dr * cell);
+}
+
+// Fills the n x n matrices (n = nrow ncol, leading dimension ld) from the
+// offset tables: 32-byte rows of four entries per thread.
+__global__ void __launch_bounds__(256) matern_fill_kernel(const double* __restrict__ table,
+                                                          uint32_t batch, uint32_t nrow,
+                                                          uint32_t ncol, double* __restrict__ cov,
+                                                          uint64_t ld, uint64_t mstride) {
+  const uint64_t n = (uint64_t)nrow * ncol;
+  const uint64_t q = (n + 3) / 4;                    // groups of four columns per row
+  const uint64_t per = n * q;
+  const uint64_t per_t = (uint64_t)(2 * nrow - 1) * (2 * ncol - 1);
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per * batch; t += step) {
+    const uint32_t b = (uint32_t)(t / per);
+    const uint64_t rem = t - (uint64_t)b * per;
+    const uint64_t i = rem / q;
+    const uint64_t j0 = (rem - i * q) * 4;
+    const uint32_t ri = (uint32_t)(i / ncol), ci = (uint32_t)(i % ncol);
+    const double* tb = table + (uint64_t)b * per_t;
+    double* row = cov + (uint64_t)b * mstride + i * ld;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint64_t j = j0 + e;
+      if (j < n) {
+        const uint32_t rj = (uint32_t)(j / ncol), cj = (uint32_t)(j % ncol);
+        const int dr = (int)ri - (int)rj, dc = (int)ci - (int)cj;
+        row[j] = tb[(uint64_t)(dr + (int)nrow - 1) * (2 * ncol - 1) + (dc + (int)ncol - 1)];
+      }
+    }
+  }
+}
+
+// Arbitrary points (n x 2, x then y, device): one entry per thread.
+__global__ void __launch_bounds__(256) matern_points_kernel(const MaternParams* __restrict__ prm,
+                                                            uint32_t batch, const double* __restrict__ xy,
+                                                            uint64_t n, double* __restrict__ cov,
+                                                            uint64_t ld, uint64_t mstride) {
+  const uint64_t per = n * n;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per * batch; t += step) {
+    const uint32_t b = (uint32_t)(t / per);
+    const uint64_t rem = t - (uint64_t)b * per;
+    const uint64_t i = rem / n, j = rem - i * n;
+    const double dx = xy[2 * i] - xy[2 * j], dy = xy[2 * i + 1] - xy[2 * j + 1];
+    cov[(uint64_t)b * mstride + i * ld + j] = i == j ? prm[b].var : matern_cov_at(prm[b], dx, dy);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operand slicing.  An operand of the products is a set of rows with a K
+// extent of 128 (zero beyond the panel's width), stored as an image of
+// blocks of RB rows; block b holds S slices of RB x 128 bf16 each, in the
+// shared-memory layout the MMA reads (tc_sm100.cuh), so that a block's slice
+// is one contiguous bulk copy.  exps[row] = e_row.
+// ---------------------------------------------------------------------------
+
+// Biased exponent field of an fp64 value (0 for zero and subnormals).
+__device__ __forceinline__ int biased_exp(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
+// round(v 2^-e 2^(7S)) as an integer, for |v| < 2^(e-1); subnormals give 0.
+template <int S>
+__device__ __forceinline__ int64_t fixed_point(double v, int e) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  if (eb == 0) return 0;
+  const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  // v = m 2^(eb - 1075); X = m 2^(eb - 1075 + 7S - e) = m >> sh
+  const int sh = 1075 - eb - 7 * S + e;
+  int64_t x;
+  if (sh <= 0) x = (int64_t)(m << (-sh));          // sh >= -2 (|v| < 2^(e-1), S <= 8)
+  else if (sh >= 60) x = 0;
+  else x = (int64_t)((m + (1ull << (sh - 1))) >> sh);
+  return (bits >> 63) ? -x : x;
+}
+
+// bf16 bits of a small integer d (|d| <= 64: exact).
+__device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
+
+// One row of an operand, four consecutive K elements per lane (k = 4 lane ..
+// 4 lane + 3, zero beyond the panel), sliced by one warp: the row exponent
+// (warp maximum), then S digits per element written into the image block
+// `blk` (RB rows) at row rr.  All 32 lanes must call it.
+template <int S>
+__device__ __forceinline__ void slice_row(const double v[4], uint8_t* __restrict__ blk, int RB,
+                                          int rr, int32_t* __restrict__ exp_out) {
+  const int lane = threadIdx.x & 31;
+  int emax = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) emax = max(emax, biased_exp(v[i]));
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  // |v| < 2^(emax - 1022) = 2^(e - 1): entries of the scaled row lie in (-1/2, 1/2)
+  const int e = emax == 0 ? 0 : emax - 1023 + 2;
+  uint32_t dig[S][2];
+  int64_t x[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = emax == 0 ? 0 : fixed_point<S>(v[i], e);
+  uint32_t d16[S][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t X = x[i];
+#pragma unroll
+    for (int p = S - 1; p >= 1; --p) {
+      const int d = (int)((X + 64) & 127) - 64;   // balanced digit in [-64, 63]
+      d16[p][i] = bf16_of_small_int(d);
+      X = (X - d) >> 7;
+    }
+    d16[0][i] = bf16_of_small_int((int)X);        // |X| <= 64
+  }
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+    dig[p][0] = d16[p][0] | (d16[p][1] << 16);
+    dig[p][1] = d16[p][2] | (d16[p][3] << 16);
+  }
+  const uint32_t off = tc::sw128_offset((uint32_t)RB, (uint32_t)rr, (uint32_t)(4 * lane));
+#pragma unroll
+  for (int p = 0; p < S; ++p)
+    *reinterpret_cast<uint2*>(blk + (size_t)p * RB * NB * 2 + off) = make_uint2(dig[p][0], dig[p][1]);
+  if (lane == 0) *exp_out = e;
+}
+
+// Slices rows [0, rows_pad) of a panel: row r is a[(r) * lda + k] for k < kb
+// (zero for r >= rows or k >= kb).  Into img_a (A role, 128-row blocks) as is,
+// and, when img_b is set, into img_b (B role, 64-row blocks) multiplied by
+// colscale[k] (W = L D).  One warp per row.
+struct SliceArgs {
+  const double* a;
+  uint64_t lda, a_mstride;
+  uint32_t rows, rows_pad, kb;
+  uint8_t* img_a;
+  int32_t* exp_a;
+  uint64_t img_a_mstride, exp_a_mstride;
+  uint8_t* img_b;
+  int32_t* exp_b;
+  uint64_t img_b_mstride, exp_b_mstride;
+  const double* colscale;
+  uint64_t colscale_mstride;
+};
+
+template <int S>
+__global__ void __launch_bounds__(256) slice_kernel(SliceArgs g) {
+  const uint32_t b = blockIdx.y;
+  const uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= g.rows_pad) return;  // whole warps leave together
+  const int lane = threadIdx.x & 31;
+  const double* row = g.a + b * g.a_mstride + (uint64_t)r * g.lda;
+  double v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t k = 4 * lane + i;
+    v[i] = (r < g.rows && k < g.kb) ? row[k] : 0.0;
+  }
+  slice_row<S>(v, g.img_a + b * g.img_a_mstride + (uint64_t)(r / RB_A) * S * SLICE_A, RB_A,
+               (int)(r % RB_A), g.exp_a + b * g.exp_a_mstride + r);
+  if (g.img_b) {
+    const double* cs = g.colscale + b * g.colscale_mstride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t k = 4 * lane + i;
+      v[i] = k < g.kb ? v[i] * cs[k] : 0.0;
+    }
+    slice_row<S>(v, g.img_b + b * g.img_b_mstride + (uint64_t)(r / RB_B) * S * SLICE_B, RB_B,
+                 (int)(r % RB_B), g.exp_b + b * g.exp_b_mstride + r);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The products on the tensor cores.  One CTA (128 threads) per 128 x 64
+// output tile: thread 0 bulk-copies the B block's S slices and streams the A
+// block's slices through a ring of NST stages, issuing for A slice p the
+// MMAs with B slices q = 0 .. S-1-p into TMEM accumulator p + q (64 columns
+// each, S x 64 <= 512); then all four warps read the accumulators, combine
+// the levels exactly and write (PANEL: C = product) or subtract (TRAIL:
+// C -= product) in fp64.
+// ---------------------------------------------------------------------------
+
+struct GemmArgs {
+  const uint8_t* img_a;    // A-role image: block ti = rows [128 ti, 128 ti + 128) of the output
+  const int32_t* exp_a;
+  const uint8_t* img_b;    // B-role image: block tj = columns [64 tj, 64 tj + 64)
+  const int32_t* exp_b;
+  uint64_t img_a_mstride, exp_a_mstride, img_b_mstride, exp_b_mstride;
+  double* c;               // output element (r, col) at c + b c_mstride + r ldc + col
+  uint64_t ldc, c_mstride;
+  uint32_t m, n;           // output rows and columns
+  uint32_t tiles_n;        // PANEL: column tiles per row of tiles
+  int* status;
+};
+
+template <int S>
+struct GemmSmem {
+  static constexpr int NST = 3;                                   // A-slice ring stages
+  static constexpr uint32_t B_BYTES = (uint32_t)S * SLICE_B;
+  static constexpr uint32_t A_OFF = B_BYTES;
+  static constexpr uint32_t BAR_OFF = A_OFF + NST * SLICE_A;
+  static constexpr uint32_t TOTAL = BAR_OFF + 128 + 1024;         // barriers + slot, alignment slack
+};
+
+// Tile (ti, tj) of the lower-triangular tile set of an m x m output with
+// 128 x 64 tiles: row of tiles ti holds tiles tj < min(2 ti + 2, tiles_n).
+__device__ __forceinline__ void lower_tile(uint32_t x, uint32_t& ti, uint32_t& tj) {
+  uint32_t t = (uint32_t)((sqrtf(4.0f * (float)x + 1.0f) - 1.0f) * 0.5f);
+  while ((uint64_t)(t + 1) * (t + 2) <= x) ++t;
+  while ((uint64_t)t * (t + 1) > x) --t;
+  ti = t;
+  tj = x - t * (t + 1);
+}
+
+// 128-bit two's-complement value T = hi 2^64 + lo times 2^E, rounded to
+// nearest-even fp64 (0 for T = 0 and below the normal range).
+__device__ __forceinline__ double scaled_i128_to_f64(uint64_t hi, uint64_t lo, int E) {
+  if ((hi | lo) == 0) return 0.0;
+  const uint64_t sgn = hi & 0x8000000000000000ull;
+  if (sgn) {                                  // magnitude: two's-complement negation
+    lo = ~lo + 1;
+    hi = ~hi + (lo == 0);
+  }
+  int lz;
+  uint64_t top, low;
+  if (hi) {
+    lz = __clzll((long long)hi);
+    top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    low = lo << lz;
+  } else {
+    lz = 64 + __clzll((long long)lo);
+    top = lo << (lz - 64);
+    low = 0;
+  }
+  const int eb = 127 - lz + E + 1023;         // biased exponent of the result
+  if (eb <= 0) return 0.0;
+  uint64_t mant = top >> 11;                  // 53 bits with the leading one
+  const uint64_t rem = top & 0x7FF;
+  const bool above = rem > 0x400 || (rem == 0x400 && low != 0);
+  mant += above | ((rem == 0x400) & (low == 0) & (mant & 1));
+  const uint64_t bits = ((uint64_t)(eb - 1) << 52) + mant;   // a rounding carry steps the exponent
+  return __longlong_as_double((long long)(bits | sgn));
+}
+
+template <int S, bool TRAIL>
+__global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs g) {
+  using SM = GemmSmem<S>;
+  constexpr int NST = SM::NST;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + SM::A_OFF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::BAR_OFF);
+  uint64_t* full_b = bar;                 // [1]
+  uint64_t* full_a = bar + 1;             // [NST]
+  uint64_t* empty_a = bar + 1 + NST;      // [NST]
+  uint64_t* done = bar + 1 + 2 * NST;     // [1]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + 2 * NST);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 3 + 2 * NST);
+
+  uint32_t ti, tj;
+  if (TRAIL) {
+    lower_tile(blockIdx.x, ti, tj);
+  } else {
+    ti = blockIdx.x / g.tiles_n;
+    tj = blockIdx.x % g.tiles_n;
+  }
+  const uint32_t row0 = ti * BM, col0 = tj * BN;
+  if (row0 >= g.m || col0 >= g.n) return;   // uniform over the CTA, before any allocation
+  const uint32_t b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    tc::mbar_init(full_b, 1);
+    for (int i = 0; i < NST; ++i) {
+      tc::mbar_init(&full_a[i], 1);
+      tc::mbar_init(&empty_a[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, 512);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint8_t* gA = g.img_a + b * g.img_a_mstride + (uint64_t)ti * S * SLICE_A;
+      const uint8_t* gB = g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B;
+      tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
+      tc::bulk_g2s(sB, gB, SM::B_BYTES, full_b);
+      for (int p = 0; p < NST && p < S; ++p) {
+        tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
+        tc::bulk_g2s(sA + p * SLICE_A, gA + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
+      }
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      bool ok = tc::mbar_wait(full_b, 0, WAIT_NS);
+      for (int p = 0; p < S && ok; ++p) {
+        const int st = p % NST;
+        ok = tc::mbar_wait(&full_a[st], (p / NST) & 1, WAIT_NS);
+        if (!ok) break;
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_u32(sA + st * SLICE_A);
+        for (int q = 0; q < S - p; ++q) {
+          const uint32_t b_base = tc::smem_u32(sB + q * SLICE_B);
+          const uint32_t d = tmem + (uint32_t)(p + q) * BN;
+#pragma unroll
+          for (int kk = 0; kk < NB / 16; ++kk) {
+            const uint32_t ao = a_base + (kk >> 2) * (RB_A * 128) + (kk & 3) * 32;
+            const uint32_t bo = b_base + (kk >> 2) * (RB_B * 128) + (kk & 3) * 32;
+            tc::mma_bf16(d, tc::sw128_desc(ao), tc::sw128_desc(bo), idesc, (p > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&empty_a[st]);
+        // refill the stage of slice p - 1 once its MMAs are done (those of
+        // slice p are queued behind them, so the tensor pipe keeps busy)
+        const int pr = p - 1;
+        if (pr >= 0 && pr + NST < S) {
+          const int sr = pr % NST;
+          ok = tc::mbar_wait(&empty_a[sr], (pr / NST) & 1, WAIT_NS);
+          if (!ok) break;
+          tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
+          tc::bulk_g2s(sA + sr * SLICE_A, gA + (size_t)(pr + NST) * SLICE_A, SLICE_A, &full_a[sr]);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(g.status, ERR_TIMEOUT);
+      }
+      tc::mma_commit(done);   // every MMA issued above has completed when this arrives
+    }
+    __syncwarp();
+  }
+  // all threads: the accumulators are final (bounded wait)
+  const bool fin = tc::mbar_wait(done, 0, WAIT_NS);
+  __syncthreads();
+  if (!fin && threadIdx.x == 0) atomicOr(g.status, ERR_TIMEOUT);
+  if (fin && *abort_flag == 0) {
+    tc::tc_fence_after();
+    const uint32_t r = (uint32_t)(warp * 32 + lane);
+    const uint32_t row = row0 + r;
+    const bool row_ok = row < g.m;
+    const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
+    double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
+    // sum_l acc_l 128^(S-1-l) with acc_l read as (bits of acc_l + 1.5 2^23)
+    // - 0x4B400000, the constant part subtracted once
+    uint64_t magic_lo = 0, magic_hi = 0;
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      magic_hi = (magic_hi << 7) | (magic_lo >> 57);
+      magic_lo = (magic_lo << 7) + 0x4B400000u;
+      magic_hi += magic_lo < 0x4B400000u;
+    }
+    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (uint32_t c0 = 0; c0 < BN; c0 += 8) {
+      float acc[S][8];
+#pragma unroll
+      for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
+      tc::tmem_ld_wait();
+      if (!row_ok) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const uint32_t col = col0 + c0 + e;
+        if (col >= g.n) break;
+        // T = sum_l acc_l 128^(S-1-l) needs up to 7 S + 13 bits: two words,
+        // hi:lo, a Horner step shifting both by 7 and adding the level's
+        // offset integer into lo with its carry
+        uint64_t lo = 0, hi = 0;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          hi = (hi << 7) | (lo >> 57);
+          lo <<= 7;
+          const uint64_t add = __float_as_uint(acc[l][e] + 12582912.0f);
+          lo += add;
+          hi += lo < add;
+        }
+        hi -= magic_hi + (lo < magic_lo);
+        lo -= magic_lo;
+        const int eb = g.exp_b[b * g.exp_b_mstride + col];
+        const double v = scaled_i128_to_f64(hi, lo, ea + eb - 7 * (S + 1));
+        if (TRAIL) crow[col] = crow[col] - v;
+        else crow[col] = v;
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal block: LDL^T of a kb x kb block (kb <= 128) and the inverse X of
+// its unit lower factor, by one CTA of 512 threads per matrix, in
+// double-float arithmetic (fp32 pairs; GB300's FP64 rate is a small fraction
+// of its FP32 rate) on the block scaled by a power of two (its largest
+// diagonal entry brought near 1, so that fp32's exponent range holds it).
+// Writes L (strict lower part of the block, unit diagonal implied), D (on the
+// block's diagonal and into d[]), and the B-role operand of the panel
+// product, row n of B = row n of X divided by d_n (so that L_ik = A_ik B^T).
+// ---------------------------------------------------------------------------
+
+constexpr int DG = NB + 1;   // row pitch of the shared block, in float pairs (odd: fewer bank conflicts)
+
+struct DiagArgs {
+  double* a;
+  uint64_t lda, a_mstride;
+  double* d;
+  uint64_t d_mstride;
+  uint32_t k0, kb;
+  uint8_t* img_x;
+  int32_t* exp_x;
+  uint64_t img_x_mstride, exp_x_mstride;
+  int* info;               // per matrix: 0, or 1 + the first non-positive pivot's index
+};
+
+__device__ __forceinline__ df df_of(double x) {
+  const float hi = __double2float_rn(x);
+  return df{hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double f64_of(df v) { return (double)v.hi + (double)v.lo; }
+
+// a - b c in double-float
+__device__ __forceinline__ df df_fnms(df a, df b, df c) {
+  const float p = __fmul_rn(b.hi, c.hi);
+  float e = __fmaf_rn(b.hi, c.hi, -p);
+  e = __fmaf_rn(b.hi, c.lo, e);
+  e = __fmaf_rn(b.lo, c.hi, e);
+  const df s = two_sum(a.hi, -p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, e)));
+}
+
+template <int S>
+__global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
+  extern __shared__ df sm[];               // [NB][DG]: L below the diagonal, X^T above
+  __shared__ df s_w[NB];
+  __shared__ double s_r[NB];               // 1 / d_j of the scaled block
+  __shared__ double s_d[NB];
+  __shared__ int s_scale, s_bad;
+  const uint32_t b = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kb = (int)g.kb;
+  double* A = g.a + b * g.a_mstride + (uint64_t)g.k0 * g.lda + g.k0;
+  if (warp == 0) {
+    int em = 0;
+    for (int j = lane; j < kb; j += 32) em = max(em, biased_exp(A[(uint64_t)j * g.lda + j]));
+    em = __reduce_max_sync(0xffffffffu, em);
+    if (lane == 0) {
+      s_scale = em == 0 ? 0 : em - 1023;
+      s_bad = 0;
+    }
+  }
+  __syncthreads();
+  const int sc = s_scale;
+  const double down = scalbn(1.0, -sc), up = scalbn(1.0, sc);
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx / kb, j = idx - (idx / kb) * kb;
+    sm[i * DG + j] = j <= i ? df_of(A[(uint64_t)i * g.lda + j] * down) : df{0.0f, 0.0f};
+  }
+  __syncthreads();
+  // right-looking LDL^T
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      const double dj = f64_of(sm[j * DG + j]);
+      if (!(dj > 0x1p-100)) {
+        if (!s_bad) s_bad = 1 + j;
+        s_r[j] = 0.0;
+      } else {
+        s_r[j] = 1.0 / dj;
+      }
+      s_d[j] = dj;
+    }
+    __syncthreads();
+    const df rj = df_of(s_r[j]);
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) {
+      const df w = sm[i * DG + j];
+      s_w[i] = w;
+      sm[i * DG + j] = df_mul(w, rj);
+    }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < kb; i += 16) {
+      const df lij = sm[i * DG + j];
+      for (int l = j + 1 + lane; l <= i; l += 32) sm[i * DG + l] = df_fnms(sm[i * DG + l], lij, s_w[l]);
+    }
+    __syncthreads();
+  }
+  // X = L^-1 (unit lower), column-oriented forward substitution in outer-
+  // product order; X[i][c] (i > c) is kept at sm[c][i]
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    const int c = idx / kb, i = idx - (idx / kb) * kb;
+    if (i > c) sm[c * DG + i] = df{0.0f, 0.0f};
+  }
+  __syncthreads();
+  for (int m = 0; m < kb; ++m) {
+    for (int i = m + 1 + warp; i < kb; i += 16) {
+      const df lim = sm[i * DG + m];
+      for (int c = lane; c <= m; c += 32) {
+        const df xmc = c == m ? df{1.0f, 0.0f} : sm[c * DG + m];
+        sm[c * DG + i] = df_fnms(sm[c * DG + i], lim, xmc);
+      }
+    }
+    __syncthreads();
+  }
+  // outputs: L and D into the matrix, D into d[]
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx / kb, j = idx - (idx / kb) * kb;
+    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of(sm[i * DG + j]);
+    else if (j == i) A[(uint64_t)i * g.lda + j] = s_d[i] * up;
+  }
+  for (int j = tid; j < kb; j += blockDim.x) g.d[b * g.d_mstride + g.k0 + j] = s_d[j] * up;
+  if (tid == 0 && s_bad) atomicCAS(&g.info[b], 0, (int)g.k0 + s_bad);
+  // B-role operand of the panel product: row n = X[n][:] / d_n, unscaled
+  uint8_t* img = g.img_x + b * g.img_x_mstride;
+  for (int n = warp; n < NB; n += 16) {
+    double v[4];
+    const double rn = n < kb ? s_r[n] * down : 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * lane + i;
+      double x = 0.0;
+      if (n < kb && k < kb) x = k == n ? 1.0 : (k < n ? f64_of(sm[k * DG + n]) : 0.0);
+      v[i] = x * rn;
+    }
+    slice_row<S>(v, img + (uint64_t)(n / RB_B) * S * SLICE_B, RB_B, n % RB_B,
+                 g.exp_x + b * g.exp_x_mstride + n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Equilibration by powers of two (exact): the products above are accurate to
+// ~2^-55 of their operand rows' largest entries, so a matrix whose diagonal
+// spans many orders of magnitude is factored as S A S with S = diag(2^-e_i),
+// e_i = floor(log2(a_ii) / 2), and its factors scaled back:
+// L_ij = L'_ij 2^(e_i - e_j), D_i = D'_i 2^(2 e_i).  A matrix whose e_i are
+// all equal (a stationary covariance: every a_ii = sigma^2) is left alone.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) equil_exps_kernel(const double* __restrict__ a, uint64_t lda,
+                                                         uint64_t a_mstride, uint64_t n,
+                                                         int32_t* __restrict__ e,
+                                                         uint64_t e_mstride, int* nonuniform) {
+  const uint32_t b = blockIdx.y;
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* A = a + b * a_mstride;
+  auto half_exp = [](double v) {
+    const int eb = biased_exp(v);
+    return eb == 0 ? 0 : (eb - 1023) >> 1;   // floor((eb - 1023) / 2)
+  };
+  const int ei = half_exp(A[i * lda + i]);
+  e[b * e_mstride + i] = ei;
+  if (ei != half_exp(A[0])) atomicOr(&nonuniform[b], 1);
+}
+
+// dir > 0: a_ij <- a_ij 2^(-e_i - e_j) on the lower triangle; dir < 0: the
+// factor back, L_ij <- L_ij 2^(e_i - e_j) (j < i), D_i <- D_i 2^(2 e_i) on
+// the diagonal and in d.  No-op for a matrix whose exponents are uniform.
+__global__ void __launch_bounds__(256) equil_apply_kernel(double* __restrict__ a, uint64_t lda,
+                                                          uint64_t a_mstride, uint64_t n,
+                                                          const int32_t* __restrict__ e,
+                                                          uint64_t e_mstride,
+                                                          const int* __restrict__ nonuniform,
+                                                          double* __restrict__ d, int dir) {
+  const uint32_t b = blockIdx.y;
+  if (!nonuniform[b]) return;
+  const int32_t* eb = e + b * e_mstride;
+  double* A = a + b * a_mstride;
+  const uint64_t total = n * (n + 1) / 2;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += step) {
+    // t -> (i, j), j <= i, row-major over the lower triangle
+    uint64_t i = (uint64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > t) --i;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    const uint64_t j = t - i * (i + 1) / 2;
+    double& v = A[i * lda + j];
+    if (dir > 0) {
+      v = scalbn(v, -eb[i] - eb[j]);
+    } else if (j < i) {
+      v = scalbn(v, eb[i] - eb[j]);
+    } else {
+      v = scalbn(v, 2 * eb[i]);
+      d[b * n + i] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step 4: U = L D^(1/2) Z for nsim columns of standard normals per matrix.
+// z and u are [batch][nsim][n] (one simulation contiguous); y = D^(1/2) z is
+// formed first, then one warp per row i accumulates sum_{j <= i} L_ij y_j
+// for every simulation (L_ii = 1) in fp64.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) scale_sqrt_d_kernel(const double* __restrict__ d,
+                                                           uint64_t d_mstride,
+                                                           const double* __restrict__ z,
+                                                           double* __restrict__ y, uint64_t n,
+                                                           uint32_t nsim, uint32_t batch) {
+  const uint64_t per = (uint64_t)nsim * n;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * batch) return;
+  const uint32_t b = (uint32_t)(t / per);
+  const uint64_t j = (t - (uint64_t)b * per) % n;
+  y[t] = sqrt(d[b * d_mstride + j]) * z[t];
+}
+
+constexpr int SIM_MAX = 8;   // simulations handled per pass of a row
+
+__global__ void __launch_bounds__(256) lower_times_y_kernel(const double* __restrict__ l,
+                                                            uint64_t ldl, uint64_t l_mstride,
+                                                            const double* __restrict__ y,
+                                                            double* __restrict__ u, uint64_t n,
+                                                            uint32_t nsim, uint32_t batch) {
+  const uint64_t row = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t b = blockIdx.y;
+  if (row >= n) return;
+  const double* lr = l + b * l_mstride + row * ldl;
+  const double* yb = y + (uint64_t)b * nsim * n;
+  double* ub = u + (uint64_t)b * nsim * n;
+  for (uint32_t s0 = 0; s0 < nsim; s0 += SIM_MAX) {
+    double acc[SIM_MAX];
+#pragma unroll
+    for (int s = 0; s < SIM_MAX; ++s) acc[s] = 0.0;
+    for (uint64_t j = lane; j <= row; j += 32) {
+      const double lij = j == row ? 1.0 : lr[j];
+#pragma unroll
+      for (int s = 0; s < SIM_MAX; ++s)
+        if (s0 + s < nsim) acc[s] = fma(lij, yb[(uint64_t)(s0 + s) * n + j], acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < SIM_MAX; ++s) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < SIM_MAX; ++s)
+        if (s0 + s < nsim) ub[(uint64_t)(s0 + s) * n + row] = acc[s];
+    }
+  }
+}
+
+}  // namespace grf
+}  // namespace mrg

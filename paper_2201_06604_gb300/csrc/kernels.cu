@@ -556,11 +556,14 @@ cudaError_t launch_generate_g(const DevStreams& s, uint64_t n, int dist, int dty
   uint64_t L = cfg.seg_len;
   if (L == 0) {
     // Heuristic: about 8 segments per resident lane slot, at least 512 draws
-    // (jump cost amortised), at most the whole row.
+    // (jump cost amortised), at most the whole row.  A call too small to give
+    // every lane slot 512 draws (a single stream of 10^6 draws, say) takes
+    // shorter segments, down to 64 draws, so that it still spreads over the
+    // GPU instead of running a few warps through long serial segments.
     const uint64_t lanes = (uint64_t)sm_count() * 2048;
     const uint64_t total = n * s.n;
     L = total / (lanes * 8);
-    L = std::max<uint64_t>(L, 512);
+    if (L < 512) L = std::min<uint64_t>(std::max<uint64_t>(total / lanes, 64), 512);
   }
   L = (L + ce - 1) / ce * ce;                 // multiple of 8 (even: pairs stay aligned)
   const uint64_t ncap = (n + ce - 1) / ce * ce;

@@ -78,6 +78,13 @@ class _BatchTuneEntry(ctypes.Structure):
     _fields_ = [("tiling", Tiling), ("tiles", ctypes.c_uint64), ("ms", ctypes.c_float)]
 
 
+class MaternParams(ctypes.Structure):
+    """One Matern parameter set (mrg_matern_params, Sec. 5)."""
+    _fields_ = [("shape", ctypes.c_double), ("range", ctypes.c_double),
+                ("variance", ctypes.c_double), ("aniso_ratio", ctypes.c_double),
+                ("aniso_angle", ctypes.c_double)]
+
+
 class _Streams(ctypes.Structure):
     _fields_ = [("cur", ctypes.c_void_p), ("start", ctypes.c_void_p), ("sub", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("stride", ctypes.c_uint64)]
@@ -151,6 +158,17 @@ def _load():
         "mrg_server_inflight": ([vp], u64),
         "mrg_server_restart": ([vp], i32),
         "mrg_server_destroy": ([vp], i32),
+        "mrg_grf_matern_scratch_bytes": ([ctypes.c_uint32] * 3, u64),
+        "mrg_grf_matern_raster": ([ctypes.POINTER(MaternParams), ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint32, ctypes.c_double, vp, u64, vp, u64, vp], i32),
+        "mrg_grf_matern_points": ([ctypes.POINTER(MaternParams), ctypes.c_uint32, vp, u64, vp, u64,
+                                   vp, u64, vp], i32),
+        "mrg_grf_ldl_workspace_bytes": ([u64, ctypes.c_uint32], u64),
+        "mrg_grf_ldl": ([vp, u64, u64, ctypes.c_uint32, vp, vp, u64,
+                         ctypes.POINTER(ctypes.c_int32), vp], i32),
+        "mrg_grf_simulate_scratch_bytes": ([u64, ctypes.c_uint32, ctypes.c_uint32], u64),
+        "mrg_grf_simulate": ([vp, vp, u64, u64, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp, u64,
+                              vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
