@@ -412,6 +412,99 @@ def run_serving(mrg, W, dev, seed, seconds=10.0, arena_gb=40):
                           "speedup": plain_sat_s / sat_s}}
 
 
+def grf_tensor_flops(n: int, batch: int, nb: int = 128, bm: int = 128, bn: int = 64,
+                     slices: int = 8) -> float:
+    """bf16 tensor-core FLOPs the factorisation issues: per 128-column panel
+    step, the panel product (tiles of 128 x 64) and the lower-triangle tiles
+    of the trailing product, each tile slices (slices + 1) / 2 digit products
+    of bm x bn x nb multiply-adds."""
+    per_tile = slices * (slices + 1) // 2 * 2.0 * bm * bn * nb
+    tiles = 0
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        nt = n - k0 - kb
+        if nt <= 0:
+            break
+        T = -(-nt // bm)
+        tiles += T * (-(-kb // bn))                     # panel
+        tiles += T * (T - 1) + (-(-nt // bn))           # trailing, lower tiles
+    return per_tile * tiles * batch
+
+
+def run_grf(dev, stream, peaks, steps=3):
+    """Gaussian random fields on the paper's example (Sec. 5): the 62 x 90
+    raster of 4 km cells, the four printed parameter sets, two simulations
+    each -- covariance, LDL^T and U = L D^(1/2) Z, with Z from the
+    generator's normals."""
+    import torch
+    from paper_2201_06604_gb300 import grf as R, mrg
+    from paper_2201_06604_gb300 import workloads as W
+    P = np.array(W.GRF_PARAMS)
+    nrow, ncol = W.GRF_GRID
+    cell = W.GRF_CELL
+    n, batch, nsim = nrow * ncol, len(P), W.GRF_NSIM
+    cov = torch.empty((batch, n, n), dtype=torch.float64, device=dev)
+    d = torch.empty((batch, n), dtype=torch.float64, device=dev)
+    ws = R.ldl_workspace(n, batch, dev)
+    s = mrg.create_streams(batch * nsim, device=dev, seed=(12345,) * 6)
+    z = torch.empty((batch, nsim, n), dtype=torch.float64, device=dev)
+    u = torch.empty_like(z)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def one():
+        e = [ev() for _ in range(5)]
+        e[0].record(stream)
+        R.matern_raster(P, nrow, ncol, cell, out=cov)
+        e[1].record(stream)
+        R.ldl(cov, d, ws, check=False)
+        e[2].record(stream)
+        mrg.generate(s, n, "normal", torch.float64, out=z.view(batch * nsim, n))
+        e[3].record(stream)
+        R.simulate(cov, d, z, out=u)
+        e[4].record(stream)
+        torch.cuda.synchronize()
+        return [e[i].elapsed_time(e[i + 1]) for i in range(4)]
+    one()
+    _, _, info = R.ldl(R.matern_raster(P, nrow, ncol, cell, out=cov), d, ws, check=True)
+    t = np.array([one() for _ in range(steps)]).mean(axis=0)
+    # each parameter set alone (batch of one)
+    alone = []
+    for b in range(batch):
+        c1 = cov[b:b + 1]
+        R.matern_raster(P[b:b + 1], nrow, ncol, cell, out=c1)
+        R.ldl(c1, d[b:b + 1], ws, check=False)
+        torch.cuda.synchronize()
+        R.matern_raster(P[b:b + 1], nrow, ncol, cell, out=c1)
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        R.ldl(c1, d[b:b + 1], ws, check=False)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        alone.append(a0.elapsed_time(a1))
+    tf = grf_tensor_flops(n, batch)
+    fp64_flops = batch * n ** 3 / 3.0
+    bf16 = float(peaks.get("bf16_tflops", 1887.0))
+    bf16_s = float(peaks.get("bf16_tflops_sustained", bf16))
+    ldl_s = t[1] / 1e3
+    del cov, d, ws, s, z, u
+    torch.cuda.empty_cache()
+    return {"workload": f"62 x 90 raster of 4 km cells (n = {n}), the paper's {batch} Matern "
+                        f"parameter sets, {nsim} simulations each",
+            "covariance_ms": t[0], "ldl_ms": t[1], "normals_ms": t[2], "simulate_ms": t[3],
+            "total_ms": float(t.sum()), "ldl_ms_per_parameter_set_alone": alone,
+            "info": info,
+            "ldl_tensor_tflops": tf / ldl_s / 1e12,
+            "ldl_tensor_frac_of_bf16_burst": tf / ldl_s / 1e12 / bf16,
+            "ldl_tensor_frac_of_bf16_sustained": tf / ldl_s / 1e12 / bf16_s,
+            "ldl_tensor_flops": tf,
+            "ldl_fp64_equivalent_tflops": fp64_flops / ldl_s / 1e12,
+            "method": "blocked LDL^T, 128-column panels; panel and trailing products as 8-slice "
+                      "bf16 Ozaki splits on tcgen05 (36 digit products per K = 128 block); "
+                      "diagonal blocks in double-float"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -643,6 +736,11 @@ def run_gpu(args):
                                 "gbs": total_out * ES[dt] / (t / 1e3) / 1e9}
         del s31
 
+    # Gaussian random fields (Sec. 5, Algorithm 2) on the paper's example
+    grf_res = None
+    if not args.skip_grf:
+        grf_res = run_grf(dev, stream, load_peaks()[0])
+
     # batched uneven requests vs back-to-back plain launches at identical output
     batched = None
     if not args.skip_batched:
@@ -661,6 +759,16 @@ def run_gpu(args):
         cpu = {"value": v, "unit": "draws/s", "cores": cores, "kind": "oracle",
                "sample": f"16384 of 65536 streams x 16384 draws x 5 variants ({tot} draws) in "
                          f"{sec:.2f} s, OpenMP over streams"}
+        if grf_res is not None:
+            from oracle import grf as OG
+            pts = OG.square_grid(*W.GRF_GRID, W.GRF_CELL)
+            sig = OG.matern_cov(pts, W.GRF_PARAMS[0])
+            t0 = time.perf_counter()
+            OG.ldl(sig)
+            gsec = time.perf_counter() - t0
+            cpu["grf_ldl_ms_per_matrix"] = gsec * 1e3
+            cpu["grf_sample"] = (f"oracle LDL^T (numpy Cholesky) of one 5580 x 5580 covariance matrix "
+                                 f"in {gsec:.2f} s")
         if fisher is not None:
             month = load_table("fisher_month.txt")
             ost, _ = oracle.create_streams(tuple(W.PAPER_SEED), 4096)
@@ -690,6 +798,7 @@ def run_gpu(args):
         "fused": fused,
         "mrg31k3p": g31,
         "fisher": fisher,
+        "grf": grf_res,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
@@ -713,6 +822,7 @@ def main():
     ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-mrg31k3p", action="store_true")
+    ap.add_argument("--skip-grf", action="store_true")
     ap.add_argument("--skip-fisher", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)

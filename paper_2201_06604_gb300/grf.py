@@ -11,16 +11,9 @@ import numpy as np
 import torch
 
 from . import mrg
+from .workloads import GRF_CELL, GRF_GRID, GRF_NSIM, GRF_PARAMS  # noqa: F401 (re-exported)
 from .mrg import MaternParams, _check, _stream_handle, lib
 
-# The paper's four parameter sets (Sec. 5, step 2): shape, range [m],
-# variance, anisoRatio, anisoAngleRadians.
-PAPER_PARAMS = ((1.25, 50e3, 1.5, 1.0, 0.0),
-                (2.15, 60e3, 2.0, 4.0, np.pi / 7),
-                (0.60, 30e3, 2.0, 2.0, np.pi / 5),
-                (3.00, 30e3, 2.0, 2.0, np.pi / 7))
-# The paper's raster: 62 rows x 90 columns.
-PAPER_GRID = (62, 90)
 
 
 def _params(params):

@@ -19,6 +19,17 @@ MATERIALISED_VARIANTS = (("uniform", "f64"), ("uniform", "f32"), ("normal", "f64
                          ("normal", "f32"), ("exponential", "f32"))
 # Fused consumer: 2^20 streams x 4096 draws.
 FUSED = dict(streams=1 << 20, draws=4096)
+# Gaussian random fields (Sec. 5): the paper's four Matern parameter sets
+# (shape, range [m], variance, anisoRatio, anisoAngleRadians), its 62 x 90
+# raster (the swissRain extent is not available: 4 km square cells stand in
+# for it) and two simulations per parameter set.
+GRF_PARAMS = ((1.25, 50e3, 1.5, 1.0, 0.0),
+              (2.15, 60e3, 2.0, 4.0, np.pi / 7),
+              (0.60, 30e3, 2.0, 2.0, np.pi / 5),
+              (3.00, 30e3, 2.0, 2.0, np.pi / 7))
+GRF_GRID = (62, 90)
+GRF_CELL = 4000.0
+GRF_NSIM = 2
 
 
 def random_states(n: int, seed: int = 0) -> np.ndarray:
