@@ -265,8 +265,9 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     gp.n = kb;
     gp.tiles_n = (kb + BN - 1) / BN;
     gp.status = status;
+    gp.vec32 = reinterpret_cast<uintptr_t>(a) % 32 == 0 && lda % 4 == 0;
     const dim3 pgrid((unsigned)((nt + BM - 1) / BM * gp.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, false><<<pgrid, 128, GemmSmem<kSlices>::TOTAL, st>>>(gp);
+    ozaki_gemm_kernel<kSlices, false><<<pgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, st>>>(gp);
     if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (panel)"))) return rc;
     // trailing operands: L_ik (A role) and W = L_ik D_k (B role)
     sa.img_b = reinterpret_cast<uint8_t*>(base + L.img_w);
@@ -285,7 +286,7 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     gt.tiles_n = (uint32_t)((nt + BN - 1) / BN);
     const uint64_t T = (nt + BM - 1) / BM;
     const dim3 tgrid((unsigned)(T * (T - 1) + gt.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, true><<<tgrid, 128, GemmSmem<kSlices>::TOTAL, st>>>(gt);
+    ozaki_gemm_kernel<kSlices, true><<<tgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, st>>>(gt);
     if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (trailing)"))) return rc;
   }
   equil_apply_kernel<<<agrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, -1);

@@ -273,6 +273,7 @@ struct GemmArgs {
   uint64_t ldc, c_mstride;
   uint32_t m, n;           // output rows and columns
   uint32_t tiles_n;        // PANEL: column tiles per row of tiles
+  int vec32;               // c and ldc * 8 are multiples of 32 bytes (vector row access)
   int* status;
 };
 
@@ -325,8 +326,22 @@ __device__ __forceinline__ double scaled_i128_to_f64(uint64_t hi, uint64_t lo, i
   return __longlong_as_double((long long)(bits | sgn));
 }
 
+// 32-byte global accesses of four doubles (address 32-byte aligned).
+__device__ __forceinline__ void ld_v4f64(const double* p, double* v) {
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p));
+}
+__device__ __forceinline__ void st_v4f64(double* p, const double* v) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+               "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+
+constexpr int GEMM_THREADS = 256;   // warp 0 lane 0 issues copies and MMAs; all 8 warps drain TMEM
+
 template <int S, bool TRAIL>
-__global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g) {
   using SM = GemmSmem<S>;
   constexpr int NST = SM::NST;
   extern __shared__ uint8_t smem_raw[];
@@ -424,50 +439,71 @@ __global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs g) {
   if (!fin && threadIdx.x == 0) atomicOr(g.status, ERR_TIMEOUT);
   if (fin && *abort_flag == 0) {
     tc::tc_fence_after();
-    const uint32_t r = (uint32_t)(warp * 32 + lane);
+    // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and the half
+    // w div 4 of the tile's 64 columns
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t r = (uint32_t)(quarter * 32 + lane);
     const uint32_t row = row0 + r;
     const bool row_ok = row < g.m;
     const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
     double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
-    // sum_l acc_l 128^(S-1-l) with acc_l read as (bits of acc_l + 1.5 2^23)
-    // - 0x4B400000, the constant part subtracted once
-    uint64_t magic_lo = 0, magic_hi = 0;
-#pragma unroll
-    for (int l = 0; l < S; ++l) {
-      magic_hi = (magic_hi << 7) | (magic_lo >> 57);
-      magic_lo = (magic_lo << 7) + 0x4B400000u;
-      magic_hi += magic_lo < 0x4B400000u;
-    }
-    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+    const int32_t* eb_row = g.exp_b + b * g.exp_b_mstride;
+    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t cbeg = (uint32_t)half * (BN / 2);
+    // whole 8-column chunks inside the output and a 32-byte aligned row: two
+    // 32-byte accesses per chunk, else element by element
+    const bool vec = g.vec32 != 0;
 #pragma unroll 1
-    for (uint32_t c0 = 0; c0 < BN; c0 += 8) {
+    for (uint32_t c0 = cbeg; c0 < cbeg + BN / 2; c0 += 8) {
+      const uint32_t colc = col0 + c0;
+      const bool full = row_ok && colc + 8 <= g.n;
+      double cv[8];
+      if (TRAIL && full && vec) {
+        ld_v4f64(crow + colc, cv);
+        ld_v4f64(crow + colc + 4, cv + 4);
+      }
       float acc[S][8];
 #pragma unroll
       for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
       tc::tmem_ld_wait();
-      if (!row_ok) continue;
+      if (!row_ok || colc >= g.n) continue;
+      double v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const uint32_t col = col0 + c0 + e;
-        if (col >= g.n) break;
-        // T = sum_l acc_l 128^(S-1-l) needs up to 7 S + 13 bits: two words,
-        // hi:lo, a Horner step shifting both by 7 and adding the level's
-        // offset integer into lo with its carry
-        uint64_t lo = 0, hi = 0;
+        // T = sum_l acc_l 128^(S-1-l) (up to 7 S + 13 bits) as
+        // T_hi 128^(S-H) + T_lo, each half an exact int64 Horner sum of
+        // the level integers (acc + 1.5 2^23 read as bits, minus the bits
+        // of 1.5 2^23), then one 128-bit add
+        constexpr int H = S / 2;
+        int64_t th = 0, tl = 0;
 #pragma unroll
-        for (int l = 0; l < S; ++l) {
-          hi = (hi << 7) | (lo >> 57);
-          lo <<= 7;
-          const uint64_t add = __float_as_uint(acc[l][e] + 12582912.0f);
-          lo += add;
-          hi += lo < add;
+        for (int l = 0; l < H; ++l)
+          th = th * 128 + (int32_t)(__float_as_uint(acc[l][e] + 12582912.0f) - 0x4B400000u);
+#pragma unroll
+        for (int l = H; l < S; ++l)
+          tl = tl * 128 + (int32_t)(__float_as_uint(acc[l][e] + 12582912.0f) - 0x4B400000u);
+        uint64_t hi = (uint64_t)(th >> (64 - 7 * (S - H)));
+        uint64_t lo = (uint64_t)th << (7 * (S - H));
+        const uint64_t lo2 = lo + (uint64_t)tl;
+        hi += (uint64_t)(tl >> 63) + (lo2 < lo);
+        lo = lo2;
+        const uint32_t col = colc + e;
+        const int eb = col < g.n ? eb_row[col] : 0;
+        v[e] = scaled_i128_to_f64(hi, lo, ea + eb - 7 * (S + 1));
+      }
+      if (full && vec) {
+        if (TRAIL) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = cv[e] - v[e];
         }
-        hi -= magic_hi + (lo < magic_lo);
-        lo -= magic_lo;
-        const int eb = g.exp_b[b * g.exp_b_mstride + col];
-        const double v = scaled_i128_to_f64(hi, lo, ea + eb - 7 * (S + 1));
-        if (TRAIL) crow[col] = crow[col] - v;
-        else crow[col] = v;
+        st_v4f64(crow + colc, v);
+        st_v4f64(crow + colc + 4, v + 4);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t col = colc + e;
+          if (col < g.n) crow[col] = TRAIL ? crow[col] - v[e] : v[e];
+        }
       }
     }
   }
@@ -501,11 +537,34 @@ struct DiagArgs {
   int* info;               // per matrix: 0, or 1 + the first non-positive pivot's index
 };
 
-__device__ __forceinline__ df df_of(double x) {
-  const float hi = __double2float_rn(x);
-  return df{hi, __double2float_rn(x - (double)hi)};
+// x 2^-sc as a double-float, in integers (no FP64 instruction): hi = x
+// rounded to fp32 at bit 29 of the significand, lo = the remainder (up to 29
+// bits, rounded to fp32).  Requires x 2^-sc zero or within fp32's normal range.
+__device__ __forceinline__ df df_of_scaled(double x, int sc) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  if (e == 0) return df{0.0f, 0.0f};
+  const uint32_t sgn = (uint32_t)(bits >> 32) & 0x80000000u;
+  const uint64_t m = bits & 0xFFFFFFFFFFFFFull;
+  const uint64_t mh = (m + 0x0FFFFFFFull + ((m >> 29) & 1)) >> 29;   // 23 bits (+ a carry)
+  const int ef = e - sc - 1023 + 127;                                 // biased fp32 exponent
+  if (ef <= 0) return df{0.0f, 0.0f};                                 // below 2^-126: flushed
+  if (ef >= 255) return df{__uint_as_float(sgn | 0x7F800000u), 0.0f};  // beyond fp32: inf
+  const float hi = __uint_as_float(sgn | (((uint32_t)ef << 23) + (uint32_t)mh));
+  const int64_t r = (int64_t)m - (int64_t)(mh << 29);                 // |r| <= 2^28
+  // lo = r 2^(e - sc - 1023 - 52); its scale as a float while that is normal
+  if (ef <= 52) return df{hi, 0.0f};
+  const float lo = __fmul_rn(__ll2float_rn(sgn ? -r : r), __uint_as_float((uint32_t)(ef - 52) << 23));
+  return df{hi, lo};
 }
-__device__ __forceinline__ double f64_of(df v) { return (double)v.hi + (double)v.lo; }
+
+// A normalised double-float times 2^sc as a double (integer conversion of
+// the pair, then the exponent moved; zero stays zero).
+__device__ __forceinline__ double f64_of_scaled(df v, int sc) {
+  uint64_t bits = df_to_f64_bits(v);
+  if ((bits & 0x7FFFFFFFFFFFFFFFull) != 0) bits += (uint64_t)(int64_t)sc << 52;
+  return __longlong_as_double((long long)bits);
+}
 
 // a - b c in double-float
 __device__ __forceinline__ df df_fnms(df a, df b, df c) {
@@ -517,15 +576,40 @@ __device__ __forceinline__ df df_fnms(df a, df b, df c) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, e)));
 }
 
+// 1 / d in double-float: fp32 reciprocal and one Newton step whose residual
+// 1 - d r0 is formed exactly (the product's error by FMA; 1 - p is exact).
+__device__ __forceinline__ df df_recip(df d) {
+  const float r0 = __frcp_rn(d.hi);
+  const float p = __fmul_rn(d.hi, r0);
+  const float pe = __fmaf_rn(d.hi, r0, -p);
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(d.lo, r0));
+  return fast_two_sum(r0, __fmul_rn(r0, e));
+}
+
+constexpr int NPAIR = NB * (NB - 1) / 2;   // pairs (i, l), 1 <= l <= i < 128
+
+// Right-looking LDL^T and, in the same sweep, the inverse X = L^-1: after
+// column j of L is known (step j), every thread takes its share of one flat
+// index space covering
+//   * the trailing update a_il -= l_ij w_l (j < l <= i < kb, w = column j
+//     before scaling), from a table of (i, l) pairs ordered by column l
+//     descending, so that the pairs of step j are a prefix of it, and
+//   * the inverse's step, X[i][c] -= l_ij X[j][c] (j < i < kb, c <= j,
+//     X[j][j] = 1: a column-oriented forward substitution, backward stable
+//     per column), X[i][c] kept at sm[c][i] above the diagonal;
+// so every lane works on every step and a step costs two barriers.
 template <int S>
 __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
   extern __shared__ df sm[];               // [NB][DG]: L below the diagonal, X^T above
-  __shared__ df s_w[NB];
-  __shared__ double s_r[NB];               // 1 / d_j of the scaled block
-  __shared__ double s_d[NB];
+  __shared__ df s_w[NB];                   // column j before scaling
+  __shared__ df s_l[NB];                   // column j of L
+  __shared__ df s_d[NB];                   // the pivots (scaled block)
+  __shared__ df s_rcp[NB];                 // their reciprocals
+  __shared__ uint16_t s_pair[NPAIR];       // (i << 8) | l
   __shared__ int s_scale, s_bad;
   const uint32_t b = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NT = 512;
   const int kb = (int)g.kb;
   double* A = g.a + b * g.a_mstride + (uint64_t)g.k0 * g.lda + g.k0;
   if (warp == 0) {
@@ -537,76 +621,76 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
       s_bad = 0;
     }
   }
+  // pair table: column l (1 <= l < kb) holds rows l .. kb-1 at offset
+  // (kb-1-l)(kb-l)/2
+  for (int l = tid + 1; l < kb; l += NT) {
+    const int off = (kb - 1 - l) * (kb - l) / 2;
+    for (int i = l; i < kb; ++i) s_pair[off + i - l] = (uint16_t)((i << 8) | l);
+  }
   __syncthreads();
   const int sc = s_scale;
-  const double down = scalbn(1.0, -sc), up = scalbn(1.0, sc);
-  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+  for (int idx = tid; idx < kb * kb; idx += NT) {
     const int i = idx / kb, j = idx - (idx / kb) * kb;
-    sm[i * DG + j] = j <= i ? df_of(A[(uint64_t)i * g.lda + j] * down) : df{0.0f, 0.0f};
+    sm[i * DG + j] = j <= i ? df_of_scaled(A[(uint64_t)i * g.lda + j], sc) : df{0.0f, 0.0f};
   }
   __syncthreads();
-  // right-looking LDL^T
   for (int j = 0; j < kb; ++j) {
+    // pivot and column j of L: every thread forms 1 / d_j itself
+    const df dj = sm[j * DG + j];
+    const bool pos = dj.hi > 0x1p-100f;
+    const df rj = pos ? df_recip(dj) : df{0.0f, 0.0f};
     if (tid == 0) {
-      const double dj = f64_of(sm[j * DG + j]);
-      if (!(dj > 0x1p-100)) {
-        if (!s_bad) s_bad = 1 + j;
-        s_r[j] = 0.0;
-      } else {
-        s_r[j] = 1.0 / dj;
-      }
       s_d[j] = dj;
+      s_rcp[j] = rj;
+      if (!pos && !s_bad) s_bad = 1 + j;
     }
-    __syncthreads();
-    const df rj = df_of(s_r[j]);
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) {
+    for (int i = j + 1 + tid; i < kb; i += NT) {
       const df w = sm[i * DG + j];
+      const df l = df_mul(w, rj);
       s_w[i] = w;
-      sm[i * DG + j] = df_mul(w, rj);
+      s_l[i] = l;
+      sm[i * DG + j] = l;
     }
     __syncthreads();
-    for (int i = j + 1 + warp; i < kb; i += 16) {
-      const df lij = sm[i * DG + j];
-      for (int l = j + 1 + lane; l <= i; l += 32) sm[i * DG + l] = df_fnms(sm[i * DG + l], lij, s_w[l]);
-    }
-    __syncthreads();
-  }
-  // X = L^-1 (unit lower), column-oriented forward substitution in outer-
-  // product order; X[i][c] (i > c) is kept at sm[c][i]
-  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-    const int c = idx / kb, i = idx - (idx / kb) * kb;
-    if (i > c) sm[c * DG + i] = df{0.0f, 0.0f};
-  }
-  __syncthreads();
-  for (int m = 0; m < kb; ++m) {
-    for (int i = m + 1 + warp; i < kb; i += 16) {
-      const df lim = sm[i * DG + m];
-      for (int c = lane; c <= m; c += 32) {
-        const df xmc = c == m ? df{1.0f, 0.0f} : sm[c * DG + m];
-        sm[c * DG + i] = df_fnms(sm[c * DG + i], lim, xmc);
+    const int np = (kb - 1 - j) * (kb - j) / 2;    // trailing pairs of step j
+    const int nc = j + 1;                          // inverse: columns 0 .. j
+    const int nx = (kb - 1 - j) * nc;              // inverse: (rows j+1 .. kb-1) x columns
+    const float inv_nc = 1.0f / (float)nc;
+    for (int t = tid; t < np + nx; t += NT) {
+      if (t < np) {
+        const int pr = s_pair[t];
+        const int i = pr >> 8, l = pr & 255;
+        sm[i * DG + l] = df_fnms(sm[i * DG + l], s_l[i], s_w[l]);
+      } else {
+        const int u = t - np;
+        // u = (i - j - 1) nc + c; exact: (u + 1/2) / nc stays >= 1/256 from an integer
+        const int q = __float2int_rz(((float)u + 0.5f) * inv_nc);
+        const int c = u - q * nc, i = j + 1 + q;
+        const df xjc = c == j ? df{1.0f, 0.0f} : sm[c * DG + j];
+        sm[c * DG + i] = df_fnms(sm[c * DG + i], s_l[i], xjc);
       }
     }
     __syncthreads();
   }
-  // outputs: L and D into the matrix, D into d[]
-  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+  // outputs: L (strict lower part) and D into the matrix, D into d[]
+  for (int idx = tid; idx < kb * kb; idx += NT) {
     const int i = idx / kb, j = idx - (idx / kb) * kb;
-    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of(sm[i * DG + j]);
-    else if (j == i) A[(uint64_t)i * g.lda + j] = s_d[i] * up;
+    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(sm[i * DG + j], 0);
+    else if (j == i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(s_d[i], sc);
   }
-  for (int j = tid; j < kb; j += blockDim.x) g.d[b * g.d_mstride + g.k0 + j] = s_d[j] * up;
+  for (int j = tid; j < kb; j += NT) g.d[b * g.d_mstride + g.k0 + j] = f64_of_scaled(s_d[j], sc);
   if (tid == 0 && s_bad) atomicCAS(&g.info[b], 0, (int)g.k0 + s_bad);
   // B-role operand of the panel product: row n = X[n][:] / d_n, unscaled
   uint8_t* img = g.img_x + b * g.img_x_mstride;
-  for (int n = warp; n < NB; n += 16) {
+  for (int n = warp; n < NB; n += NT / 32) {
     double v[4];
-    const double rn = n < kb ? s_r[n] * down : 0.0;
+    const df rn = n < kb ? s_rcp[n] : df{0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = 4 * lane + i;
-      double x = 0.0;
-      if (n < kb && k < kb) x = k == n ? 1.0 : (k < n ? f64_of(sm[k * DG + n]) : 0.0);
-      v[i] = x * rn;
+      df x = df{0.0f, 0.0f};
+      if (n < kb && k < kb) x = k == n ? rn : (k < n ? df_mul(sm[k * DG + n], rn) : df{0.0f, 0.0f});
+      v[i] = f64_of_scaled(x, -sc);
     }
     slice_row<S>(v, img + (uint64_t)(n / RB_B) * S * SLICE_B, RB_B, n % RB_B,
                  g.exp_x + b * g.exp_x_mstride + n);
