@@ -24,23 +24,66 @@ struct ParamBlock {
 
 uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
-// Per-matrix workspace layout of the factorisation (bytes, 1024-aligned parts).
+// Per-matrix workspace layout of the factorisation (bytes, 1024-aligned
+// parts).  The operand images of the panel and trailing products exist twice:
+// step k writes set k mod 2 while the bulk of step k - 1's trailing update
+// still reads the other.
 struct LdlLayout {
-  uint64_t img_a, img_w, img_x, exp_a, exp_w, exp_x, exp_eq, per_matrix, common;
+  uint64_t img_a[2], img_w[2], img_x, exp_a[2], exp_w[2], exp_x, exp_eq, per_matrix, common;
   explicit LdlLayout(uint64_t n) {
     const uint64_t ta = (n + RB_A - 1) / RB_A;
-    img_a = 0;
-    img_w = img_a + ta * kSlices * SLICE_A;
-    img_x = img_w + 2 * ta * kSlices * SLICE_B;
-    exp_a = img_x + 2 * kSlices * SLICE_B;
-    exp_w = exp_a + align_up(ta * RB_A * 4, 1024);
-    exp_x = exp_w + align_up(ta * RB_A * 4, 1024);
+    uint64_t o = 0;
+    for (int q = 0; q < 2; ++q) {
+      img_a[q] = o;
+      o += ta * kSlices * SLICE_A;
+      img_w[q] = o;
+      o += 2 * ta * kSlices * SLICE_B;
+    }
+    img_x = o;
+    o += 2 * kSlices * SLICE_B;
+    for (int q = 0; q < 2; ++q) {
+      exp_a[q] = o;
+      o += align_up(ta * RB_A * 4, 1024);
+      exp_w[q] = o;
+      o += align_up(ta * RB_A * 4, 1024);
+    }
+    exp_x = o;
     exp_eq = exp_x + 1024;
     per_matrix = exp_eq + align_up(n * 4, 1024);
     common = 2048;   // status word, per-matrix info and equilibration flags (<= 255 matrices)
   }
   uint64_t bytes(uint32_t batch) const { return common + per_matrix * batch; }
 };
+
+// The factorisation's two streams on the current device, created once: a
+// high-priority one for the critical chain (diagonal block, slicing, panel,
+// the next panel's trailing tiles) and one for the bulk of each trailing
+// update, with the events that order them.
+struct LdlStreams {
+  cudaStream_t chain = nullptr, bulk = nullptr;
+  cudaEvent_t ops = nullptr, rest = nullptr, fork = nullptr, join = nullptr;
+};
+
+int ldl_streams(LdlStreams** out) {
+  static std::mutex mu;
+  static LdlStreams per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return mrg::set_error(MRG_ECUDA, "cudaGetDevice failed");
+  std::lock_guard<std::mutex> lk(mu);
+  LdlStreams& S = per_dev[dev];
+  if (!S.chain) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S.chain, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S.bulk, cudaStreamNonBlocking, least);
+    for (cudaEvent_t* ev : {&S.ops, &S.rest, &S.fork, &S.join})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "creating the factorisation's streams");
+  }
+  *out = &S;
+  return MRG_OK;
+}
 
 int set_attrs_once() {
   static std::mutex mu;
@@ -195,20 +238,35 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
   int* status = reinterpret_cast<int*>(ws);
   int* dinfo = status + 1;
   int* nonuniform = status + 256;
-  cudaError_t e = cudaMemsetAsync(ws, 0, L.common, st);
-  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "clearing the status words");
+  LdlStreams* SS = nullptr;
+  if ((rc = ldl_streams(&SS))) return rc;
+  // the streams and events are shared by every call on this device: calls
+  // are serialised on the host, so that no call records an event again
+  // before another call's waits on it are enqueued
+  static std::mutex call_mu;
+  std::lock_guard<std::mutex> call_lk(call_mu);
+  cudaStream_t hi = SS->chain, lo = SS->bulk;
+  cudaError_t e = cudaEventRecord(SS->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, SS->fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(lo, SS->fork, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, L.common, hi);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "starting the factorisation");
   char* base = ws + L.common;
   const uint64_t pm = L.per_matrix;
   const uint64_t a_ms = n * lda;
   int32_t* eq = reinterpret_cast<int32_t*>(base + L.exp_eq);
   const dim3 egrid((unsigned)((n + 255) / 256), batch);
-  equil_exps_kernel<<<egrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform);
+  equil_exps_kernel<<<egrid, 256, 0, hi>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform);
   if ((rc = after(cudaSuccess, "equil_exps_kernel"))) return rc;
   const dim3 agrid((unsigned)std::min<uint64_t>((n * (n + 1) / 2 + 255) / 256,
                                                 (uint64_t)mrg::sm_count() * 16), batch);
-  equil_apply_kernel<<<agrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, 1);
+  equil_apply_kernel<<<agrid, 256, 0, hi>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, 1);
   if ((rc = after(cudaSuccess, "equil_apply_kernel (scale)"))) return rc;
-  for (uint64_t k0 = 0; k0 < n; k0 += NB) {
+  const int vec32 = reinterpret_cast<uintptr_t>(a) % 32 == 0 && lda % 4 == 0;
+  bool rest_pending = false;   // a bulk trailing update is in flight on `lo`
+  int k = 0;
+  for (uint64_t k0 = 0; k0 < n; k0 += NB, ++k) {
+    const int q = k & 1;
     const uint32_t kb = (uint32_t)std::min<uint64_t>(NB, n - k0);
     const uint64_t t0 = k0 + kb, nt = n - t0;
     DiagArgs dg;
@@ -224,7 +282,7 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     dg.img_x_mstride = pm;
     dg.exp_x_mstride = pm / 4;
     dg.info = dinfo;
-    ldl_diag_kernel<kSlices><<<batch, 512, NB * DG * sizeof(mrg::df), st>>>(dg);
+    ldl_diag_kernel<kSlices><<<batch, 512, NB * DG * sizeof(mrg::df), hi>>>(dg);
     if ((rc = after(cudaSuccess, "ldl_diag_kernel"))) return rc;
     if (nt == 0) break;
     const uint32_t rows_pad = (uint32_t)align_up(nt, RB_A);
@@ -236,8 +294,8 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     sa.rows = (uint32_t)nt;
     sa.rows_pad = rows_pad;
     sa.kb = kb;
-    sa.img_a = reinterpret_cast<uint8_t*>(base + L.img_a);
-    sa.exp_a = reinterpret_cast<int32_t*>(base + L.exp_a);
+    sa.img_a = reinterpret_cast<uint8_t*>(base + L.img_a[q]);
+    sa.exp_a = reinterpret_cast<int32_t*>(base + L.exp_a[q]);
     sa.img_a_mstride = pm;
     sa.exp_a_mstride = pm / 4;
     sa.img_b = nullptr;
@@ -246,7 +304,7 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     sa.colscale = nullptr;
     sa.colscale_mstride = 0;
     const dim3 sgrid(rows_pad / 8, batch);
-    slice_kernel<kSlices><<<sgrid, 256, 0, st>>>(sa);
+    slice_kernel<kSlices><<<sgrid, 256, 0, hi>>>(sa);
     if ((rc = after(cudaSuccess, "slice_kernel (panel)"))) return rc;
     // L_ik = A_ik X^T, written over A_ik
     GemmArgs gp;
@@ -264,33 +322,63 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     gp.m = (uint32_t)nt;
     gp.n = kb;
     gp.tiles_n = (kb + BN - 1) / BN;
+    gp.tile_set = TILES_LOWER;
+    gp.vec32 = vec32;
     gp.status = status;
-    gp.vec32 = reinterpret_cast<uintptr_t>(a) % 32 == 0 && lda % 4 == 0;
     const dim3 pgrid((unsigned)((nt + BM - 1) / BM * gp.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, false><<<pgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, st>>>(gp);
+    ozaki_gemm_kernel<kSlices, false><<<pgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gp);
     if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (panel)"))) return rc;
     // trailing operands: L_ik (A role) and W = L_ik D_k (B role)
-    sa.img_b = reinterpret_cast<uint8_t*>(base + L.img_w);
-    sa.exp_b = reinterpret_cast<int32_t*>(base + L.exp_w);
+    sa.img_b = reinterpret_cast<uint8_t*>(base + L.img_w[q]);
+    sa.exp_b = reinterpret_cast<int32_t*>(base + L.exp_w[q]);
     sa.img_b_mstride = pm;
     sa.exp_b_mstride = pm / 4;
     sa.colscale = d + k0;
     sa.colscale_mstride = n;
-    slice_kernel<kSlices><<<sgrid, 256, 0, st>>>(sa);
+    slice_kernel<kSlices><<<sgrid, 256, 0, hi>>>(sa);
     if ((rc = after(cudaSuccess, "slice_kernel (trailing)"))) return rc;
+    // The trailing update A_ij -= L_i W_j^T.  Its two tile columns of the
+    // next panel are on the critical chain; they also update columns that
+    // the previous step's bulk update writes, so they wait for it.  The
+    // rest goes to the bulk stream and overlaps the next step's chain.
     GemmArgs gt = gp;
     gt.img_b = sa.img_b;
     gt.exp_b = sa.exp_b;
     gt.c = a + t0 * lda + t0;
     gt.n = (uint32_t)nt;
-    gt.tiles_n = (uint32_t)((nt + BN - 1) / BN);
-    const uint64_t T = (nt + BM - 1) / BM;
-    const dim3 tgrid((unsigned)(T * (T - 1) + gt.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, true><<<tgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, st>>>(gt);
-    if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (trailing)"))) return rc;
+    const uint64_t T = (nt + BM - 1) / BM, Tc = (nt + BN - 1) / BN;
+    if (rest_pending && (e = cudaStreamWaitEvent(hi, SS->rest, 0)) != cudaSuccess)
+      return mrg::set_error(MRG_ECUDA, "ordering the trailing updates");
+    gt.tile_set = TILES_NEXT;
+    gt.tiles_n = (uint32_t)std::min<uint64_t>(2, Tc);
+    const dim3 ngrid((unsigned)(T * gt.tiles_n), batch);
+    ozaki_gemm_kernel<kSlices, true><<<ngrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gt);
+    if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (next panel)"))) return rc;
+    rest_pending = false;
+    if (Tc > 2) {
+      if ((e = cudaEventRecord(SS->ops, hi)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(lo, SS->ops, 0)) != cudaSuccess)
+        return mrg::set_error(MRG_ECUDA, "handing the trailing update to the bulk stream");
+      gt.tile_set = TILES_REST;
+      gt.tiles_n = (uint32_t)Tc;
+      const dim3 rgrid((unsigned)((T - 2) * (T - 1) + (Tc - 2)), batch);
+      ozaki_gemm_kernel<kSlices, true><<<rgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, lo>>>(gt);
+      if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (trailing)"))) return rc;
+      if ((e = cudaEventRecord(SS->rest, lo)) != cudaSuccess)
+        return mrg::set_error(MRG_ECUDA, "recording the trailing update");
+      rest_pending = true;
+    }
   }
-  equil_apply_kernel<<<agrid, 256, 0, st>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, -1);
+  if (rest_pending && (e = cudaStreamWaitEvent(hi, SS->rest, 0)) != cudaSuccess)
+    return mrg::set_error(MRG_ECUDA, "joining the trailing updates");
+  equil_apply_kernel<<<agrid, 256, 0, hi>>>(a, lda, a_ms, n, eq, pm / 4, nonuniform, d, -1);
   if ((rc = after(cudaSuccess, "equil_apply_kernel (unscale)"))) return rc;
+  // the caller's stream continues once both streams are done
+  e = cudaEventRecord(SS->join, hi);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, SS->join, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(SS->join, lo);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, SS->join, 0);
+  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, "joining the factorisation's streams");
   if (info) {
     int32_t h[256];
     e = cudaMemcpyAsync(h, ws, 4 * (1 + batch), cudaMemcpyDeviceToHost, st);

@@ -272,10 +272,15 @@ struct GemmArgs {
   double* c;               // output element (r, col) at c + b c_mstride + r ldc + col
   uint64_t ldc, c_mstride;
   uint32_t m, n;           // output rows and columns
-  uint32_t tiles_n;        // PANEL: column tiles per row of tiles
+  uint32_t tiles_n;        // rectangle tile sets: column tiles per row of tiles
+  int tile_set;            // TRAIL: TILES_LOWER, TILES_NEXT (tj < 2) or TILES_REST (tj >= 2)
   int vec32;               // c and ldc * 8 are multiples of 32 bytes (vector row access)
   int* status;
 };
+
+// Tile sets of a trailing update: all lower tiles, the two tile columns of
+// the next panel (a rectangle: tiles_n = 2), or the lower tiles right of it.
+constexpr int TILES_LOWER = 0, TILES_NEXT = 1, TILES_REST = 2;
 
 template <int S>
 struct GemmSmem {
@@ -283,7 +288,8 @@ struct GemmSmem {
   static constexpr uint32_t B_BYTES = (uint32_t)S * SLICE_B;
   static constexpr uint32_t A_OFF = B_BYTES;
   static constexpr uint32_t BAR_OFF = A_OFF + NST * SLICE_A;
-  static constexpr uint32_t TOTAL = BAR_OFF + 128 + 1024;         // barriers + slot, alignment slack
+  static constexpr uint32_t EB_OFF = BAR_OFF + 128;                // exponents of the tile's B rows
+  static constexpr uint32_t TOTAL = EB_OFF + 256 + 1024;          // + alignment slack
 };
 
 // Tile (ti, tj) of the lower-triangular tile set of an m x m output with
@@ -299,29 +305,27 @@ __device__ __forceinline__ void lower_tile(uint32_t x, uint32_t& ti, uint32_t& t
 // 128-bit two's-complement value T = hi 2^64 + lo times 2^E, rounded to
 // nearest-even fp64 (0 for T = 0 and below the normal range).
 __device__ __forceinline__ double scaled_i128_to_f64(uint64_t hi, uint64_t lo, int E) {
-  if ((hi | lo) == 0) return 0.0;
   const uint64_t sgn = hi & 0x8000000000000000ull;
-  if (sgn) {                                  // magnitude: two's-complement negation
-    lo = ~lo + 1;
-    hi = ~hi + (lo == 0);
-  }
-  int lz;
-  uint64_t top, low;
-  if (hi) {
-    lz = __clzll((long long)hi);
-    top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
-    low = lo << lz;
-  } else {
-    lz = 64 + __clzll((long long)lo);
-    top = lo << (lz - 64);
-    low = 0;
-  }
-  const int eb = 127 - lz + E + 1023;         // biased exponent of the result
+  // magnitude (two's-complement negation when negative), without branches
+  const uint64_t flip = (uint64_t)((int64_t)hi >> 63);
+  lo ^= flip;
+  hi ^= flip;
+  const uint64_t lo1 = lo - flip;             // + 1 when negative
+  hi += (flip & (lo1 == 0));
+  lo = lo1;
+  const bool h = hi != 0;
+  const uint64_t w = h ? hi : lo;
+  if (w == 0) return 0.0;
+  const int lzw = __clzll((long long)w);
+  // the leading 64 bits and what lies below them
+  const uint64_t top = h ? (hi << lzw) | (lzw ? lo >> (64 - lzw) : 0) : lo << lzw;
+  const uint64_t low = h ? lo << lzw : 0;
+  const int eb = 127 - (h ? lzw : 64 + lzw) + E + 1023;   // biased exponent of the result
   if (eb <= 0) return 0.0;
   uint64_t mant = top >> 11;                  // 53 bits with the leading one
   const uint64_t rem = top & 0x7FF;
-  const bool above = rem > 0x400 || (rem == 0x400 && low != 0);
-  mant += above | ((rem == 0x400) & (low == 0) & (mant & 1));
+  const bool up = rem > 0x400 || (rem == 0x400 && (low != 0 || (mant & 1)));
+  mant += up;
   const uint64_t bits = ((uint64_t)(eb - 1) << 52) + mant;   // a rounding carry steps the exponent
   return __longlong_as_double((long long)(bits | sgn));
 }
@@ -338,7 +342,8 @@ __device__ __forceinline__ void st_v4f64(double* p, const double* v) {
                : "memory");
 }
 
-constexpr int GEMM_THREADS = 256;   // warp 0 lane 0 issues copies and MMAs; all 8 warps drain TMEM
+constexpr int GEMM_THREADS = 512;   // warp 0 lane 0 issues copies and MMAs; all 16 warps drain TMEM
+constexpr int EPI_COLS = BN * 4 / (GEMM_THREADS / 32);   // columns per thread in the epilogue (16)
 
 template <int S, bool TRAIL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g) {
@@ -358,9 +363,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 3 + 2 * NST);
 
   uint32_t ti, tj;
-  if (TRAIL) {
+  if (TRAIL && g.tile_set == TILES_REST) {
+    // lower tiles right of the next panel (tj >= 2): row ti >= 1 holds
+    // 2 ti of them, rows before it ti (ti - 1) in all
+    uint32_t t = (uint32_t)((1.0f + sqrtf(4.0f * (float)blockIdx.x + 1.0f)) * 0.5f);
+    while ((uint64_t)t * (t - 1) > blockIdx.x) --t;
+    while ((uint64_t)(t + 1) * t <= blockIdx.x) ++t;
+    ti = t;
+    tj = 2 + blockIdx.x - t * (t - 1);
+  } else if (TRAIL && g.tile_set == TILES_LOWER) {
     lower_tile(blockIdx.x, ti, tj);
-  } else {
+  } else {   // a rectangle of tiles_n columns of tiles (the panel; the next panel of a trailing update)
     ti = blockIdx.x / g.tiles_n;
     tj = blockIdx.x % g.tiles_n;
   }
@@ -384,6 +397,27 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tslot;
+
+  // Epilogue inputs, fetched while the MMAs run: warp w later drains TMEM
+  // lanes 32 (w mod 4) .. + 31 (its rows) and the part w div 4 of the tile's
+  // 64 columns, EPI_COLS columns per thread; the old C values of those
+  // (TRAIL, row in range, 32-byte aligned rows) go to registers now.
+  const int quarter = warp & 3, part = warp >> 2;
+  const uint32_t r = (uint32_t)(quarter * 32 + lane);
+  const uint32_t row = row0 + r;
+  const bool row_ok = row < g.m;
+  const uint32_t cbeg = col0 + (uint32_t)part * EPI_COLS;
+  double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
+  const bool vec = g.vec32 != 0 && row_ok && cbeg + EPI_COLS <= g.n;
+  double cv[EPI_COLS];
+  if (TRAIL && vec) {
+#pragma unroll
+    for (int k = 0; k < EPI_COLS; k += 4) ld_v4f64(crow + cbeg + k, cv + k);
+  }
+  int* s_eb = reinterpret_cast<int*>(smem + SM::EB_OFF);
+  if (threadIdx.x < BN)
+    s_eb[threadIdx.x] = col0 + threadIdx.x < g.n ? g.exp_b[b * g.exp_b_mstride + col0 + threadIdx.x] : 0;
+  const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -439,62 +473,47 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   if (!fin && threadIdx.x == 0) atomicOr(g.status, ERR_TIMEOUT);
   if (fin && *abort_flag == 0) {
     tc::tc_fence_after();
-    // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and the half
-    // w div 4 of the tile's 64 columns
-    const int quarter = warp & 3, half = warp >> 2;
-    const uint32_t r = (uint32_t)(quarter * 32 + lane);
-    const uint32_t row = row0 + r;
-    const bool row_ok = row < g.m;
-    const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
-    double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
-    const int32_t* eb_row = g.exp_b + b * g.exp_b_mstride;
+    static_assert(S == 8, "the level sum below is written for eight slices");
     const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
-    const uint32_t cbeg = (uint32_t)half * (BN / 2);
-    // whole 8-column chunks inside the output and a 32-byte aligned row: two
-    // 32-byte accesses per chunk, else element by element
-    const bool vec = g.vec32 != 0;
-#pragma unroll 1
-    for (uint32_t c0 = cbeg; c0 < cbeg + BN / 2; c0 += 8) {
-      const uint32_t colc = col0 + c0;
-      const bool full = row_ok && colc + 8 <= g.n;
-      double cv[8];
-      if (TRAIL && full && vec) {
-        ld_v4f64(crow + colc, cv);
-        ld_v4f64(crow + colc + 4, cv + 4);
-      }
+    const int ebase = ea - 7 * (S + 1);
+#pragma unroll
+    for (int k = 0; k < EPI_COLS; k += 8) {
+      const uint32_t c0 = (uint32_t)part * EPI_COLS + (uint32_t)k;   // column inside the tile
       float acc[S][8];
 #pragma unroll
       for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
       tc::tmem_ld_wait();
-      if (!row_ok || colc >= g.n) continue;
+      if (!row_ok || col0 + c0 >= g.n) continue;
       double v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        // T = sum_l acc_l 128^(S-1-l) (up to 7 S + 13 bits) as
-        // T_hi 128^(S-H) + T_lo, each half an exact int64 Horner sum of
-        // the level integers (acc + 1.5 2^23 read as bits, minus the bits
-        // of 1.5 2^23), then one 128-bit add
-        constexpr int H = S / 2;
-        int64_t th = 0, tl = 0;
+        // level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
+        // |acc_l| <= 2^22); T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with
+        //   t_hi = (acc_0 128 + acc_1) 2^14 + acc_2 128 + acc_3   (< 2^44)
+        //   t_lo = (acc_4 128 + acc_5) 2^14 + acc_6 128 + acc_7
+        // (the pairs in 32-bit wrapping arithmetic: each pair fits in 30 bits)
+        uint32_t u[S];
 #pragma unroll
-        for (int l = 0; l < H; ++l)
-          th = th * 128 + (int32_t)(__float_as_uint(acc[l][e] + 12582912.0f) - 0x4B400000u);
-#pragma unroll
-        for (int l = H; l < S; ++l)
-          tl = tl * 128 + (int32_t)(__float_as_uint(acc[l][e] + 12582912.0f) - 0x4B400000u);
-        uint64_t hi = (uint64_t)(th >> (64 - 7 * (S - H)));
-        uint64_t lo = (uint64_t)th << (7 * (S - H));
+        for (int l = 0; l < S; ++l) u[l] = __float_as_uint(acc[l][e] + 12582912.0f);
+        constexpr uint32_t M129 = 0x4B400000u * 129u;   // the offsets of a pair (mod 2^32)
+        const int32_t p01 = (int32_t)(u[0] * 128u + u[1] - M129);
+        const int32_t p23 = (int32_t)(u[2] * 128u + u[3] - M129);
+        const int32_t p45 = (int32_t)(u[4] * 128u + u[5] - M129);
+        const int32_t p67 = (int32_t)(u[6] * 128u + u[7] - M129);
+        const int64_t th = (int64_t)p01 * 16384 + p23;
+        const int64_t tl = (int64_t)p45 * 16384 + p67;
+        uint64_t hi = (uint64_t)(th >> 36);
+        uint64_t lo = (uint64_t)th << 28;
         const uint64_t lo2 = lo + (uint64_t)tl;
         hi += (uint64_t)(tl >> 63) + (lo2 < lo);
         lo = lo2;
-        const uint32_t col = colc + e;
-        const int eb = col < g.n ? eb_row[col] : 0;
-        v[e] = scaled_i128_to_f64(hi, lo, ea + eb - 7 * (S + 1));
+        v[e] = scaled_i128_to_f64(hi, lo, ebase + s_eb[c0 + e]);
       }
-      if (full && vec) {
+      const uint32_t colc = col0 + c0;
+      if (vec) {
         if (TRAIL) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = cv[e] - v[e];
+          for (int e = 0; e < 8; ++e) v[e] = cv[k + e] - v[e];
         }
         st_v4f64(crow + colc, v);
         st_v4f64(crow + colc + 4, v + 4);
@@ -588,6 +607,19 @@ __device__ __forceinline__ df df_recip(df d) {
 
 constexpr int NPAIR = NB * (NB - 1) / 2;   // pairs (i, l), 1 <= l <= i < 128
 
+// Shared-memory storage of a double-float, 8-byte aligned so that a pair
+// moves in one access.
+struct __align__(8) dfs {
+  float hi, lo;
+};
+__device__ __forceinline__ df ld_df(const dfs& x) {
+  const float2 v = *reinterpret_cast<const float2*>(&x);
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void st_df(dfs& x, df v) {
+  *reinterpret_cast<float2*>(&x) = make_float2(v.hi, v.lo);
+}
+
 // Right-looking LDL^T and, in the same sweep, the inverse X = L^-1: after
 // column j of L is known (step j), every thread takes its share of one flat
 // index space covering
@@ -600,11 +632,11 @@ constexpr int NPAIR = NB * (NB - 1) / 2;   // pairs (i, l), 1 <= l <= i < 128
 // so every lane works on every step and a step costs two barriers.
 template <int S>
 __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
-  extern __shared__ df sm[];               // [NB][DG]: L below the diagonal, X^T above
-  __shared__ df s_w[NB];                   // column j before scaling
-  __shared__ df s_l[NB];                   // column j of L
-  __shared__ df s_d[NB];                   // the pivots (scaled block)
-  __shared__ df s_rcp[NB];                 // their reciprocals
+  extern __shared__ dfs sm[];              // [NB][DG]: L below the diagonal, X^T above
+  __shared__ dfs s_w[NB];                  // column j before scaling
+  __shared__ dfs s_l[NB];                  // column j of L
+  __shared__ dfs s_d[NB];                  // the pivots (scaled block)
+  __shared__ dfs s_rcp[NB];                // their reciprocals
   __shared__ uint16_t s_pair[NPAIR];       // (i << 8) | l
   __shared__ int s_scale, s_bad;
   const uint32_t b = blockIdx.x;
@@ -631,43 +663,43 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
   const int sc = s_scale;
   for (int idx = tid; idx < kb * kb; idx += NT) {
     const int i = idx / kb, j = idx - (idx / kb) * kb;
-    sm[i * DG + j] = j <= i ? df_of_scaled(A[(uint64_t)i * g.lda + j], sc) : df{0.0f, 0.0f};
+    st_df(sm[i * DG + j], j <= i ? df_of_scaled(A[(uint64_t)i * g.lda + j], sc) : df{0.0f, 0.0f});
   }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     // pivot and column j of L: every thread forms 1 / d_j itself
-    const df dj = sm[j * DG + j];
+    const df dj = ld_df(sm[j * DG + j]);
     const bool pos = dj.hi > 0x1p-100f;
     const df rj = pos ? df_recip(dj) : df{0.0f, 0.0f};
     if (tid == 0) {
-      s_d[j] = dj;
-      s_rcp[j] = rj;
+      st_df(s_d[j], dj);
+      st_df(s_rcp[j], rj);
       if (!pos && !s_bad) s_bad = 1 + j;
     }
     for (int i = j + 1 + tid; i < kb; i += NT) {
-      const df w = sm[i * DG + j];
+      const df w = ld_df(sm[i * DG + j]);
       const df l = df_mul(w, rj);
-      s_w[i] = w;
-      s_l[i] = l;
-      sm[i * DG + j] = l;
+      st_df(s_w[i], w);
+      st_df(s_l[i], l);
+      st_df(sm[i * DG + j], l);
     }
     __syncthreads();
     const int np = (kb - 1 - j) * (kb - j) / 2;    // trailing pairs of step j
     const int nc = j + 1;                          // inverse: columns 0 .. j
     const int nx = (kb - 1 - j) * nc;              // inverse: (rows j+1 .. kb-1) x columns
-    const float inv_nc = 1.0f / (float)nc;
+    // u div nc as a multiply-high: exact for u < 2^14 with m = ceil(2^32 / nc)
+    const uint64_t inv_nc = (0x100000000ull + nc - 1) / nc;    // <= 2^32
     for (int t = tid; t < np + nx; t += NT) {
       if (t < np) {
         const int pr = s_pair[t];
         const int i = pr >> 8, l = pr & 255;
-        sm[i * DG + l] = df_fnms(sm[i * DG + l], s_l[i], s_w[l]);
+        st_df(sm[i * DG + l], df_fnms(ld_df(sm[i * DG + l]), ld_df(s_l[i]), ld_df(s_w[l])));
       } else {
         const int u = t - np;
-        // u = (i - j - 1) nc + c; exact: (u + 1/2) / nc stays >= 1/256 from an integer
-        const int q = __float2int_rz(((float)u + 0.5f) * inv_nc);
+        const int q = (int)(((uint64_t)u * inv_nc) >> 32);    // u = (i - j - 1) nc + c
         const int c = u - q * nc, i = j + 1 + q;
-        const df xjc = c == j ? df{1.0f, 0.0f} : sm[c * DG + j];
-        sm[c * DG + i] = df_fnms(sm[c * DG + i], s_l[i], xjc);
+        const df xjc = c == j ? df{1.0f, 0.0f} : ld_df(sm[c * DG + j]);
+        st_df(sm[c * DG + i], df_fnms(ld_df(sm[c * DG + i]), ld_df(s_l[i]), xjc));
       }
     }
     __syncthreads();
@@ -675,21 +707,21 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
   // outputs: L (strict lower part) and D into the matrix, D into d[]
   for (int idx = tid; idx < kb * kb; idx += NT) {
     const int i = idx / kb, j = idx - (idx / kb) * kb;
-    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(sm[i * DG + j], 0);
-    else if (j == i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(s_d[i], sc);
+    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(ld_df(sm[i * DG + j]), 0);
+    else if (j == i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(ld_df(s_d[i]), sc);
   }
-  for (int j = tid; j < kb; j += NT) g.d[b * g.d_mstride + g.k0 + j] = f64_of_scaled(s_d[j], sc);
+  for (int j = tid; j < kb; j += NT) g.d[b * g.d_mstride + g.k0 + j] = f64_of_scaled(ld_df(s_d[j]), sc);
   if (tid == 0 && s_bad) atomicCAS(&g.info[b], 0, (int)g.k0 + s_bad);
   // B-role operand of the panel product: row n = X[n][:] / d_n, unscaled
   uint8_t* img = g.img_x + b * g.img_x_mstride;
   for (int n = warp; n < NB; n += NT / 32) {
     double v[4];
-    const df rn = n < kb ? s_rcp[n] : df{0.0f, 0.0f};
+    const df rn = n < kb ? ld_df(s_rcp[n]) : df{0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = 4 * lane + i;
       df x = df{0.0f, 0.0f};
-      if (n < kb && k < kb) x = k == n ? rn : (k < n ? df_mul(sm[k * DG + n], rn) : df{0.0f, 0.0f});
+      if (n < kb && k < kb) x = k == n ? rn : (k < n ? df_mul(ld_df(sm[k * DG + n]), rn) : df{0.0f, 0.0f});
       v[i] = f64_of_scaled(x, -sc);
     }
     slice_row<S>(v, img + (uint64_t)(n / RB_B) * S * SLICE_B, RB_B, n % RB_B,
