@@ -108,6 +108,20 @@ int set_attrs_once() {
   return MRG_OK;
 }
 
+// Tiles per CTA of a product launch: enough for one wave over the SMs, at
+// most `cap` (the bulk of a trailing update takes short chunks, so that the
+// critical chain's kernels find SMs between them).
+uint32_t chunk(uint64_t tiles, uint32_t batch, uint32_t cap) {
+  const uint64_t items = tiles * batch;
+  const uint64_t sms = (uint64_t)mrg::sm_count();
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(cap, (items + sms - 1) / sms));
+}
+
+dim3 grid_of(const GemmArgs& g) {
+  const uint64_t items = (uint64_t)g.tiles_total * g.batch;
+  return dim3((unsigned)((items + g.per_cta - 1) / g.per_cta));
+}
+
 int after(cudaError_t e, const char* what) {
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, what);
@@ -325,8 +339,10 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     gp.tile_set = TILES_LOWER;
     gp.vec32 = vec32;
     gp.status = status;
-    const dim3 pgrid((unsigned)((nt + BM - 1) / BM * gp.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, false><<<pgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gp);
+    gp.batch = batch;
+    gp.tiles_total = (uint32_t)((nt + BM - 1) / BM * gp.tiles_n);
+    gp.per_cta = chunk(gp.tiles_total, batch, 1 << 30);
+    ozaki_gemm_kernel<kSlices, false><<<grid_of(gp), GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gp);
     if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (panel)"))) return rc;
     // trailing operands: L_ik (A role) and W = L_ik D_k (B role)
     sa.img_b = reinterpret_cast<uint8_t*>(base + L.img_w[q]);
@@ -351,8 +367,9 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
       return mrg::set_error(MRG_ECUDA, "ordering the trailing updates");
     gt.tile_set = TILES_NEXT;
     gt.tiles_n = (uint32_t)std::min<uint64_t>(2, Tc);
-    const dim3 ngrid((unsigned)(T * gt.tiles_n), batch);
-    ozaki_gemm_kernel<kSlices, true><<<ngrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gt);
+    gt.tiles_total = (uint32_t)(T * gt.tiles_n);
+    gt.per_cta = chunk(gt.tiles_total, batch, 1 << 30);
+    ozaki_gemm_kernel<kSlices, true><<<grid_of(gt), GEMM_THREADS, GemmSmem<kSlices>::TOTAL, hi>>>(gt);
     if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (next panel)"))) return rc;
     rest_pending = false;
     if (Tc > 2) {
@@ -361,8 +378,9 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
         return mrg::set_error(MRG_ECUDA, "handing the trailing update to the bulk stream");
       gt.tile_set = TILES_REST;
       gt.tiles_n = (uint32_t)Tc;
-      const dim3 rgrid((unsigned)((T - 2) * (T - 1) + (Tc - 2)), batch);
-      ozaki_gemm_kernel<kSlices, true><<<rgrid, GEMM_THREADS, GemmSmem<kSlices>::TOTAL, lo>>>(gt);
+      gt.tiles_total = (uint32_t)((T - 2) * (T - 1) + (Tc - 2));
+      gt.per_cta = chunk(gt.tiles_total, batch, 4);
+      ozaki_gemm_kernel<kSlices, true><<<grid_of(gt), GEMM_THREADS, GemmSmem<kSlices>::TOTAL, lo>>>(gt);
       if ((rc = after(cudaSuccess, "ozaki_gemm_kernel (trailing)"))) return rc;
       if ((e = cudaEventRecord(SS->rest, lo)) != cudaSuccess)
         return mrg::set_error(MRG_ECUDA, "recording the trailing update");

@@ -274,6 +274,9 @@ struct GemmArgs {
   uint32_t m, n;           // output rows and columns
   uint32_t tiles_n;        // rectangle tile sets: column tiles per row of tiles
   int tile_set;            // TRAIL: TILES_LOWER, TILES_NEXT (tj < 2) or TILES_REST (tj >= 2)
+  uint32_t tiles_total;    // tiles of the set per matrix
+  uint32_t batch;          // matrices
+  uint32_t per_cta;        // consecutive items (tiles) each CTA processes
   int vec32;               // c and ldc * 8 are multiples of 32 bytes (vector row access)
   int* status;
 };
@@ -345,10 +348,37 @@ __device__ __forceinline__ void st_v4f64(double* p, const double* v) {
 constexpr int GEMM_THREADS = 512;   // warp 0 lane 0 issues copies and MMAs; all 16 warps drain TMEM
 constexpr int EPI_COLS = BN * 4 / (GEMM_THREADS / 32);   // columns per thread in the epilogue (16)
 
+// The tile (ti, tj) of item x of the tile set (identical for every thread).
+__device__ __forceinline__ void tile_of(const GemmArgs& g, bool trail, uint32_t x, uint32_t& ti,
+                                        uint32_t& tj) {
+  if (trail && g.tile_set == TILES_REST) {
+    // lower tiles right of the next panel (tj >= 2): row ti >= 1 holds
+    // 2 ti of them, the rows before it ti (ti - 1) in all
+    uint32_t t = (uint32_t)((1.0f + sqrtf(4.0f * (float)x + 1.0f)) * 0.5f);
+    while ((uint64_t)t * (t - 1) > x) --t;
+    while ((uint64_t)(t + 1) * t <= x) ++t;
+    ti = t;
+    tj = 2 + x - t * (t - 1);
+  } else if (trail && g.tile_set == TILES_LOWER) {
+    lower_tile(x, ti, tj);
+  } else {   // a rectangle of tiles_n columns of tiles (the panel; the next panel of a trailing update)
+    ti = x / g.tiles_n;
+    tj = x % g.tiles_n;
+  }
+}
+
+// One CTA takes `per_cta` consecutive items of the flat set (matrix-major:
+// item = b * tiles + x) -- a chunk of persistence: while its 16 warps drain
+// one tile's accumulators, the next tile's operands are already on their way
+// into shared memory (the MMAs of the finished tile have released it).
+// Thread 0 of warp 0 issues the copies and the MMAs; the MMA issue is fully
+// unrolled over precomputed descriptors (one tcgen05.mma per instruction
+// slot, not a descriptor computation each).
 template <int S, bool TRAIL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g) {
   using SM = GemmSmem<S>;
   constexpr int NST = SM::NST;
+  static_assert(S == 8 && NST == 3, "the unrolled MMA schedule below is written for 8 slices");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -361,25 +391,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   uint64_t* done = bar + 1 + 2 * NST;     // [1]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + 2 * NST);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 3 + 2 * NST);
+  int* s_eb = reinterpret_cast<int*>(smem + SM::EB_OFF);
 
-  uint32_t ti, tj;
-  if (TRAIL && g.tile_set == TILES_REST) {
-    // lower tiles right of the next panel (tj >= 2): row ti >= 1 holds
-    // 2 ti of them, rows before it ti (ti - 1) in all
-    uint32_t t = (uint32_t)((1.0f + sqrtf(4.0f * (float)blockIdx.x + 1.0f)) * 0.5f);
-    while ((uint64_t)t * (t - 1) > blockIdx.x) --t;
-    while ((uint64_t)(t + 1) * t <= blockIdx.x) ++t;
-    ti = t;
-    tj = 2 + blockIdx.x - t * (t - 1);
-  } else if (TRAIL && g.tile_set == TILES_LOWER) {
-    lower_tile(blockIdx.x, ti, tj);
-  } else {   // a rectangle of tiles_n columns of tiles (the panel; the next panel of a trailing update)
-    ti = blockIdx.x / g.tiles_n;
-    tj = blockIdx.x % g.tiles_n;
-  }
-  const uint32_t row0 = ti * BM, col0 = tj * BN;
-  if (row0 >= g.m || col0 >= g.n) return;   // uniform over the CTA, before any allocation
-  const uint32_t b = blockIdx.y;
+  const uint64_t total = (uint64_t)g.tiles_total * g.batch;
+  const uint64_t it0 = (uint64_t)blockIdx.x * g.per_cta;
+  if (it0 >= total) return;                  // uniform over the CTA, before any allocation
+  const uint32_t nit = (uint32_t)(total - it0 < g.per_cta ? total - it0 : g.per_cta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -398,136 +415,185 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   tc::tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // Epilogue inputs, fetched while the MMAs run: warp w later drains TMEM
-  // lanes 32 (w mod 4) .. + 31 (its rows) and the part w div 4 of the tile's
-  // 64 columns, EPI_COLS columns per thread; the old C values of those
-  // (TRAIL, row in range, 32-byte aligned rows) go to registers now.
+  // thread 0's barrier phase bookkeeping: completed loads / commits per stage
+  uint32_t fcnt[NST] = {0, 0, 0}, ecnt[NST] = {0, 0, 0};
+  auto item_ptrs = [&](uint64_t it, const uint8_t*& gA, const uint8_t*& gB) {
+    const uint32_t b = (uint32_t)(it / g.tiles_total);
+    uint32_t ti, tj;
+    tile_of(g, TRAIL, (uint32_t)(it - (uint64_t)b * g.tiles_total), ti, tj);
+    gA = g.img_a + b * g.img_a_mstride + (uint64_t)ti * S * SLICE_A;
+    gB = g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B;
+  };
+  // the first tile's B block and A slices 0 .. NST-1
+  if (threadIdx.x == 0) {
+    const uint8_t *gA, *gB;
+    item_ptrs(it0, gA, gB);
+    tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
+    tc::bulk_g2s(sB, gB, SM::B_BYTES, full_b);
+#pragma unroll
+    for (int p = 0; p < NST; ++p) {
+      tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
+      tc::bulk_g2s(sA + p * SLICE_A, gA + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
+    }
+  }
+
   const int quarter = warp & 3, part = warp >> 2;
   const uint32_t r = (uint32_t)(quarter * 32 + lane);
-  const uint32_t row = row0 + r;
-  const bool row_ok = row < g.m;
-  const uint32_t cbeg = col0 + (uint32_t)part * EPI_COLS;
-  double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
-  const bool vec = g.vec32 != 0 && row_ok && cbeg + EPI_COLS <= g.n;
-  double cv[EPI_COLS];
-  if (TRAIL && vec) {
+  const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+  for (uint32_t k = 0; k < nit; ++k) {
+    const uint64_t it = it0 + k;
+    const uint32_t b = (uint32_t)(it / g.tiles_total);
+    uint32_t ti, tj;
+    tile_of(g, TRAIL, (uint32_t)(it - (uint64_t)b * g.tiles_total), ti, tj);
+    const uint32_t row0 = ti * BM, col0 = tj * BN;
+    // epilogue inputs of this tile, fetched while its MMAs run: the old C
+    // values of this thread's EPI_COLS columns (TRAIL, row in range, 32-byte
+    // aligned rows), the row exponent, and the tile's column exponents
+    const uint32_t row = row0 + r;
+    const bool row_ok = row < g.m;
+    const uint32_t cbeg = col0 + (uint32_t)part * EPI_COLS;
+    double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
+    const bool vec = g.vec32 != 0 && row_ok && cbeg + EPI_COLS <= g.n;
+    double cv[EPI_COLS];
+    if (TRAIL && vec) {
 #pragma unroll
-    for (int k = 0; k < EPI_COLS; k += 4) ld_v4f64(crow + cbeg + k, cv + k);
-  }
-  int* s_eb = reinterpret_cast<int*>(smem + SM::EB_OFF);
-  if (threadIdx.x < BN)
-    s_eb[threadIdx.x] = col0 + threadIdx.x < g.n ? g.exp_b[b * g.exp_b_mstride + col0 + threadIdx.x] : 0;
-  const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
+      for (int e = 0; e < EPI_COLS; e += 4) ld_v4f64(crow + cbeg + e, cv + e);
+    }
+    if (threadIdx.x < BN)
+      s_eb[threadIdx.x] =
+          col0 + threadIdx.x < g.n ? g.exp_b[b * g.exp_b_mstride + col0 + threadIdx.x] : 0;
+    const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
 
-  if (warp == 0) {
-    if (lane == 0) {
-      const uint8_t* gA = g.img_a + b * g.img_a_mstride + (uint64_t)ti * S * SLICE_A;
-      const uint8_t* gB = g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B;
+    if (warp == 0) {
+      if (lane == 0 && *abort_flag == 0) {
+        const uint8_t *gA, *gB;
+        item_ptrs(it, gA, gB);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+        const uint64_t ad0 = tc::sw128_desc(tc::smem_u32(sA));
+        const uint64_t bd0 = tc::sw128_desc(tc::smem_u32(sB));
+        bool ok = tc::mbar_wait(full_b, k & 1, WAIT_NS);
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
+          const int st = p % NST;
+          if (ok) ok = tc::mbar_wait(&full_a[st], fcnt[st] & 1, WAIT_NS);
+          ++fcnt[st];
+          if (ok) {
+            tc::tc_fence_after();
+            // descriptor start addresses advance in 16-byte units
+            const uint64_t ad = ad0 + (uint64_t)((st * SLICE_A) >> 4);
+#pragma unroll
+            for (int q = 0; q < S - p; ++q) {
+              const uint64_t bd = bd0 + (uint64_t)((q * SLICE_B) >> 4);
+              const uint32_t d = tmem + (uint32_t)(p + q) * BN;
+#pragma unroll
+              for (int kk = 0; kk < NB / 16; ++kk)
+                tc::mma_bf16(d, ad + (uint64_t)(((kk >> 2) * (RB_A * 128) + (kk & 3) * 32) >> 4),
+                             bd + (uint64_t)(((kk >> 2) * (RB_B * 128) + (kk & 3) * 32) >> 4), idesc,
+                             (p > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(&empty_a[st]);
+          ++ecnt[st];
+          // refill the stage of slice p - 1 with slice p - 1 + NST once its
+          // MMAs are done (those of slice p are queued behind them)
+          if (p >= 1 && p - 1 + NST < S) {
+            const int sr = (p - 1) % NST;
+            if (ok) ok = tc::mbar_wait(&empty_a[sr], (ecnt[sr] - 1) & 1, WAIT_NS);
+            if (ok) {
+              tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
+              tc::bulk_g2s(sA + sr * SLICE_A, gA + (size_t)(p - 1 + NST) * SLICE_A, SLICE_A,
+                           &full_a[sr]);
+            }
+          }
+        }
+        if (!ok) {
+          *abort_flag = 1;
+          atomicOr(g.status, ERR_TIMEOUT);
+        }
+        tc::mma_commit(done);   // every MMA issued above has completed when this arrives
+      } else if (lane == 0) {
+        tc::mma_commit(done);
+      }
+      __syncwarp();
+    }
+    // all threads: the accumulators are final (bounded wait)
+    const bool fin = tc::mbar_wait(done, k & 1, WAIT_NS);
+    __syncthreads();
+    if (!fin && threadIdx.x == 0) {
+      *abort_flag = 1;
+      atomicOr(g.status, ERR_TIMEOUT);
+    }
+    // the MMAs are done with shared memory: the next tile's operands start
+    // loading now, under this tile's epilogue
+    if (threadIdx.x == 0 && k + 1 < nit && *abort_flag == 0) {
+      const uint8_t *gA, *gB;
+      item_ptrs(it + 1, gA, gB);
       tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
       tc::bulk_g2s(sB, gB, SM::B_BYTES, full_b);
-      for (int p = 0; p < NST && p < S; ++p) {
+#pragma unroll
+      for (int p = 0; p < NST; ++p) {
         tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
         tc::bulk_g2s(sA + p * SLICE_A, gA + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
       }
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-      bool ok = tc::mbar_wait(full_b, 0, WAIT_NS);
-      for (int p = 0; p < S && ok; ++p) {
-        const int st = p % NST;
-        ok = tc::mbar_wait(&full_a[st], (p / NST) & 1, WAIT_NS);
-        if (!ok) break;
-        tc::tc_fence_after();
-        const uint32_t a_base = tc::smem_u32(sA + st * SLICE_A);
-        for (int q = 0; q < S - p; ++q) {
-          const uint32_t b_base = tc::smem_u32(sB + q * SLICE_B);
-          const uint32_t d = tmem + (uint32_t)(p + q) * BN;
-#pragma unroll
-          for (int kk = 0; kk < NB / 16; ++kk) {
-            const uint32_t ao = a_base + (kk >> 2) * (RB_A * 128) + (kk & 3) * 32;
-            const uint32_t bo = b_base + (kk >> 2) * (RB_B * 128) + (kk & 3) * 32;
-            tc::mma_bf16(d, tc::sw128_desc(ao), tc::sw128_desc(bo), idesc, (p > 0 || kk > 0) ? 1u : 0u);
-          }
-        }
-        tc::mma_commit(&empty_a[st]);
-        // refill the stage of slice p - 1 once its MMAs are done (those of
-        // slice p are queued behind them, so the tensor pipe keeps busy)
-        const int pr = p - 1;
-        if (pr >= 0 && pr + NST < S) {
-          const int sr = pr % NST;
-          ok = tc::mbar_wait(&empty_a[sr], (pr / NST) & 1, WAIT_NS);
-          if (!ok) break;
-          tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
-          tc::bulk_g2s(sA + sr * SLICE_A, gA + (size_t)(pr + NST) * SLICE_A, SLICE_A, &full_a[sr]);
-        }
-      }
-      if (!ok) {
-        *abort_flag = 1;
-        atomicOr(g.status, ERR_TIMEOUT);
-      }
-      tc::mma_commit(done);   // every MMA issued above has completed when this arrives
     }
-    __syncwarp();
-  }
-  // all threads: the accumulators are final (bounded wait)
-  const bool fin = tc::mbar_wait(done, 0, WAIT_NS);
-  __syncthreads();
-  if (!fin && threadIdx.x == 0) atomicOr(g.status, ERR_TIMEOUT);
-  if (fin && *abort_flag == 0) {
-    tc::tc_fence_after();
-    static_assert(S == 8, "the level sum below is written for eight slices");
-    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int ebase = ea - 7 * (S + 1);
+    if (fin && *abort_flag == 0) {
+      tc::tc_fence_after();
+      const int ebase = ea - 7 * (S + 1);
 #pragma unroll
-    for (int k = 0; k < EPI_COLS; k += 8) {
-      const uint32_t c0 = (uint32_t)part * EPI_COLS + (uint32_t)k;   // column inside the tile
-      float acc[S][8];
+      for (int kc = 0; kc < EPI_COLS; kc += 8) {
+        const uint32_t c0 = (uint32_t)part * EPI_COLS + (uint32_t)kc;   // column inside the tile
+        float acc[S][8];
 #pragma unroll
-      for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
-      tc::tmem_ld_wait();
-      if (!row_ok || col0 + c0 >= g.n) continue;
-      double v[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        // level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
-        // |acc_l| <= 2^22); T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with
-        //   t_hi = (acc_0 128 + acc_1) 2^14 + acc_2 128 + acc_3   (< 2^44)
-        //   t_lo = (acc_4 128 + acc_5) 2^14 + acc_6 128 + acc_7
-        // (the pairs in 32-bit wrapping arithmetic: each pair fits in 30 bits)
-        uint32_t u[S];
-#pragma unroll
-        for (int l = 0; l < S; ++l) u[l] = __float_as_uint(acc[l][e] + 12582912.0f);
-        constexpr uint32_t M129 = 0x4B400000u * 129u;   // the offsets of a pair (mod 2^32)
-        const int32_t p01 = (int32_t)(u[0] * 128u + u[1] - M129);
-        const int32_t p23 = (int32_t)(u[2] * 128u + u[3] - M129);
-        const int32_t p45 = (int32_t)(u[4] * 128u + u[5] - M129);
-        const int32_t p67 = (int32_t)(u[6] * 128u + u[7] - M129);
-        const int64_t th = (int64_t)p01 * 16384 + p23;
-        const int64_t tl = (int64_t)p45 * 16384 + p67;
-        uint64_t hi = (uint64_t)(th >> 36);
-        uint64_t lo = (uint64_t)th << 28;
-        const uint64_t lo2 = lo + (uint64_t)tl;
-        hi += (uint64_t)(tl >> 63) + (lo2 < lo);
-        lo = lo2;
-        v[e] = scaled_i128_to_f64(hi, lo, ebase + s_eb[c0 + e]);
-      }
-      const uint32_t colc = col0 + c0;
-      if (vec) {
-        if (TRAIL) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = cv[k + e] - v[e];
-        }
-        st_v4f64(crow + colc, v);
-        st_v4f64(crow + colc + 4, v + 4);
-      } else {
+        for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
+        tc::tmem_ld_wait();
+        if (!row_ok || col0 + c0 >= g.n) continue;
+        double v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const uint32_t col = colc + e;
-          if (col < g.n) crow[col] = TRAIL ? crow[col] - v[e] : v[e];
+          // level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
+          // |acc_l| <= 2^22); T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with
+          //   t_hi = (acc_0 128 + acc_1) 2^14 + acc_2 128 + acc_3   (< 2^44)
+          //   t_lo = (acc_4 128 + acc_5) 2^14 + acc_6 128 + acc_7
+          // (the pairs in 32-bit wrapping arithmetic: each pair fits in 30 bits)
+          uint32_t u[S];
+#pragma unroll
+          for (int l = 0; l < S; ++l) u[l] = __float_as_uint(acc[l][e] + 12582912.0f);
+          constexpr uint32_t M129 = 0x4B400000u * 129u;   // the offsets of a pair (mod 2^32)
+          const int32_t p01 = (int32_t)(u[0] * 128u + u[1] - M129);
+          const int32_t p23 = (int32_t)(u[2] * 128u + u[3] - M129);
+          const int32_t p45 = (int32_t)(u[4] * 128u + u[5] - M129);
+          const int32_t p67 = (int32_t)(u[6] * 128u + u[7] - M129);
+          const int64_t th = (int64_t)p01 * 16384 + p23;
+          const int64_t tl = (int64_t)p45 * 16384 + p67;
+          uint64_t hi = (uint64_t)(th >> 36);
+          uint64_t lo = (uint64_t)th << 28;
+          const uint64_t lo2 = lo + (uint64_t)tl;
+          hi += (uint64_t)(tl >> 63) + (lo2 < lo);
+          lo = lo2;
+          v[e] = scaled_i128_to_f64(hi, lo, ebase + s_eb[c0 + e]);
+        }
+        const uint32_t colc = col0 + c0;
+        if (vec) {
+          if (TRAIL) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = cv[kc + e] - v[e];
+          }
+          st_v4f64(crow + colc, v);
+          st_v4f64(crow + colc + 4, v + 4);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t col = colc + e;
+            if (col < g.n) crow[col] = TRAIL ? crow[col] - v[e] : v[e];
+          }
         }
       }
     }
+    // TMEM and s_eb free for the next tile
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
   }
-  tc::tc_fence_before();
-  __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
@@ -688,7 +754,7 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
     const int nc = j + 1;                          // inverse: columns 0 .. j
     const int nx = (kb - 1 - j) * nc;              // inverse: (rows j+1 .. kb-1) x columns
     // u div nc as a multiply-high: exact for u < 2^14 with m = ceil(2^32 / nc)
-    const uint64_t inv_nc = (0x100000000ull + nc - 1) / nc;    // <= 2^32
+    const uint32_t inv_nc = (uint32_t)((0x100000000ull + nc - 1) / nc);   // (nc = 1: unused)
     for (int t = tid; t < np + nx; t += NT) {
       if (t < np) {
         const int pr = s_pair[t];
@@ -696,7 +762,7 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
         st_df(sm[i * DG + l], df_fnms(ld_df(sm[i * DG + l]), ld_df(s_l[i]), ld_df(s_w[l])));
       } else {
         const int u = t - np;
-        const int q = (int)(((uint64_t)u * inv_nc) >> 32);    // u = (i - j - 1) nc + c
+        const int q = nc == 1 ? u : (int)__umulhi((uint32_t)u, inv_nc);   // u = (i - j - 1) nc + c
         const int c = u - q * nc, i = j + 1 + q;
         const df xjc = c == j ? df{1.0f, 0.0f} : ld_df(sm[c * DG + j]);
         st_df(sm[c * DG + i], df_fnms(ld_df(sm[c * DG + i]), ld_df(s_l[i]), xjc));
