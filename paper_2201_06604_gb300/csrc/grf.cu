@@ -29,7 +29,7 @@ uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 // step k writes set k mod 2 while the bulk of step k - 1's trailing update
 // still reads the other.
 struct LdlLayout {
-  uint64_t img_a[2], img_w[2], img_x, exp_a[2], exp_w[2], exp_x, exp_eq, per_matrix, common;
+  uint64_t img_a[2], img_w[2], img_x, bx, exp_a[2], exp_w[2], exp_x, exp_eq, per_matrix, common;
   explicit LdlLayout(uint64_t n) {
     const uint64_t ta = (n + RB_A - 1) / RB_A;
     uint64_t o = 0;
@@ -41,6 +41,8 @@ struct LdlLayout {
     }
     img_x = o;
     o += 2 * kSlices * SLICE_B;
+    bx = o;                      // the panel product's B operand in fp64, 128 x 128
+    o += NB * NB * 8;
     for (int q = 0; q < 2; ++q) {
       exp_a[q] = o;
       o += align_up(ta * RB_A * 4, 1024);
@@ -102,6 +104,9 @@ int set_attrs_once() {
                              (int)GemmSmem<kSlices>::TOTAL);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(ldl_diag_kernel<kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(NB * DG * sizeof(mrg::df)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ldl_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(NB * DG * sizeof(mrg::df)));
   if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, cudaGetErrorString(e));
   done[dev] = true;
@@ -296,9 +301,34 @@ int mrg_grf_ldl(double* a, uint64_t n, uint64_t lda, uint32_t batch, double* d, 
     dg.img_x_mstride = pm;
     dg.exp_x_mstride = pm / 4;
     dg.info = dinfo;
-    ldl_diag_kernel<kSlices><<<batch, 512, NB * DG * sizeof(mrg::df), hi>>>(dg);
+    ldl_diag_kernel<kSlices><<<batch, DIAG_THREADS, NB * DG * sizeof(mrg::df), hi>>>(dg);
     if ((rc = after(cudaSuccess, "ldl_diag_kernel"))) return rc;
     if (nt == 0) break;
+    // B = L_kk^-1 / d (by columns, many CTAs) and its B-role slices
+    double* bx = reinterpret_cast<double*>(base + L.bx);
+    ldl_inverse_kernel<<<dim3(NB / INV_COLS, batch), INV_COLS * 32, NB * DG * sizeof(mrg::df), hi>>>(
+        a, lda, a_ms, (uint32_t)k0, kb, d, n, bx, pm / 8);
+    if ((rc = after(cudaSuccess, "ldl_inverse_kernel"))) return rc;
+    {
+      SliceArgs sx;
+      sx.a = bx;
+      sx.lda = NB;
+      sx.a_mstride = pm / 8;
+      sx.rows = NB;
+      sx.rows_pad = NB;
+      sx.kb = NB;
+      sx.img_a = nullptr;
+      sx.exp_a = nullptr;
+      sx.img_a_mstride = sx.exp_a_mstride = 0;
+      sx.img_b = dg.img_x;
+      sx.exp_b = dg.exp_x;
+      sx.img_b_mstride = pm;
+      sx.exp_b_mstride = pm / 4;
+      sx.colscale = nullptr;
+      sx.colscale_mstride = 0;
+      slice_kernel<kSlices><<<dim3(NB / 8, batch), 256, 0, hi>>>(sx);
+      if ((rc = after(cudaSuccess, "slice_kernel (panel B)"))) return rc;
+    }
     const uint32_t rows_pad = (uint32_t)align_up(nt, RB_A);
     // panel operand: A_ik (rows t0.., columns k0.., kb wide)
     SliceArgs sa;

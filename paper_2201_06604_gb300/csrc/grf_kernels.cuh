@@ -209,9 +209,10 @@ __device__ __forceinline__ void slice_row(const double v[4], uint8_t* __restrict
 }
 
 // Slices rows [0, rows_pad) of a panel: row r is a[(r) * lda + k] for k < kb
-// (zero for r >= rows or k >= kb).  Into img_a (A role, 128-row blocks) as is,
-// and, when img_b is set, into img_b (B role, 64-row blocks) multiplied by
-// colscale[k] (W = L D).  One warp per row.
+// (zero for r >= rows or k >= kb).  When img_a is set, into img_a (A role,
+// 128-row blocks) as is; when img_b is set, into img_b (B role, 64-row
+// blocks), multiplied by colscale[k] if that is set (W = L D).  One warp per
+// row.
 struct SliceArgs {
   const double* a;
   uint64_t lda, a_mstride;
@@ -239,14 +240,17 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs g) {
     const uint32_t k = 4 * lane + i;
     v[i] = (r < g.rows && k < g.kb) ? row[k] : 0.0;
   }
-  slice_row<S>(v, g.img_a + b * g.img_a_mstride + (uint64_t)(r / RB_A) * S * SLICE_A, RB_A,
-               (int)(r % RB_A), g.exp_a + b * g.exp_a_mstride + r);
+  if (g.img_a)
+    slice_row<S>(v, g.img_a + b * g.img_a_mstride + (uint64_t)(r / RB_A) * S * SLICE_A, RB_A,
+                 (int)(r % RB_A), g.exp_a + b * g.exp_a_mstride + r);
   if (g.img_b) {
-    const double* cs = g.colscale + b * g.colscale_mstride;
+    if (g.colscale) {
+      const double* cs = g.colscale + b * g.colscale_mstride;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t k = 4 * lane + i;
-      v[i] = k < g.kb ? v[i] * cs[k] : 0.0;
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t k = 4 * lane + i;
+        v[i] = k < g.kb ? v[i] * cs[k] : 0.0;
+      }
     }
     slice_row<S>(v, g.img_b + b * g.img_b_mstride + (uint64_t)(r / RB_B) * S * SLICE_B, RB_B,
                  (int)(r % RB_B), g.exp_b + b * g.exp_b_mstride + r);
@@ -661,10 +665,11 @@ __device__ __forceinline__ df df_fnms(df a, df b, df c) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, e)));
 }
 
-// 1 / d in double-float: fp32 reciprocal and one Newton step whose residual
+// 1 / d in double-float: approximate fp32 reciprocal and one Newton step whose residual
 // 1 - d r0 is formed exactly (the product's error by FMA; 1 - p is exact).
 __device__ __forceinline__ df df_recip(df d) {
-  const float r0 = __frcp_rn(d.hi);
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(d.hi));   // the Newton step below corrects it
   const float p = __fmul_rn(d.hi, r0);
   const float pe = __fmaf_rn(d.hi, r0, -p);
   const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(d.lo, r0));
@@ -672,6 +677,8 @@ __device__ __forceinline__ df df_recip(df d) {
 }
 
 constexpr int NPAIR = NB * (NB - 1) / 2;   // pairs (i, l), 1 <= l <= i < 128
+
+
 
 // Shared-memory storage of a double-float, 8-byte aligned so that a pair
 // moves in one access.
@@ -686,28 +693,51 @@ __device__ __forceinline__ void st_df(dfs& x, df v) {
   *reinterpret_cast<float2*>(&x) = make_float2(v.hi, v.lo);
 }
 
-// Right-looking LDL^T and, in the same sweep, the inverse X = L^-1: after
-// column j of L is known (step j), every thread takes its share of one flat
-// index space covering
-//   * the trailing update a_il -= l_ij w_l (j < l <= i < kb, w = column j
-//     before scaling), from a table of (i, l) pairs ordered by column l
-//     descending, so that the pairs of step j are a prefix of it, and
-//   * the inverse's step, X[i][c] -= l_ij X[j][c] (j < i < kb, c <= j,
-//     X[j][j] = 1: a column-oriented forward substitution, backward stable
-//     per column), X[i][c] kept at sm[c][i] above the diagonal;
-// so every lane works on every step and a step costs two barriers.
+// The lower triangle (strict: below the diagonal only) of a kb x kb fp64
+// block times 2^-sc into a shared double-float array of row pitch DG; eight
+// loads in flight per thread before the first conversion.
+template <int NTH>
+__device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint64_t lda, int kb,
+                                              int sc, dfs* dst, bool strict) {
+  constexpr int U = 8;
+  const int n2 = kb * kb;
+  for (int base = (int)threadIdx.x; base < n2; base += U * NTH) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NTH;
+      const int i = idx / kb, j = idx - i * kb;
+      v[u] = idx < n2 && (strict ? j < i : j <= i) ? A[(uint64_t)i * lda + j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NTH;
+      const int i = idx / kb, j = idx - i * kb;
+      if (idx < n2 && (strict ? j < i : j <= i)) st_df(dst[i * DG + j], df_of_scaled(v[u], sc));
+    }
+  }
+}
+
+// Right-looking LDL^T of the diagonal block, one CTA per matrix: after
+// column j of L is known (step j), every thread takes its share of the
+// trailing update a_il -= l_ij w_l (j < l <= i < kb, w = column j before
+// scaling), from a table of (i, l) pairs ordered by column l descending, so
+// that the pairs of step j are a prefix of it: every lane works on every
+// step, and a step costs two barriers.  Double-float arithmetic on the FP32
+// pipes (GB300's FP64 pipe retires under one DFMA per cycle per SM).
+constexpr int DIAG_THREADS = 1024;
+
 template <int S>
-__global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
-  extern __shared__ dfs sm[];              // [NB][DG]: L below the diagonal, X^T above
+__global__ void __launch_bounds__(DIAG_THREADS, 1) ldl_diag_kernel(DiagArgs g) {
+  extern __shared__ dfs sm[];              // [NB][DG]: the block, L below the diagonal
   __shared__ dfs s_w[NB];                  // column j before scaling
   __shared__ dfs s_l[NB];                  // column j of L
   __shared__ dfs s_d[NB];                  // the pivots (scaled block)
-  __shared__ dfs s_rcp[NB];                // their reciprocals
   __shared__ uint16_t s_pair[NPAIR];       // (i << 8) | l
   __shared__ int s_scale, s_bad;
   const uint32_t b = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int NT = 512;
+  constexpr int NT = DIAG_THREADS;
   const int kb = (int)g.kb;
   double* A = g.a + b * g.a_mstride + (uint64_t)g.k0 * g.lda + g.k0;
   if (warp == 0) {
@@ -727,10 +757,7 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
   }
   __syncthreads();
   const int sc = s_scale;
-  for (int idx = tid; idx < kb * kb; idx += NT) {
-    const int i = idx / kb, j = idx - (idx / kb) * kb;
-    st_df(sm[i * DG + j], j <= i ? df_of_scaled(A[(uint64_t)i * g.lda + j], sc) : df{0.0f, 0.0f});
-  }
+  load_lower_df<NT>(A, g.lda, kb, sc, sm, false);
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     // pivot and column j of L: every thread forms 1 / d_j itself
@@ -739,7 +766,6 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
     const df rj = pos ? df_recip(dj) : df{0.0f, 0.0f};
     if (tid == 0) {
       st_df(s_d[j], dj);
-      st_df(s_rcp[j], rj);
       if (!pos && !s_bad) s_bad = 1 + j;
     }
     for (int i = j + 1 + tid; i < kb; i += NT) {
@@ -750,23 +776,17 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
       st_df(sm[i * DG + j], l);
     }
     __syncthreads();
+    // two elements per thread and trip, loaded before either is computed
     const int np = (kb - 1 - j) * (kb - j) / 2;    // trailing pairs of step j
-    const int nc = j + 1;                          // inverse: columns 0 .. j
-    const int nx = (kb - 1 - j) * nc;              // inverse: (rows j+1 .. kb-1) x columns
-    // u div nc as a multiply-high: exact for u < 2^14 with m = ceil(2^32 / nc)
-    const uint32_t inv_nc = (uint32_t)((0x100000000ull + nc - 1) / nc);   // (nc = 1: unused)
-    for (int t = tid; t < np + nx; t += NT) {
-      if (t < np) {
-        const int pr = s_pair[t];
-        const int i = pr >> 8, l = pr & 255;
-        st_df(sm[i * DG + l], df_fnms(ld_df(sm[i * DG + l]), ld_df(s_l[i]), ld_df(s_w[l])));
-      } else {
-        const int u = t - np;
-        const int q = nc == 1 ? u : (int)__umulhi((uint32_t)u, inv_nc);   // u = (i - j - 1) nc + c
-        const int c = u - q * nc, i = j + 1 + q;
-        const df xjc = c == j ? df{1.0f, 0.0f} : ld_df(sm[c * DG + j]);
-        st_df(sm[c * DG + i], df_fnms(ld_df(sm[c * DG + i]), ld_df(s_l[i]), xjc));
-      }
+    for (int t = tid; t < np; t += 2 * NT) {
+      const int tb = t + NT;
+      const int pa = s_pair[t], pb = tb < np ? s_pair[tb] : pa;   // pb = pa: computed, not stored
+      const int ia = pa >> 8, la = pa & 255, ib = pb >> 8, lb = pb & 255;
+      const df xa = ld_df(sm[ia * DG + la]), xb = ld_df(sm[ib * DG + lb]);
+      const df ya = df_fnms(xa, ld_df(s_l[ia]), ld_df(s_w[la]));
+      const df yb = df_fnms(xb, ld_df(s_l[ib]), ld_df(s_w[lb]));
+      st_df(sm[ia * DG + la], ya);
+      if (tb < np) st_df(sm[ib * DG + lb], yb);
     }
     __syncthreads();
   }
@@ -778,20 +798,63 @@ __global__ void __launch_bounds__(512, 1) ldl_diag_kernel(DiagArgs g) {
   }
   for (int j = tid; j < kb; j += NT) g.d[b * g.d_mstride + g.k0 + j] = f64_of_scaled(ld_df(s_d[j]), sc);
   if (tid == 0 && s_bad) atomicCAS(&g.info[b], 0, (int)g.k0 + s_bad);
-  // B-role operand of the panel product: row n = X[n][:] / d_n, unscaled
-  uint8_t* img = g.img_x + b * g.img_x_mstride;
-  for (int n = warp; n < NB; n += NT / 32) {
-    double v[4];
-    const df rn = n < kb ? ld_df(s_rcp[n]) : df{0.0f, 0.0f};
+}
+
+// The panel product's B operand from the diagonal block's factor:
+// B[n][k] = X[n][k] / d_n with X = L_kk^-1 (unit lower), so that
+// L_ik = A_ik L_kk^-T D^-1 = A_ik B^T.  The columns of X are independent
+// solutions of L x = e_c: one warp per column, by forward substitution in
+// outer-product order (x = e_c; for m = c, c+1, ..: x_i -= L[i][m] x_m for
+// i > m -- backward stable per column), lanes over the rows, double-float
+// arithmetic, L from the matrix (fp64, written by ldl_diag_kernel).  Grid:
+// (columns / 8, matrices), 8 warps per CTA.  Writes B (fp64, 128 x 128,
+// zero outside kb x kb) to bx.
+constexpr int INV_COLS = 8;   // columns (warps) per CTA
+
+__global__ void __launch_bounds__(INV_COLS * 32) ldl_inverse_kernel(const double* __restrict__ a,
+                                                                    uint64_t lda, uint64_t a_mstride,
+                                                                    uint32_t k0, uint32_t kb,
+                                                                    const double* __restrict__ d,
+                                                                    uint64_t d_mstride,
+                                                                    double* __restrict__ bx,
+                                                                    uint64_t bx_mstride) {
+  extern __shared__ dfs sLf[];             // [NB][DG]: L of the diagonal block (strict lower part)
+  const uint32_t b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* A = a + b * a_mstride + (uint64_t)k0 * lda + k0;
+  load_lower_df<INV_COLS * 32>(A, lda, (int)kb, 0, sLf, true);
+  __syncthreads();
+  const int c = blockIdx.x * INV_COLS + warp;
+  double* B = bx + b * bx_mstride;
+  if (c >= NB) return;
+  if (c >= (int)kb) {                       // padding column: zero
+    for (int n = lane; n < NB; n += 32) B[n * NB + c] = 0.0;
+    return;
+  }
+  // x_i for i = lane + 32 t, t = 0..3
+  df x[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = 4 * lane + i;
-      df x = df{0.0f, 0.0f};
-      if (n < kb && k < kb) x = k == n ? rn : (k < n ? df_mul(ld_df(sm[k * DG + n]), rn) : df{0.0f, 0.0f});
-      v[i] = f64_of_scaled(x, -sc);
+  for (int t = 0; t < 4; ++t) x[t] = lane + 32 * t == c ? df{1.0f, 0.0f} : df{0.0f, 0.0f};
+  for (int m = c; m < (int)kb - 1; ++m) {
+    // x_m, broadcast from the lane that holds it
+    const int tm = m >> 5, lm = m & 31;
+    df xm;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t == tm) xm = df{__shfl_sync(0xffffffffu, x[t].hi, lm), __shfl_sync(0xffffffffu, x[t].lo, lm)};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = lane + 32 * t;
+      if (i > m && i < (int)kb) x[t] = df_fnms(x[t], ld_df(sLf[i * DG + m]), xm);
     }
-    slice_row<S>(v, img + (uint64_t)(n / RB_B) * S * SLICE_B, RB_B, n % RB_B,
-                 g.exp_x + b * g.exp_x_mstride + n);
+  }
+  // B[n][c] = x_n / d_n (x_n = 0 above the diagonal, n < c)
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int n = lane + 32 * t;
+    double v = 0.0;
+    if (n < (int)kb && n >= c) v = f64_of_scaled(x[t], 0) / d[b * d_mstride + k0 + n];
+    B[n * NB + c] = v;
   }
 }
 
