@@ -668,9 +668,22 @@ def run_gpu(args):
             e2e_step()
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / KE
+        # the box's device -> pinned host copy ceiling: plain 1 GiB copies
+        # (cudaMemcpyAsync through torch) into the same pinned buffer
+        ch = host[: 1 << 30]
+        ch.copy_(scratch, non_blocking=True)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(4):
+            ch.copy_(scratch, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ceiling = 4 * (1 << 30) / (c0.elapsed_time(c1) / 1e3) / 1e9
         e2e = {"value": draws_step * world / (e2e_ms / 1e3), "unit": "draws/s",
                "h2d_bytes_per_step": 24, "d2h_bytes_per_step": bytes_step, "ms_per_step": e2e_ms,
-               "d2h_gbs": bytes_step / (e2e_ms / 1e3) / 1e9}
+               "d2h_gbs": bytes_step / (e2e_ms / 1e3) / 1e9, "d2h_copy_ceiling_gbs": ceiling,
+               "frac_of_copy_ceiling": bytes_step / (e2e_ms / 1e3) / 1e9 / ceiling}
         del host, scratch
 
     # fused no-store consumer: 2^20 streams x 4096 draws -> count and sum
