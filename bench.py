@@ -680,10 +680,25 @@ def run_gpu(args):
         c1.record(stream)
         torch.cuda.synchronize()
         ceiling = 4 * (1 << 30) / (c0.elapsed_time(c1) / 1e3) / 1e9
+        # where pinned memory can live: the NUMA nodes this process sees and
+        # the GPU's own node (sysfs)
+        numa_nodes = len([n for n in os.listdir("/sys/devices/system/node")
+                          if n.startswith("node") and n[4:].isdigit()]) \
+            if os.path.isdir("/sys/devices/system/node") else None
+        gpu_node = None
+        try:
+            bus = torch.cuda.get_device_properties(dev)
+            path = (f"/sys/bus/pci/devices/{bus.pci_domain_id:04x}:{bus.pci_bus_id:02x}:"
+                    f"{bus.pci_device_id:02x}.0/numa_node")
+            with open(path) as f:
+                gpu_node = int(f.read().strip())
+        except (OSError, ValueError, AttributeError):
+            pass
         e2e = {"value": draws_step * world / (e2e_ms / 1e3), "unit": "draws/s",
                "h2d_bytes_per_step": 24, "d2h_bytes_per_step": bytes_step, "ms_per_step": e2e_ms,
                "d2h_gbs": bytes_step / (e2e_ms / 1e3) / 1e9, "d2h_copy_ceiling_gbs": ceiling,
-               "frac_of_copy_ceiling": bytes_step / (e2e_ms / 1e3) / 1e9 / ceiling}
+               "frac_of_copy_ceiling": bytes_step / (e2e_ms / 1e3) / 1e9 / ceiling,
+               "numa_nodes_visible": numa_nodes, "gpu_numa_node": gpu_node}
         del host, scratch
 
     # fused no-store consumer: 2^20 streams x 4096 draws -> count and sum
