@@ -151,3 +151,44 @@ def test_static_batch_refuses_requests_before_any_device_work():
     assert b"16384" in L.mrg_last_error()
     # an empty call is a no-op that touches nothing
     assert _static_call([mrg._Request(0, 0, 0, 0, mrg.UNIFORM, mrg.F64, 1.0, None)]) == mrg.OK
+
+
+def test_grf_argument_errors():
+    P = mrg.MaternParams
+    good = (P * 1)(P(1.25, 50e3, 1.5, 1.0, 0.0))
+    nb = L.mrg_grf_matern_scratch_bytes(1, 4, 5)
+    assert nb == 4096 + 7 * 9 * 8
+    r = L.mrg_grf_matern_raster
+    assert r(None, 1, 4, 5, 4000.0, FAKE, 20, FAKE, nb, None) == mrg.EINVAL
+    assert r(good, 0, 4, 5, 4000.0, FAKE, 20, FAKE, nb, None) == mrg.EINVAL       # empty batch
+    assert r(good, 65, 4, 5, 4000.0, FAKE, 20, FAKE, 1 << 30, None) == mrg.EINVAL  # batch > 64
+    assert r(good, 1, 4, 5, 4000.0, FAKE, 19, FAKE, nb, None) == mrg.EINVAL       # ld < n
+    assert r(good, 1, 4, 5, 0.0, FAKE, 20, FAKE, nb, None) == mrg.EINVAL          # cell
+    assert r(good, 1, 4, 5, 4000.0, FAKE, 20, FAKE, nb - 8, None) == mrg.EINVAL   # scratch
+    assert r(good, 1, 4, 5, 4000.0, FAKE + 8, 20, FAKE + 64, nb, None) == mrg.EINVAL  # alignment
+    assert r(good, 1, 1025, 1025, 4000.0, FAKE, 1 << 21, FAKE, 1 << 40, None) == mrg.ERANGE
+    for bad in (P(0.0, 50e3, 1.5, 1.0, 0.0), P(1.0, -1.0, 1.5, 1.0, 0.0),
+                P(1.0, 50e3, 0.0, 1.0, 0.0), P(1.0, 50e3, 1.5, 0.5, 0.0),
+                P(11.0, 50e3, 1.5, 1.0, 0.0), P(1.0, 50e3, 1.5, 1.0, float("nan"))):
+        assert r((P * 1)(bad), 1, 4, 5, 4000.0, FAKE, 20, FAKE, nb, None) == mrg.EINVAL
+    # the factorisation
+    ws = L.mrg_grf_ldl_workspace_bytes(300, 2)
+    assert ws > L.mrg_grf_ldl_workspace_bytes(300, 1) > 0
+    f = L.mrg_grf_ldl
+    assert f(None, 300, 300, 1, FAKE, FAKE, ws, None, None) == mrg.EINVAL
+    assert f(FAKE, 300, 299, 1, FAKE, FAKE, ws, None, None) == mrg.EINVAL         # lda < n
+    assert f(FAKE, 300, 300, 0, FAKE, FAKE, ws, None, None) == mrg.EINVAL         # batch 0
+    assert f(FAKE, 300, 300, 256, FAKE, FAKE, 1 << 40, None, None) == mrg.EINVAL  # batch > 255
+    assert f(FAKE, 300, 300, 2, FAKE, FAKE, ws - 1, None, None) == mrg.EINVAL     # workspace
+    assert f(FAKE, 300, 300, 2, FAKE, FAKE + 512, ws, None, None) == mrg.EINVAL   # 1024-byte alignment
+    assert f(FAKE, (1 << 20) + 1, (1 << 20) + 1, 1, FAKE, FAKE, 1 << 50, None, None) == mrg.ERANGE
+    assert f(FAKE, 0, 0, 1, FAKE, FAKE, 0, None, None) == mrg.OK                   # empty: no-op
+    # U = L D^(1/2) Z
+    sb = L.mrg_grf_simulate_scratch_bytes(300, 2, 4)
+    assert sb == 300 * 2 * 4 * 8
+    s = L.mrg_grf_simulate
+    assert s(FAKE, FAKE, 300, 300, 4, FAKE, 2, FAKE, FAKE, sb - 8, None) == mrg.EINVAL
+    assert s(FAKE, FAKE, 300, 299, 4, FAKE, 2, FAKE, FAKE, sb, None) == mrg.EINVAL
+    assert s(FAKE, FAKE + 4, 300, 300, 4, FAKE, 2, FAKE, FAKE, sb, None) == mrg.EINVAL
+    assert s(FAKE, FAKE, 300, 300, 4, FAKE, (1 << 16) + 1, FAKE, FAKE, 1 << 50, None) == mrg.ERANGE
+    assert s(FAKE, FAKE, 300, 300, 4, FAKE, 0, FAKE, FAKE, sb, None) == mrg.OK

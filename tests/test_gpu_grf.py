@@ -192,3 +192,40 @@ def test_paper_size_sampled(R):
         ref = (Lb @ y.T).T
         mag = (np.abs(Lb) @ np.abs(y.T)).T
         assert (np.abs(u[b][:, rows] - ref) <= 1e-13 * mag).all()
+
+
+def test_padded_rows_single_matrix_and_many_simulations(R):
+    """lda > n with rows that are not 32-byte aligned (the element-wise
+    epilogue path), one matrix, an odd order, and nine simulations (two passes
+    of the product kernel) -- through the C ABI directly."""
+    import ctypes
+    from paper_2201_06604_gb300 import mrg
+    rng = np.random.default_rng(9)
+    n, lda, nsim = 211, 215, 9
+    pts = rng.uniform(0, 80e3, size=(n, 2))
+    p = PARAMS[1]
+    sigma = G.matern_cov(pts, p)
+    buf = torch.zeros((1, n, lda), dtype=torch.float64, device="cuda")
+    buf[0, :, :n] = torch.tensor(sigma, device="cuda")
+    d = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    ws = R.ldl_workspace(n, 1, buf.device)
+    wp, wn = R._aligned(ws)
+    info = (ctypes.c_int32 * 1)()
+    st = torch.cuda.current_stream().cuda_stream
+    assert mrg.lib.mrg_grf_ldl(buf.data_ptr(), n, lda, 1, d.data_ptr(), wp, wn, info, st) == mrg.OK
+    assert list(info) == [0]
+    L = buf[0, :, :n].cpu().numpy()
+    D = d[0].cpu().numpy()
+    check_factor(sigma, L, D)
+    s = mrg.create_streams(nsim, seed=(12345,) * 6)
+    z = mrg.generate(s, n, "normal", torch.float64).view(1, nsim, n)
+    u = torch.empty_like(z)
+    nb = int(mrg.lib.mrg_grf_simulate_scratch_bytes(n, nsim, 1))
+    scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    assert mrg.lib.mrg_grf_simulate(buf.data_ptr(), d.data_ptr(), n, lda, 1, z.data_ptr(), nsim,
+                                    u.data_ptr(), scratch.data_ptr(), nb, st) == mrg.OK
+    Lu = np.tril(L, -1) + np.eye(n)
+    Z = z[0].cpu().numpy()
+    ref = G.simulate(Lu, D, Z.T).T
+    mag = (np.abs(Lu) @ (np.sqrt(D)[:, None] * np.abs(Z.T))).T
+    assert (np.abs(u[0].cpu().numpy() - ref) <= 1e-13 * mag + 1e-300).all()
