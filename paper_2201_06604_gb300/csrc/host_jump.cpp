@@ -116,21 +116,26 @@ void split(double v, float& hi, float& lo) {
 void transform_table_for(double M, double D, float out[kTransformEntries][4]) {
   // log buckets: centre C_k of the zn-range [2^31 + k 2^24, 2^31 + (k+1) 2^24),
   // the top bucket centred at M so that ln(C_127 / M) = 0 exactly.
+  float* inv = &out[0][0];
   for (int k = 0; k < 128; ++k) {
     const double C = k == 127 ? M : 2147483648.0 + (2.0 * k + 1.0) * 8388608.0;
-    split(1.0 / C, out[k][0], out[k][1]);
-    split(std::log1p((C - M) / M), out[k][2], out[k][3]);
+    split(1.0 / C, inv[2 * k], inv[2 * k + 1]);
   }
-  // trig buckets: a_j = (pi/2) j 2^23 / D (a_0 = 0 exactly)
+  // trig buckets: a_j = (pi/2) j 2^23 / D (a_0 = 0 exactly), each entry in
+  // kTransformTrigCopies identical copies side by side
   for (int j = 0; j < 65; ++j) {
     const double a = (M_PI / 2) * ((j * 8388608.0) / D);
-    split(std::sin(a), out[128 + j][0], out[128 + j][1]);
-    split(std::cos(a), out[128 + j][2], out[128 + j][3]);
+    for (int c = 0; c < kTransformTrigCopies; ++c) {
+      float* e = out[64 + kTransformTrigCopies * j + c];
+      split(std::sin(a), e[0], e[1]);
+      split(std::cos(a), e[2], e[3]);
+    }
   }
   // ln(C_k / (M 2^s)) = ln(C_k / M) - s ln 2 for every shift s and bucket k,
-  // as float pairs from entry 193 on (pair 128 s + k); one fused multiply-add
-  // (explicit, so that no compiler contracts it differently on another host)
-  float* ls = &out[193][0];
+  // as float pairs after the trig entries (pair 128 s + k); one fused
+  // multiply-add (explicit, so that no compiler contracts it differently on
+  // another host)
+  float* ls = &out[64 + 65 * kTransformTrigCopies][0];
   for (int sh = 0; sh < 32; ++sh)
     for (int k = 0; k < 128; ++k) {
       const double C = k == 127 ? M : 2147483648.0 + (2.0 * k + 1.0) * 8388608.0;

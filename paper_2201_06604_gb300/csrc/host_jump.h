@@ -19,12 +19,15 @@ void jump_pow2_multiple(uint32_t s[6], uint64_t e, int base);
 // True when RN64(1/(m1+1)) has exponent -32 and significand 2^52 + delta.
 bool norm_constant_ok(uint64_t delta);
 
-// Tables of the double-float transforms (layout in transforms_df.cuh):
-// entries [0, 128): 1/C_k and ln(C_k / M) for the log buckets;
-// entries [128, 193): sin and cos of the bucket angles a_j;
-// entries [193, 2241): ln(C_k / (M 2^s)) for every shift s < 32 and bucket k,
-// as 4096 float pairs.
-constexpr int kTransformEntries = 193 + 2048;
+// Tables of the double-float transforms (layout in transforms_df.cuh), in
+// units of four floats:
+// entries [0, 64): 1/C_k for the 128 log buckets, as float pairs;
+// entries [64, 584): sin and cos of the bucket angles a_j, eight copies of
+// each of the 65 entries side by side;
+// entries [584, 2632): ln(C_k / (M 2^s)) for every shift s < 32 and bucket
+// k, as 4096 float pairs.
+constexpr int kTransformTrigCopies = 8;
+constexpr int kTransformEntries = 64 + 65 * kTransformTrigCopies + 2048;
 void transform_table(float out[kTransformEntries][4]);
 
 // The same tables for uniforms u = z' / 2^32 (M = 2^32, quarter turn D = 2^30):

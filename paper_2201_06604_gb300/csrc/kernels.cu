@@ -5,7 +5,9 @@
 //   jump_kernel      x <- A^k x for every stream (skip, substreams, advance)
 //   generate_kernel  the recurrence in registers + transform + 32-byte stores
 //   fused_kernel     no-store consumer: quarter-circle count and normal sum
-//   transform_kernel the transforms of caller-provided raw draws
+//   transform_kernel the transforms of caller-provided raw draws (fp64
+//                    normals into a 32-byte aligned output:
+//                    transform_normal_f64_x2_kernel, two pairs per thread)
 //   fill_kernel      write-only stream (the write ceiling generate is held to)
 //   matrix_kernel    the paper's work-item matrix layout (matrix_kernels.cuh)
 //   fisher_kernel    Monte Carlo Fisher's exact test (fisher_kernels.cuh)
@@ -18,6 +20,9 @@
 // the recurrence in registers.  Segment q of the flattened index runs stream
 // q mod ns at segment q div ns, so the 32 lanes of a warp share the segment
 // offset whenever ns >= 32 and the jump's table reads are warp-uniform.
+// fp64 normals are transformed two pairs at a time with packed fp32x2
+// instructions (transforms_x2.cuh) when a unit holds two pairs (32-byte
+// stores), else one pair at a time; the results are bit-identical.
 // Each lane's outputs are contiguous in its row, so a lane stores whole
 // 32-byte sectors with one 256-bit st.global per 32 bytes: the L2 receives
 // full-sector writes and nothing is staged in shared memory.  (Staged
@@ -31,9 +36,11 @@
 #include <algorithm>
 #include <mutex>
 
+#include "host_jump.h"
 #include "internal.h"
 #include "mrg32k3a_core.cuh"
 #include "transforms_df.cuh"
+#include "transforms_x2.cuh"
 
 #define MRG_RAW 0
 #define MRG_UNIFORM 1
@@ -54,6 +61,9 @@ cudaError_t upload_tables(const uint32_t* tab, size_t bytes) {
   if (bytes != sizeof(c_jump)) return cudaErrorInvalidValue;
   return cudaMemcpyToSymbol(c_jump, tab, bytes);
 }
+
+static_assert(TAB_ENTRIES == host::kTransformEntries && TRIG_COPIES == host::kTransformTrigCopies,
+              "transform table layout of the host builder and the kernels");
 
 cudaError_t upload_transform_table(const float* tab, size_t bytes) {
   if (bytes != sizeof(g_ttab)) return cudaErrorInvalidValue;
@@ -197,6 +207,21 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
 #pragma unroll
     for (int e = 0; e < UE; ++e)
       w[e] = uniform_bits32(step_fast(s, c.k1, c.k2));
+  } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F64 && UE % 4 == 0) {
+    // two pairs per packed fp32x2 evaluation (bit-identical to the scalar one)
+#pragma unroll
+    for (int p = 0; p < UE / 4; ++p) {
+      const uint32_t z1a = step_fast(s, c.k1, c.k2);
+      const uint32_t z2a = step_fast(s, c.k1, c.k2);
+      const uint32_t z1b = step_fast(s, c.k1, c.k2);
+      const uint32_t z2b = step_fast(s, c.k1, c.k2);
+      uint64_t xa, ya, xb, yb;
+      box_muller_f64_x2<UM32k3a>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
+      put_f64(w + 8 * p, xa);
+      put_f64(w + 8 * p + 2, ya);
+      put_f64(w + 8 * p + 4, xb);
+      put_f64(w + 8 * p + 6, yb);
+    }
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
@@ -423,6 +448,40 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
         uint32_t* d = reinterpret_cast<uint32_t*>(out + i * ES);
         d[0] = w[e * ES / 4];
         if (ES == 8) d[1] = w[e * ES / 4 + 1];
+      }
+    }
+  }
+}
+
+// fp64 normals into a 32-byte aligned output: each thread transforms four
+// draws (two pairs) with the packed evaluation and stores 32 bytes; a last
+// unit of fewer than four draws takes the scalar one (bit-identical results
+// either way; the launcher picks this kernel by the output's alignment, so
+// both evaluations are reachable through the same entry point).
+__global__ void __launch_bounds__(256) transform_normal_f64_x2_kernel(const uint32_t* __restrict__ z,
+                                                                     uint64_t n, char* out) {
+  __shared__ float4 s_tab[TAB_ENTRIES];
+  load_ttab(s_tab);
+  const uint64_t units = (n + 3) / 4;
+  const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += step_all) {
+    const uint64_t i0 = 4 * u;
+    uint64_t* d = reinterpret_cast<uint64_t*>(out) + i0;
+    if (i0 + 4 <= n) {
+      uint32_t w[8];
+      uint64_t xa, ya, xb, yb;
+      box_muller_f64_x2<UM32k3a>(z[i0], z[i0 + 1], z[i0 + 2], z[i0 + 3], s_tab, xa, ya, xb, yb);
+      put_f64(w, xa);
+      put_f64(w + 2, ya);
+      put_f64(w + 4, xb);
+      put_f64(w + 6, yb);
+      store_vec<32>(reinterpret_cast<char*>(d), w);
+    } else {
+      for (uint64_t i = i0; i < n; i += 2) {
+        uint64_t x, y;
+        box_muller_f64(z[i], i + 1 < n ? z[i + 1] : 1u, s_tab, x, y);
+        d[i - i0] = x;
+        if (i + 1 < n) d[i + 1 - i0] = y;
       }
     }
   }
@@ -856,6 +915,7 @@ cudaError_t preload_kernels() {
   load_fn(jump31_kernel, bad);
   load_fn(jump_kernel, bad);
   load_fn(fused_kernel, bad);
+  load_fn(transform_normal_f64_x2_kernel, bad);
   load_fn(batch_kernel, bad);
   load_fn(serve_kernel, bad);
   return bad ? cudaErrorInvalidDeviceFunction : cudaSuccess;
@@ -888,9 +948,13 @@ cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype,
     c.ir_hi = (float)ir;
     c.ir_lo = (float)(ir - (double)c.ir_hi);
   }
+  char* o = reinterpret_cast<char*>(out);
+  if (dist == MRG_NORMAL && dtype == MRG_F64 && (reinterpret_cast<uintptr_t>(out) & 31) == 0) {
+    transform_normal_f64_x2_kernel<<<grid_for((n + 3) / 4, 256, 8), 256, 0, st>>>(z, n, o);
+    return after_launch();
+  }
   const uint64_t units = dist == MRG_NORMAL ? (n + 1) / 2 : n;
   const unsigned grid = grid_for(units, 256, 8);
-  char* o = reinterpret_cast<char*>(out);
   switch (dist * 4 + dtype) {
     case MRG_UNIFORM * 4 + MRG_F32: transform_kernel<MRG_UNIFORM, MRG_F32><<<grid, 256, 0, st>>>(z, n, o, c); break;
     case MRG_UNIFORM * 4 + MRG_F64: transform_kernel<MRG_UNIFORM, MRG_F64><<<grid, 256, 0, st>>>(z, n, o, c); break;

@@ -43,20 +43,37 @@ struct df {
   float hi, lo;
 };
 
-// Table layout (float4 entries), built on the host (host_jump.cpp) and
-// copied to shared memory by every block that transforms (35.9 KB):
-//   [0, 128)   log:  (1/C_k).hi, (1/C_k).lo, ln(C_k/M).hi, ln(C_k/M).lo
-//   [128, 193) trig: sin(a_j).hi, sin(a_j).lo, cos(a_j).hi, cos(a_j).lo
-//   [193, 2241) as 4096 float pairs: ln(C_k / (M 2^s)).hi, .lo at pair
-//              128 s + k (one load replaces -s ln 2 and its error-free sum)
+// Table layout (float4 units), built on the host (host_jump.cpp) and
+// copied to shared memory by every block that transforms (42.1 KB):
+//   [0, 64)      log: 128 float pairs (1/C_k).hi, (1/C_k).lo (pair k)
+//   [64, 584)    trig: sin(a_j).hi, sin(a_j).lo, cos(a_j).hi, cos(a_j).lo,
+//                eight copies of each entry side by side (entry j, copy c
+//                at 64 + 8 j + c).  A 16-byte load serves a quarter warp
+//                (8 lanes, 32 banks) per shared-memory wavefront; lane l
+//                reads copy l mod 8, which sits in banks 4c .. 4c + 3 for
+//                every j, so the lane-divergent lookup never conflicts (one
+//                copy cost ~2.6 wavefronts per quarter warp).
+//   [584, 2632)  4096 float pairs: ln(C_k / (M 2^s)).hi, .lo at pair
+//                128 s + k (one load replaces -s ln 2 and its error-free sum)
 constexpr int TAB_LOG = 0;
-constexpr int TAB_TRIG = 128;
-constexpr int TAB_LS = 193;
-constexpr int TAB_ENTRIES = 193 + 2048;
+constexpr int TAB_TRIG = 64;
+constexpr int TRIG_COPIES = 8;
+constexpr int TAB_LS = TAB_TRIG + 65 * TRIG_COPIES;
+constexpr int TAB_ENTRIES = TAB_LS + 2048;
+
+// 1 / C_k as a float pair.
+__device__ __forceinline__ float2 log_inv_ck(const float4* __restrict__ tab, uint32_t k) {
+  return reinterpret_cast<const float2*>(tab + TAB_LOG)[k];
+}
 
 // ln(C_k / (M 2^s)) as a float pair.
 __device__ __forceinline__ float2 log_ck_shift(const float4* __restrict__ tab, uint32_t s, uint32_t k) {
   return reinterpret_cast<const float2*>(tab + TAB_LS)[(s << 7) | k];
+}
+
+// sin(a_j) and cos(a_j) as float pairs, from this lane's copy.
+__device__ __forceinline__ float4 trig_entry(const float4* __restrict__ tab, uint32_t j) {
+  return tab[TAB_TRIG + j * TRIG_COPIES + (threadIdx.x & (TRIG_COPIES - 1))];
 }
 
 // The modulus M of the uniform u = z / M that the transforms take, with the
@@ -142,7 +159,7 @@ __device__ __forceinline__ df ln_u_df_m(uint32_t z, const float4* __restrict__ t
   const uint32_t k = (zn >> 24) & 127u;
   const uint32_t ck = k == 127u ? UM::TOP_CK : 0x80800000u + (k << 24);
   const int32_t d = (int32_t)(zn - ck);                 // |d| < 2^24: exact in fp32
-  const float4 T = tab[TAB_LOG + k];
+  const float2 T = log_inv_ck(tab, k);
   // r = d / C_k as the exact leading product plus the rest (not
   // renormalised: every use below takes both parts)
   const float dfl = (float)d;
@@ -179,7 +196,7 @@ __device__ __forceinline__ df ln_u_lite_raw_m(uint32_t z, const float4* __restri
   const uint32_t k = (zn >> 24) & 127u;
   const uint32_t ck = k == 127u ? UM::TOP_CK : 0x80800000u + (k << 24);
   const float df_ = (float)(int32_t)(zn - ck);          // |d| < 2^24: exact
-  const float4 T = tab[TAB_LOG + k];
+  const float2 T = log_inv_ck(tab, k);
   const float rh = __fmul_rn(T.x, df_);
   const float re = __fmaf_rn(T.y, df_, __fmaf_rn(T.x, df_, -rh));   // r = rh + re
   // ln(1 + r) - r = r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 - r / 6))))
@@ -222,9 +239,10 @@ __device__ __forceinline__ float df_mul_to_f32(df a, float b_hi, float b_lo) {
 // The exact reduction of the angle 2 pi z / M, z in [1, M - 1]: quadrant q
 // (z = q D + w, w in [0, D)), reflection w -> D - w above D / 2, table
 // bucket j and the bucket residual dwf (an exact float in [-2^22, 2^22)).
+// (The residual as an integer dw, |dw| <= 2^22; turn_reduce converts it.)
 template <class UM>
-__device__ __forceinline__ void turn_reduce(uint32_t z, uint32_t& q, bool& refl, uint32_t& j,
-                                            float& dwf) {
+__device__ __forceinline__ void turn_reduce_int(uint32_t z, uint32_t& q, bool& refl, uint32_t& j,
+                                                int32_t& dw) {
   constexpr uint32_t D = UM::D;  // M / 4
   q = z >> 30;
   uint32_t w = (z & 0x3FFFFFFFu) + UM::QFIX * q;  // z - q D  (q D = q 2^30 - QFIX q)
@@ -232,7 +250,15 @@ __device__ __forceinline__ void turn_reduce(uint32_t z, uint32_t& q, bool& refl,
   refl = 2u * w > D;
   const uint32_t wr = refl ? D - w : w;       // [0, D/2]
   j = (wr + 0x400000u) >> 23;                 // 0..64
-  dwf = small_int_to_float((int32_t)(wr - (j << 23)));
+  dw = (int32_t)(wr - (j << 23));
+}
+
+template <class UM>
+__device__ __forceinline__ void turn_reduce(uint32_t z, uint32_t& q, bool& refl, uint32_t& j,
+                                            float& dwf) {
+  int32_t dw;
+  turn_reduce_int<UM>(z, q, refl, j, dw);
+  dwf = small_int_to_float(dw);
 }
 
 // |sin| and |cos| of 2 pi z / M for z in [1, M - 1], with their signs as
@@ -247,14 +273,15 @@ __device__ __forceinline__ void sincos_turn_df_m(uint32_t z, const float4* __res
   const df delta = df_mul_f(df{UM::PID_HI, UM::PID_LO}, dwf);
   const float dh = delta.hi;
   const float d2 = __fmul_rn(dh, dh);
-  // sin(delta) = delta + delta^3 (-1/6 + delta^2 / 120)
-  const float sc = __fmul_rn(__fmul_rn(dh, d2), __fmaf_rn(d2, 1.0f / 120.0f, -1.0f / 6.0f));
-  const df sd = fast_two_sum(dh, __fadd_rn(delta.lo, sc));
+  // sin(delta) = delta + delta^3 (-1/6 + delta^2 / 120), the cubic term
+  // added to delta.lo in the same rounding as its last product (one FMA)
+  const float sd_lo = __fmaf_rn(__fmul_rn(dh, d2), __fmaf_rn(d2, 1.0f / 120.0f, -1.0f / 6.0f), delta.lo);
+  const df sd = fast_two_sum(dh, sd_lo);
   // cos(delta) - 1 = -delta^2/2 + delta^4 (1/24 - delta^2 / 720)
   const float e2 = __fmaf_rn(2.0f * dh, delta.lo, __fmaf_rn(dh, dh, -d2));
   const float cc = __fmul_rn(__fmul_rn(d2, d2), __fmaf_rn(d2, -1.0f / 720.0f, 1.0f / 24.0f));
   const df cm1 = fast_two_sum(-0.5f * d2, __fmaf_rn(-0.5f, e2, cc));
-  const float4 T = tab[TAB_TRIG + j];
+  const float4 T = trig_entry(tab, j);
   const df sj{T.x, T.y}, cj{T.z, T.w};
   // sin(a + d) = sj + cj sin d + sj (cos d - 1);  cos(a + d) = cj - sj sin d + cj (cos d - 1).
   // |sin d| <= 0.0062 and |cos d - 1| <= 2e-5, so each product is formed as
@@ -374,7 +401,7 @@ __device__ __forceinline__ void sincos_turn_lite_m(uint32_t z, const float4* __r
   const float sdl = __fmaf_rn(__fmul_rn(dh, d2), __fmaf_rn(d2, 1.0f / 120.0f, -1.0f / 6.0f), dl);
   // cos d - 1 = d^2 (-1/2 + d^2 (1/24 - d^2 / 720))
   const float cm1 = __fmul_rn(d2, __fmaf_rn(d2, __fmaf_rn(d2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
-  const float4 T = tab[TAB_TRIG + j];
+  const float4 T = trig_entry(tab, j);
   df sp, cp;
   {  // sj + cj sin d + sj (cos d - 1); |sj.hi| >= |cj.hi dh| or sj = 0
     const float p = __fmul_rn(T.z, dh);

@@ -136,3 +136,37 @@ def test_odd_normal_count_and_zero_crossings(mrg):
     ref = O.box_muller_of(np.array([12345, D, 777, 3 * D, 5, 1], dtype=np.uint32))[:5]
     assert got[0] == 0.0 and got[2] == 0.0
     assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_normal_f64_packed_and_scalar_evaluations_identical(mrg):
+    # A 32-byte aligned fp64 output takes the packed two-pair evaluation, a
+    # misaligned one the scalar one-pair evaluation: bit-identical outputs on
+    # random draws and on every reduction boundary (the accuracy tests above
+    # check the aligned path against the oracle).
+    z = all_inputs(n_random=1 << 20)
+    zt = torch.from_numpy(z.view(np.int32)).cuda()
+    n = z.size
+    aligned = mrg.transform(zt, "normal", torch.float64)
+    assert aligned.data_ptr() % 32 == 0
+    big = torch.full((n + 5,), -7.0, dtype=torch.float64, device="cuda")
+    shifted = big[1:n + 1]
+    assert shifted.data_ptr() % 32 != 0
+    mrg.transform(zt, "normal", torch.float64, out=shifted)
+    a = aligned.cpu().numpy().view(np.uint64)
+    b = shifted.cpu().numpy().view(np.uint64)
+    assert np.array_equal(a, b), np.argwhere(a != b)[:5]
+    assert big[0].item() == -7.0 and (big[n + 1:] == -7.0).all()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 9, 1001, 4099])
+def test_normal_f64_packed_tails(mrg, n):
+    # counts that end inside a unit of four draws: the last pair (or the
+    # lone last draw, whose pair partner is taken as 1) goes the scalar way
+    z = all_inputs(n_random=4096, seed=n)[:n]
+    zt = torch.from_numpy(z.view(np.int32)).cuda()
+    big = torch.full((n + 8,), -7.0, dtype=torch.float64, device="cuda")
+    got = mrg.transform(zt, "normal", torch.float64, out=big[:n])
+    zz = np.concatenate([z, np.ones(n % 2, dtype=np.uint32)])
+    ref = O.box_muller_of(zz)[:n]
+    assert np.abs(got.cpu().numpy() - ref).max() <= 1e-12
+    assert (big[n:] == -7.0).all()

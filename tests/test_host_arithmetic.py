@@ -7,8 +7,9 @@ own header and checked on the CPU (no GPU needed):
 * the same for MRG31k3p, the paper's own generator: its exact fp64 uniform
   z / 2^31 and fp32 rounding for every z, and its step against the oracle;
 * every entry of the transform tables the library builds on the host (1/C_k,
-  ln(C_k / M), sin and cos of the bucket angles, ln(C_k / (M 2^s)) for all
-  shifts), as float pairs, against 50-digit values from mpmath;
+  sin and cos of the bucket angles in each of their eight copies,
+  ln(C_k / (M 2^s)) for all shifts), as float pairs, against 50-digit values
+  from mpmath;
 * the device Matern correlation's Bessel function (matern.cuh, compiled for
   the host) against scipy's exponentially scaled K and the Matern
   correlation against the GRF oracle.
@@ -121,19 +122,23 @@ def test_transform_tables_against_high_precision(harness):
         tab = tabs[t]
         D = M // 4
         C = [M if k == 127 else (1 << 31) + (2 * k + 1) * (1 << 23) for k in range(128)]
+        # layout in units of four floats: [0, 64) 1/C_k as 128 pairs;
+        # [64, 584) 65 trig entries, 8 identical copies each; [584, 2632)
+        # ln(C_k / (M 2^s)) as 4096 pairs
+        assert len(tab) == 64 + 65 * 8 + 2048
         for k in range(128):
-            e = tab[k]
+            e = tab[k // 2][2 * (k % 2):2 * (k % 2) + 2]
             assert close(e[0], e[1], mp.mpf(1) / C[k]), (t, k)
-            assert close(e[2], e[3], mp.log(mp.mpf(C[k]) / M)), (t, k)
         for j in range(65):
             a = mp.pi / 2 * j * (1 << 23) / D
-            e = tab[128 + j]
+            e = tab[64 + 8 * j]
             assert close(e[0], e[1], mp.sin(a)), (t, j)
             assert close(e[2], e[3], mp.cos(a)), (t, j)
+            assert all(tab[64 + 8 * j + c] == e for c in range(1, 8)), (t, j)
         for s in range(32):
             for k in range(128):
                 i = 128 * s + k
-                e = tab[193 + i // 2][2 * (i % 2):2 * (i % 2) + 2]
+                e = tab[584 + i // 2][2 * (i % 2):2 * (i % 2) + 2]
                 assert close(e[0], e[1], mp.log(mp.mpf(C[k]) / (mp.mpf(M) * 2 ** s))), (t, s, k)
 
 
