@@ -32,13 +32,14 @@ DTYPE_NOTE = ("exact 32-bit integer recurrence; uniforms formed in integers; nor
               "exponentials in double-float (fp32 pairs); fp64 and fp32 outputs")
 
 # Warp-level instructions issued per output by generate_kernel, measured with
-# ncu (smsp__inst_executed.sum x 32 / outputs) on 16384 streams x 4096 draws.
-# These kernels are bound by instruction issue (the FP64 pipe is not used and
-# the recurrence is integer multiply-add work), so the dominant kernel's
-# roofline is issue slots: 4 warp-instructions per cycle per SM.
+# ncu (smsp__inst_executed.sum x 32 / outputs) on 16384 streams x 4096 draws
+# (profiles/generate_issue_mix_16384x4096.txt).  These kernels are bound by
+# instruction issue or by the IMAD (fmaheavy) pipe (the FP64 pipe is not used
+# and the recurrence is integer multiply-add work), so beside the HBM
+# roofline the bench reports issue slots: 4 warp-instructions per cycle per SM.
 INSTR_PER_OUTPUT = {("raw", "u32"): 27.4, ("uniform", "f64"): 43.0, ("uniform", "f32"): 37.5,
-                    ("normal", "f64"): 134.2, ("normal", "f32"): 88.6,
-                    ("exponential", "f32"): 63.8, ("exponential", "f64"): 106.7}
+                    ("normal", "f64"): 117.5, ("normal", "f32"): 91.2,
+                    ("exponential", "f32"): 64.7, ("exponential", "f64"): 107.9}
 
 
 def env_rank():
@@ -176,10 +177,11 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 # DRAM bytes (read + write) per output of generate_kernel, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) on 65536 streams x 4096 draws.
+# (dram__bytes_read.sum + dram__bytes_write.sum) on 65536 streams x 4096 draws
+# (profiles/generate_dram_traffic_65536x4096.txt).
 TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.824, ("uniform", "f32"): 3.814,
-                      ("normal", "f64"): 7.817, ("normal", "f32"): 3.809,
-                      ("exponential", "f32"): 3.810}
+                      ("normal", "f64"): 7.829, ("normal", "f32"): 3.817,
+                      ("exponential", "f32"): 3.813}
 
 
 def roofline(dom, hbm, peak_kind, issue_peak, total_out, sm_count):
