@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/mrg32k3a.h"
 #include "grf_kernels.cuh"
@@ -129,7 +130,10 @@ dim3 grid_of(const GemmArgs& g) {
 
 int after(cudaError_t e, const char* what) {
   if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) return mrg::set_error(MRG_ECUDA, what);
+  if (e != cudaSuccess) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return mrg::set_error(MRG_ECUDA, msg.c_str());
+  }
   mrg::g_launches.fetch_add(1, std::memory_order_relaxed);
   return MRG_OK;
 }

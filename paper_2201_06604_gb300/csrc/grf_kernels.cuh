@@ -258,13 +258,12 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// The products on the tensor cores.  One CTA (128 threads) per 128 x 64
-// output tile: thread 0 bulk-copies the B block's S slices and streams the A
-// block's slices through a ring of NST stages, issuing for A slice p the
-// MMAs with B slices q = 0 .. S-1-p into TMEM accumulator p + q (64 columns
-// each, S x 64 <= 512); then all four warps read the accumulators, combine
-// the levels exactly and write (PANEL: C = product) or subtract (TRAIL:
-// C -= product) in fp64.
+// The products on the tensor cores, on 128 x 64 output tiles: the B block's
+// S slices stay in shared memory while the A block's slices stream through a
+// ring of NST stages; A slice p meets B slices q = 0 .. S-1-p in TMEM
+// accumulator p + q (64 columns each, S x 64 <= 512); the accumulators are
+// combined exactly and the result written (PANEL: C = product) or subtracted
+// (TRAIL: C -= product) in fp64.
 // ---------------------------------------------------------------------------
 
 struct GemmArgs {
@@ -295,8 +294,9 @@ struct GemmSmem {
   static constexpr uint32_t B_BYTES = (uint32_t)S * SLICE_B;
   static constexpr uint32_t A_OFF = B_BYTES;
   static constexpr uint32_t BAR_OFF = A_OFF + NST * SLICE_A;
-  static constexpr uint32_t EB_OFF = BAR_OFF + 128;                // exponents of the tile's B rows
-  static constexpr uint32_t TOTAL = EB_OFF + 256 + 1024;          // + alignment slack
+  // mbarriers: full_b, full_a[NST], empty_a[NST], level[S], tmem_free; then
+  // the TMEM base address and the abort flag
+  static constexpr uint32_t TOTAL = BAR_OFF + 256 + 1024;         // + alignment slack
 };
 
 // Tile (ti, tj) of the lower-triangular tile set of an m x m output with
@@ -349,35 +349,61 @@ __device__ __forceinline__ void st_v4f64(double* p, const double* v) {
                : "memory");
 }
 
-constexpr int GEMM_THREADS = 512;   // warp 0 lane 0 issues copies and MMAs; all 16 warps drain TMEM
-constexpr int EPI_COLS = BN * 4 / (GEMM_THREADS / 32);   // columns per thread in the epilogue (16)
+// Warps 0-15 drain TMEM (warp w reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31,
+// as tcgen05.ld requires); warp 16 allocates TMEM and its lane 0 issues the
+// copies and the MMAs.  (The runtime charges a block's registers in groups of
+// four warps, so 17 warps leave 96 registers per thread, as measured.)
+constexpr int EPI_WARPS = 16;
+constexpr int PRODUCER_WARP = EPI_WARPS;
+constexpr int GEMM_THREADS = (EPI_WARPS + 1) * 32;
+constexpr int EPI_COLS = BN * 4 / EPI_WARPS;   // columns per epilogue thread (16)
 
-// The tile (ti, tj) of item x of the tile set (identical for every thread).
+// The tile (ti, tj) of item x of the tile set (identical for every thread),
+// column by column: consecutive items share their column of tiles and so
+// their B block, which a CTA then loads once for its whole run of them.
 __device__ __forceinline__ void tile_of(const GemmArgs& g, bool trail, uint32_t x, uint32_t& ti,
                                         uint32_t& tj) {
+  const uint32_t rows = (g.m + BM - 1) / BM;   // tile rows of the output
   if (trail && g.tile_set == TILES_REST) {
-    // lower tiles right of the next panel (tj >= 2): row ti >= 1 holds
-    // 2 ti of them, the rows before it ti (ti - 1) in all
-    uint32_t t = (uint32_t)((1.0f + sqrtf(4.0f * (float)x + 1.0f)) * 0.5f);
-    while ((uint64_t)t * (t - 1) > x) --t;
-    while ((uint64_t)(t + 1) * t <= x) ++t;
-    ti = t;
-    tj = 2 + x - t * (t - 1);
+    // lower tiles right of the next panel: column tj >= 2 holds the tile rows
+    // ti >= tj / 2 (64 tj < 128 (ti + 1)), rows - tj / 2 of them; columns
+    // 2 m and 2 m + 1 hold rows - m each, so (m - 1)(2 rows - m) items
+    // precede column 2 m: solve for m, then place x in the pair
+    const float bq = 2.0f * (float)rows + 1.0f;
+    const float disc = fmaxf(bq * bq - 4.0f * (2.0f * (float)rows + (float)x), 0.0f);
+    uint32_t m = max((uint32_t)((bq - sqrtf(disc)) * 0.5f), 1u);
+    auto before = [rows](uint32_t mm) { return (mm - 1) * (2 * rows - mm); };
+    while (m + 1 <= rows && before(m + 1) <= x) ++m;
+    while (m > 1 && before(m) > x) --m;
+    const uint32_t y = x - before(m);
+    if (y < rows - m) {
+      tj = 2 * m;
+      ti = m + y;
+    } else {
+      tj = 2 * m + 1;
+      ti = m + y - (rows - m);
+    }
   } else if (trail && g.tile_set == TILES_LOWER) {
     lower_tile(x, ti, tj);
   } else {   // a rectangle of tiles_n columns of tiles (the panel; the next panel of a trailing update)
-    ti = x / g.tiles_n;
-    tj = x % g.tiles_n;
+    ti = x % rows;
+    tj = x / rows;
   }
 }
 
 // One CTA takes `per_cta` consecutive items of the flat set (matrix-major:
-// item = b * tiles + x) -- a chunk of persistence: while its 16 warps drain
-// one tile's accumulators, the next tile's operands are already on their way
-// into shared memory (the MMAs of the finished tile have released it).
-// Thread 0 of warp 0 issues the copies and the MMAs; the MMA issue is fully
-// unrolled over precomputed descriptors (one tcgen05.mma per instruction
-// slot, not a descriptor computation each).
+// item = b * tiles + x).  Warp 16 produces: its lane 0 streams the A block's
+// slices through a ring of NST stages without a break between tiles (the
+// next tile's first slices load while this tile's last ones multiply),
+// reloads the B block only when the tile column changes, and issues for A
+// slice p the MMAs with B slices q = 0 .. S-1-p into TMEM accumulator p + q.
+// Level l (accumulator l) receives its last product from slice l, so after
+// slice p's MMAs a commit on level[p] marks level p final; the 16 epilogue
+// warps read and fold level l while slices l+1 .. S-1 multiply, release TMEM
+// after the last level (tmem_free), and round and store the tile while the
+// next tile's MMAs run.  The MMA issue is fully unrolled over precomputed
+// descriptors.  Every wait is bounded; after a timeout the producer keeps
+// committing (empty) level barriers so that no warp waits out more bounds.
 template <int S, bool TRAIL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g) {
   using SM = GemmSmem<S>;
@@ -389,13 +415,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   uint8_t* sB = smem;
   uint8_t* sA = smem + SM::A_OFF;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::BAR_OFF);
-  uint64_t* full_b = bar;                 // [1]
-  uint64_t* full_a = bar + 1;             // [NST]
-  uint64_t* empty_a = bar + 1 + NST;      // [NST]
-  uint64_t* done = bar + 1 + 2 * NST;     // [1]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + 2 * NST);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 3 + 2 * NST);
-  int* s_eb = reinterpret_cast<int*>(smem + SM::EB_OFF);
+  uint64_t* full_b = bar;                     // [1]
+  uint64_t* full_a = bar + 1;                 // [NST]
+  uint64_t* empty_a = bar + 1 + NST;          // [NST]
+  uint64_t* level = bar + 1 + 2 * NST;        // [S]
+  uint64_t* tmem_free = level + S;            // [1], EPI_WARPS arrivals per tile
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tmem_free + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_free + 2);
 
   const uint64_t total = (uint64_t)g.tiles_total * g.batch;
   const uint64_t it0 = (uint64_t)blockIdx.x * g.per_cta;
@@ -409,78 +435,75 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
       tc::mbar_init(&full_a[i], 1);
       tc::mbar_init(&empty_a[i], 1);
     }
-    tc::mbar_init(done, 1);
+    for (int l = 0; l < S; ++l) tc::mbar_init(&level[l], 1);
+    tc::mbar_init(tmem_free, EPI_WARPS);
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 512);
+  if (warp == PRODUCER_WARP) tc::tmem_alloc(tslot, 512);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // thread 0's barrier phase bookkeeping: completed loads / commits per stage
-  uint32_t fcnt[NST] = {0, 0, 0}, ecnt[NST] = {0, 0, 0};
-  auto item_ptrs = [&](uint64_t it, const uint8_t*& gA, const uint8_t*& gB) {
-    const uint32_t b = (uint32_t)(it / g.tiles_total);
-    uint32_t ti, tj;
-    tile_of(g, TRAIL, (uint32_t)(it - (uint64_t)b * g.tiles_total), ti, tj);
-    gA = g.img_a + b * g.img_a_mstride + (uint64_t)ti * S * SLICE_A;
-    gB = g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B;
-  };
-  // the first tile's B block and A slices 0 .. NST-1
-  if (threadIdx.x == 0) {
-    const uint8_t *gA, *gB;
-    item_ptrs(it0, gA, gB);
-    tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
-    tc::bulk_g2s(sB, gB, SM::B_BYTES, full_b);
-#pragma unroll
-    for (int p = 0; p < NST; ++p) {
-      tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
-      tc::bulk_g2s(sA + p * SLICE_A, gA + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
-    }
-  }
-
-  const int quarter = warp & 3, part = warp >> 2;
-  const uint32_t r = (uint32_t)(quarter * 32 + lane);
-  const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
-  for (uint32_t k = 0; k < nit; ++k) {
+  // item -> matrix, tile and operand blocks
+  auto item = [&](uint32_t k, uint32_t& b, uint32_t& ti, uint32_t& tj) {
     const uint64_t it = it0 + k;
-    const uint32_t b = (uint32_t)(it / g.tiles_total);
-    uint32_t ti, tj;
+    b = (uint32_t)(it / g.tiles_total);
     tile_of(g, TRAIL, (uint32_t)(it - (uint64_t)b * g.tiles_total), ti, tj);
-    const uint32_t row0 = ti * BM, col0 = tj * BN;
-    // epilogue inputs of this tile, fetched while its MMAs run: the old C
-    // values of this thread's EPI_COLS columns (TRAIL, row in range, 32-byte
-    // aligned rows), the row exponent, and the tile's column exponents
-    const uint32_t row = row0 + r;
-    const bool row_ok = row < g.m;
-    const uint32_t cbeg = col0 + (uint32_t)part * EPI_COLS;
-    double* crow = g.c + b * g.c_mstride + (uint64_t)(row_ok ? row : 0) * g.ldc;
-    const bool vec = g.vec32 != 0 && row_ok && cbeg + EPI_COLS <= g.n;
-    double cv[EPI_COLS];
-    if (TRAIL && vec) {
-#pragma unroll
-      for (int e = 0; e < EPI_COLS; e += 4) ld_v4f64(crow + cbeg + e, cv + e);
-    }
-    if (threadIdx.x < BN)
-      s_eb[threadIdx.x] =
-          col0 + threadIdx.x < g.n ? g.exp_b[b * g.exp_b_mstride + col0 + threadIdx.x] : 0;
-    const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
+  };
+  auto a_block = [&](uint32_t k) {
+    uint32_t b, ti, tj;
+    item(k, b, ti, tj);
+    return g.img_a + b * g.img_a_mstride + (uint64_t)ti * S * SLICE_A;
+  };
 
-    if (warp == 0) {
-      if (lane == 0 && *abort_flag == 0) {
-        const uint8_t *gA, *gB;
-        item_ptrs(it, gA, gB);
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-        const uint64_t ad0 = tc::sw128_desc(tc::smem_u32(sA));
-        const uint64_t bd0 = tc::sw128_desc(tc::smem_u32(sB));
-        bool ok = tc::mbar_wait(full_b, k & 1, WAIT_NS);
+  if (warp == PRODUCER_WARP) {
+    if (lane == 0) {
+      bool ok = true;
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      const uint64_t ad0 = tc::sw128_desc(tc::smem_u32(sA));
+      const uint64_t bd0 = tc::sw128_desc(tc::smem_u32(sB));
+      // the first tile's B block and A slices 0 .. NST-1
+      uint32_t b, ti, tj;
+      item(0, b, ti, tj);
+      uint32_t cur_b = b, cur_tj = tj, bloads = 1;
+      tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
+      tc::bulk_g2s(sB, g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B, SM::B_BYTES,
+                   full_b);
+      const uint8_t* gA0 = a_block(0);
+#pragma unroll
+      for (int p = 0; p < NST; ++p) {
+        tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
+        tc::bulk_g2s(sA + p * SLICE_A, gA0 + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
+      }
+      const uint8_t* gA_nxt = nit > 1 ? a_block(1) : gA0;
+      for (uint32_t k = 0; k < nit; ++k) {
+        item(k, b, ti, tj);
+        const uint8_t* gA_cur = k == 0 ? gA0 : gA_nxt;
+        if (k > 0) gA_nxt = k + 1 < nit ? a_block(k + 1) : gA_cur;
+        if (k > 0 && (b != cur_b || tj != cur_tj)) {
+          // a new tile column: its B block replaces the old one once every
+          // MMA of the previous tile (the last to read it) has completed
+          if (ok) ok = tc::mbar_wait(&level[S - 1], (k - 1) & 1, WAIT_NS);
+          if (ok) {
+            tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
+            tc::bulk_g2s(sB, g.img_b + b * g.img_b_mstride + (uint64_t)tj * S * SLICE_B,
+                         SM::B_BYTES, full_b);
+            ++bloads;
+          }
+          cur_b = b;
+          cur_tj = tj;
+        }
+        // the previous tile's accumulators have all been read
+        if (k > 0 && ok) ok = tc::mbar_wait(tmem_free, (k - 1) & 1, WAIT_NS);
+        if (ok) ok = tc::mbar_wait(full_b, (bloads - 1) & 1, WAIT_NS);
+        if (ok) tc::tc_fence_after();
 #pragma unroll
         for (int p = 0; p < S; ++p) {
-          const int st = p % NST;
-          if (ok) ok = tc::mbar_wait(&full_a[st], fcnt[st] & 1, WAIT_NS);
-          ++fcnt[st];
+          const uint32_t gp = k * S + (uint32_t)p;   // slice index over the CTA's run
+          const int st = (int)(gp % NST);
+          if (ok) ok = tc::mbar_wait(&full_a[st], (gp / NST) & 1, WAIT_NS);
           if (ok) {
             tc::tc_fence_after();
             // descriptor start addresses advance in 16-byte units
@@ -496,91 +519,115 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
                              (p > 0 || kk > 0) ? 1u : 0u);
             }
           }
-          tc::mma_commit(&empty_a[st]);
-          ++ecnt[st];
-          // refill the stage of slice p - 1 with slice p - 1 + NST once its
-          // MMAs are done (those of slice p are queued behind them)
-          if (p >= 1 && p - 1 + NST < S) {
-            const int sr = (p - 1) % NST;
-            if (ok) ok = tc::mbar_wait(&empty_a[sr], (ecnt[sr] - 1) & 1, WAIT_NS);
-            if (ok) {
-              tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
-              tc::bulk_g2s(sA + sr * SLICE_A, gA + (size_t)(p - 1 + NST) * SLICE_A, SLICE_A,
-                           &full_a[sr]);
+          tc::mma_commit(&empty_a[st]);   // stage st is free once these MMAs are done
+          tc::mma_commit(&level[p]);      // and level p is final
+          // refill the stage of slice gp - 1 with slice gp - 1 + NST (this
+          // tile's or the next tile's) once the MMAs of gp - 1 are done
+          if (gp >= 1) {
+            const uint32_t gr = gp - 1 + NST;
+            if (gr / S < nit) {
+              const int sr = (int)((gp - 1) % NST);
+              if (ok) ok = tc::mbar_wait(&empty_a[sr], ((gp - 1) / NST) & 1, WAIT_NS);
+              if (ok) {
+                tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
+                tc::bulk_g2s(sA + sr * SLICE_A,
+                             (gr / S == k ? gA_cur : gA_nxt) + (size_t)(gr % S) * SLICE_A,
+                             SLICE_A, &full_a[sr]);
+              }
             }
           }
         }
-        if (!ok) {
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(g.status, ERR_TIMEOUT);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3, part = warp >> 2;
+    const uint32_t r = (uint32_t)(quarter * 32 + lane);
+    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t c0 = (uint32_t)part * EPI_COLS;   // this thread's first column inside the tile
+    for (uint32_t k = 0; k < nit; ++k) {
+      uint32_t b, ti, tj;
+      item(k, b, ti, tj);
+      const uint32_t row = ti * BM + r, cbeg = tj * BN + c0;
+      const bool row_ok = row < g.m;
+      const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
+      // Level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
+      // |acc_l| <= 2^22), folded as the levels become final:
+      // T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with
+      //   t_hi = (acc_0 128 + acc_1) 2^14 + acc_2 128 + acc_3   (< 2^44)
+      //   t_lo = (acc_4 128 + acc_5) 2^14 + acc_6 128 + acc_7
+      // (each pair in 32-bit wrapping arithmetic: it fits in 30 bits)
+      constexpr uint32_t M129 = 0x4B400000u * 129u;   // the offsets of a pair (mod 2^32)
+      uint32_t u[EPI_COLS];
+      int32_t pa[EPI_COLS];
+      int64_t th[EPI_COLS], tl[EPI_COLS];
+      bool ok = true;
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        if (ok) ok = tc::mbar_wait(&level[l], k & 1, WAIT_NS);
+        ok = __all_sync(0xffffffffu, ok);
+        tc::tc_fence_after();
+        float acc[EPI_COLS];
+        tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc);
+        tc::tmem_ld8(tlane + (uint32_t)l * BN + c0 + 8, acc + 8);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; ++c) {
+          const uint32_t v = __float_as_uint(acc[c] + 12582912.0f);
+          if ((l & 1) == 0) {
+            u[c] = v;
+          } else {
+            const int32_t pr = (int32_t)(u[c] * 128u + v - M129);
+            if (l == 1 || l == 5) pa[c] = pr;
+            else if (l == 3) th[c] = (int64_t)pa[c] * 16384 + pr;
+            else tl[c] = (int64_t)pa[c] * 16384 + pr;
+          }
+        }
+      }
+      // every level read: the next tile's MMAs may overwrite the columns
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tmem_free);
+      if (!ok) {
+        if (lane == 0) {
           *abort_flag = 1;
           atomicOr(g.status, ERR_TIMEOUT);
         }
-        tc::mma_commit(done);   // every MMA issued above has completed when this arrives
-      } else if (lane == 0) {
-        tc::mma_commit(done);
+        continue;
       }
-      __syncwarp();
-    }
-    // all threads: the accumulators are final (bounded wait)
-    const bool fin = tc::mbar_wait(done, k & 1, WAIT_NS);
-    __syncthreads();
-    if (!fin && threadIdx.x == 0) {
-      *abort_flag = 1;
-      atomicOr(g.status, ERR_TIMEOUT);
-    }
-    // the MMAs are done with shared memory: the next tile's operands start
-    // loading now, under this tile's epilogue
-    if (threadIdx.x == 0 && k + 1 < nit && *abort_flag == 0) {
-      const uint8_t *gA, *gB;
-      item_ptrs(it + 1, gA, gB);
-      tc::mbar_arrive_expect_tx(full_b, SM::B_BYTES);
-      tc::bulk_g2s(sB, gB, SM::B_BYTES, full_b);
-#pragma unroll
-      for (int p = 0; p < NST; ++p) {
-        tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
-        tc::bulk_g2s(sA + p * SLICE_A, gA + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
-      }
-    }
-    if (fin && *abort_flag == 0) {
-      tc::tc_fence_after();
+      if (!row_ok) continue;
+      // T 2^(e_row + e_col - 7 (S + 1)), rounded once, written (panel) or
+      // subtracted from the old value (trailing update)
+      double* crow = g.c + b * g.c_mstride + (uint64_t)row * g.ldc;
+      const int32_t* eb = g.exp_b + b * g.exp_b_mstride;
       const int ebase = ea - 7 * (S + 1);
+      const bool vec = g.vec32 != 0 && cbeg + EPI_COLS <= g.n;
 #pragma unroll
       for (int kc = 0; kc < EPI_COLS; kc += 8) {
-        const uint32_t c0 = (uint32_t)part * EPI_COLS + (uint32_t)kc;   // column inside the tile
-        float acc[S][8];
-#pragma unroll
-        for (int l = 0; l < S; ++l) tc::tmem_ld8(tlane + (uint32_t)l * BN + c0, acc[l]);
-        tc::tmem_ld_wait();
-        if (!row_ok || col0 + c0 >= g.n) continue;
         double v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          // level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
-          // |acc_l| <= 2^22); T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with
-          //   t_hi = (acc_0 128 + acc_1) 2^14 + acc_2 128 + acc_3   (< 2^44)
-          //   t_lo = (acc_4 128 + acc_5) 2^14 + acc_6 128 + acc_7
-          // (the pairs in 32-bit wrapping arithmetic: each pair fits in 30 bits)
-          uint32_t u[S];
-#pragma unroll
-          for (int l = 0; l < S; ++l) u[l] = __float_as_uint(acc[l][e] + 12582912.0f);
-          constexpr uint32_t M129 = 0x4B400000u * 129u;   // the offsets of a pair (mod 2^32)
-          const int32_t p01 = (int32_t)(u[0] * 128u + u[1] - M129);
-          const int32_t p23 = (int32_t)(u[2] * 128u + u[3] - M129);
-          const int32_t p45 = (int32_t)(u[4] * 128u + u[5] - M129);
-          const int32_t p67 = (int32_t)(u[6] * 128u + u[7] - M129);
-          const int64_t th = (int64_t)p01 * 16384 + p23;
-          const int64_t tl = (int64_t)p45 * 16384 + p67;
-          uint64_t hi = (uint64_t)(th >> 36);
-          uint64_t lo = (uint64_t)th << 28;
-          const uint64_t lo2 = lo + (uint64_t)tl;
-          hi += (uint64_t)(tl >> 63) + (lo2 < lo);
+          const int c = kc + e;
+          uint64_t hi = (uint64_t)(th[c] >> 36);
+          uint64_t lo = (uint64_t)th[c] << 28;
+          const uint64_t lo2 = lo + (uint64_t)tl[c];
+          hi += (uint64_t)(tl[c] >> 63) + (lo2 < lo);
           lo = lo2;
-          v[e] = scaled_i128_to_f64(hi, lo, ebase + s_eb[c0 + e]);
+          const uint32_t col = cbeg + (uint32_t)c;
+          v[e] = scaled_i128_to_f64(hi, lo, ebase + (col < g.n ? eb[col] : 0));
         }
-        const uint32_t colc = col0 + c0;
+        const uint32_t colc = cbeg + (uint32_t)kc;
         if (vec) {
           if (TRAIL) {
+            double cv[8];
+            ld_v4f64(crow + colc, cv);
+            ld_v4f64(crow + colc + 4, cv + 4);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = cv[kc + e] - v[e];
+            for (int e = 0; e < 8; ++e) v[e] = cv[e] - v[e];
           }
           st_v4f64(crow + colc, v);
           st_v4f64(crow + colc + 4, v + 4);
@@ -593,12 +640,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
         }
       }
     }
-    // TMEM and s_eb free for the next tile
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
   }
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  // every MMA has completed (the epilogue waited for the last level of every
+  // tile) and every TMEM load has been waited for
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == PRODUCER_WARP) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
