@@ -169,10 +169,14 @@ __device__ __forceinline__ uint32_t bf16_of_small_int(int d) {
 // One row of an operand, four consecutive K elements per lane (k = 4 lane ..
 // 4 lane + 3, zero beyond the panel), sliced by one warp: the row exponent
 // (warp maximum), then S digits per element written into the image block
-// `blk` (RB rows) at row rr.  All 32 lanes must call it.
+// `blk` (RB rows) at row rr.  A-role blocks hold the S slices one after the
+// other, each an RB-row operand; B-role blocks (`stacked`) hold them as one
+// operand of S RB rows, slice p's row r at row p RB + r, so that one MMA can
+// take several consecutive slices as the rows of a wider N.  All 32 lanes
+// must call it.
 template <int S>
 __device__ __forceinline__ void slice_row(const double v[4], uint8_t* __restrict__ blk, int RB,
-                                          int rr, int32_t* __restrict__ exp_out) {
+                                          int rr, int32_t* __restrict__ exp_out, bool stacked) {
   const int lane = threadIdx.x & 31;
   int emax = 0;
 #pragma unroll
@@ -201,10 +205,15 @@ __device__ __forceinline__ void slice_row(const double v[4], uint8_t* __restrict
     dig[p][0] = d16[p][0] | (d16[p][1] << 16);
     dig[p][1] = d16[p][2] | (d16[p][3] << 16);
   }
-  const uint32_t off = tc::sw128_offset((uint32_t)RB, (uint32_t)rr, (uint32_t)(4 * lane));
+  // stacked: row p RB + rr of an S RB-row operand (its 8-row groups advance
+  // 1024 bytes, so slice p starts RB 128 bytes after slice p - 1 in each
+  // 64-element K half); else row rr of slice p's own RB-row operand
+  const uint32_t off = stacked ? tc::sw128_offset((uint32_t)(S * RB), (uint32_t)rr, (uint32_t)(4 * lane))
+                               : tc::sw128_offset((uint32_t)RB, (uint32_t)rr, (uint32_t)(4 * lane));
+  const size_t pstride = stacked ? (size_t)RB * 128 : (size_t)RB * NB * 2;
 #pragma unroll
   for (int p = 0; p < S; ++p)
-    *reinterpret_cast<uint2*>(blk + (size_t)p * RB * NB * 2 + off) = make_uint2(dig[p][0], dig[p][1]);
+    *reinterpret_cast<uint2*>(blk + (size_t)p * pstride + off) = make_uint2(dig[p][0], dig[p][1]);
   if (lane == 0) *exp_out = e;
 }
 
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs g) {
   }
   if (g.img_a)
     slice_row<S>(v, g.img_a + b * g.img_a_mstride + (uint64_t)(r / RB_A) * S * SLICE_A, RB_A,
-                 (int)(r % RB_A), g.exp_a + b * g.exp_a_mstride + r);
+                 (int)(r % RB_A), g.exp_a + b * g.exp_a_mstride + r, false);
   if (g.img_b) {
     if (g.colscale) {
       const double* cs = g.colscale + b * g.colscale_mstride;
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs g) {
       }
     }
     slice_row<S>(v, g.img_b + b * g.img_b_mstride + (uint64_t)(r / RB_B) * S * SLICE_B, RB_B,
-                 (int)(r % RB_B), g.exp_b + b * g.exp_b_mstride + r);
+                 (int)(r % RB_B), g.exp_b + b * g.exp_b_mstride + r, true);
   }
 }
 
@@ -397,13 +406,27 @@ __device__ __forceinline__ void tile_of(const GemmArgs& g, bool trail, uint32_t 
 // next tile's first slices load while this tile's last ones multiply),
 // reloads the B block only when the tile column changes, and issues for A
 // slice p the MMAs with B slices q = 0 .. S-1-p into TMEM accumulator p + q.
-// Level l (accumulator l) receives its last product from slice l, so after
-// slice p's MMAs a commit on level[p] marks level p final; the 16 epilogue
-// warps read and fold level l while slices l+1 .. S-1 multiply, release TMEM
+// Level l (accumulator l) is final once slices 0 .. l are multiplied: after
+// each slice (in kSliceOrder) a commit on level[l] marks every level that
+// became final there; the 16 epilogue warps read and fold each level while
+// the remaining slices multiply, release TMEM
 // after the last level (tmem_free), and round and store the tile while the
 // next tile's MMAs run.  The MMA issue is fully unrolled over precomputed
 // descriptors.  Every wait is bounded; after a timeout the producer keeps
 // committing (empty) level barriers so that no warp waits out more bounds.
+// The order in which a tile's A slices are multiplied: long and short ones
+// alternate (slice p takes S - p products), so that two consecutive slices
+// always outlast the copy of the next one into the ring.  Slice 0 comes
+// first: its MMAs initialise every level.  kLevelsDone(i): the levels that
+// are final once the first i + 1 slices of the order are done (level l
+// needs slices 0 .. l), as a bit mask of the levels newly final there.
+__host__ __device__ constexpr int kSliceOrder(int i) {
+  return (i & 1) ? 7 - (i >> 1) : (i >> 1);   // 0, 7, 1, 6, 2, 5, 3, 4
+}
+__host__ __device__ constexpr uint32_t kLevelsDone(int i) {
+  return i == 7 ? 0xF0u : (i & 1) ? 0u : 1u << (i >> 1);
+}
+
 template <int S, bool TRAIL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g) {
   using SM = GemmSmem<S>;
@@ -461,9 +484,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
   if (warp == PRODUCER_WARP) {
     if (lane == 0) {
       bool ok = true;
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
       const uint64_t ad0 = tc::sw128_desc(tc::smem_u32(sA));
       const uint64_t bd0 = tc::sw128_desc(tc::smem_u32(sB));
+      const uint32_t dhi = (uint32_t)(ad0 >> 32);   // equal for both operands
+      const uint32_t alo0 = (uint32_t)ad0, blo0 = (uint32_t)bd0;
       // the first tile's B block and A slices 0 .. NST-1
       uint32_t b, ti, tj;
       item(0, b, ti, tj);
@@ -473,9 +497,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
                    full_b);
       const uint8_t* gA0 = a_block(0);
 #pragma unroll
-      for (int p = 0; p < NST; ++p) {
-        tc::mbar_arrive_expect_tx(&full_a[p], SLICE_A);
-        tc::bulk_g2s(sA + p * SLICE_A, gA0 + (size_t)p * SLICE_A, SLICE_A, &full_a[p]);
+      for (int i = 0; i < NST; ++i) {
+        tc::mbar_arrive_expect_tx(&full_a[i], SLICE_A);
+        tc::bulk_g2s(sA + i * SLICE_A, gA0 + (size_t)kSliceOrder(i) * SLICE_A, SLICE_A, &full_a[i]);
       }
       const uint8_t* gA_nxt = nit > 1 ? a_block(1) : gA0;
       for (uint32_t k = 0; k < nit; ++k) {
@@ -500,29 +524,38 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
         if (ok) ok = tc::mbar_wait(full_b, (bloads - 1) & 1, WAIT_NS);
         if (ok) tc::tc_fence_after();
 #pragma unroll
-        for (int p = 0; p < S; ++p) {
-          const uint32_t gp = k * S + (uint32_t)p;   // slice index over the CTA's run
+        for (int i = 0; i < S; ++i) {
+          const int p = kSliceOrder(i);              // the A slice of this position
+          const uint32_t gp = k * S + (uint32_t)i;   // position over the CTA's run
           const int st = (int)(gp % NST);
           if (ok) ok = tc::mbar_wait(&full_a[st], (gp / NST) & 1, WAIT_NS);
           if (ok) {
             tc::tc_fence_after();
             // descriptor start addresses advance in 16-byte units
-            const uint64_t ad = ad0 + (uint64_t)((st * SLICE_A) >> 4);
+            const uint32_t alo = alo0 + (uint32_t)((st * SLICE_A) >> 4);
+            // the S - p products of slice p as MMAs over up to four consecutive
+            // B slices each (rows 64 q0 .. of the stacked B block, N = 64 c):
+            // their accumulators, levels p + q0 .. p + q0 + c - 1, are
+            // adjacent TMEM columns
 #pragma unroll
-            for (int q = 0; q < S - p; ++q) {
-              const uint64_t bd = bd0 + (uint64_t)((q * SLICE_B) >> 4);
-              const uint32_t d = tmem + (uint32_t)(p + q) * BN;
+            for (int q0 = 0; q0 < S - p; q0 += 4) {
+              const int c = S - p - q0 < 4 ? S - p - q0 : 4;
+              const uint32_t idesc = tc::idesc_bf16_f32(BM, (uint32_t)(BN * c));
+              const uint32_t blo = blo0 + (uint32_t)((q0 * RB_B * 128) >> 4);
+              const uint32_t d = tmem + (uint32_t)(p + q0) * BN;
 #pragma unroll
               for (int kk = 0; kk < NB / 16; ++kk)
-                tc::mma_bf16(d, ad + (uint64_t)(((kk >> 2) * (RB_A * 128) + (kk & 3) * 32) >> 4),
-                             bd + (uint64_t)(((kk >> 2) * (RB_B * 128) + (kk & 3) * 32) >> 4), idesc,
-                             (p > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_bf16_lo(d, alo + (uint32_t)(((kk >> 2) * (RB_A * 128) + (kk & 3) * 32) >> 4),
+                                blo + (uint32_t)(((kk >> 2) * (S * RB_B * 128) + (kk & 3) * 32) >> 4),
+                                dhi, idesc, (p > 0 || kk > 0) ? 1u : 0u);
             }
           }
           tc::mma_commit(&empty_a[st]);   // stage st is free once these MMAs are done
-          tc::mma_commit(&level[p]);      // and level p is final
-          // refill the stage of slice gp - 1 with slice gp - 1 + NST (this
-          // tile's or the next tile's) once the MMAs of gp - 1 are done
+#pragma unroll
+          for (int l = 0; l < S; ++l)      // and these levels are final
+            if (kLevelsDone(i) & (1u << l)) tc::mma_commit(&level[l]);
+          // refill the stage of position gp - 1 with position gp - 1 + NST
+          // (this tile's or the next tile's) once the MMAs of gp - 1 are done
           if (gp >= 1) {
             const uint32_t gr = gp - 1 + NST;
             if (gr / S < nit) {
@@ -530,9 +563,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
               if (ok) ok = tc::mbar_wait(&empty_a[sr], ((gp - 1) / NST) & 1, WAIT_NS);
               if (ok) {
                 tc::mbar_arrive_expect_tx(&full_a[sr], SLICE_A);
-                tc::bulk_g2s(sA + sr * SLICE_A,
-                             (gr / S == k ? gA_cur : gA_nxt) + (size_t)(gr % S) * SLICE_A,
-                             SLICE_A, &full_a[sr]);
+                const uint8_t* src = (gr / S == k ? gA_cur : gA_nxt) +
+                                     (size_t)kSliceOrder((int)(gr % S)) * SLICE_A;
+                tc::bulk_g2s(sA + sr * SLICE_A, src, SLICE_A, &full_a[sr]);
               }
             }
           }
@@ -555,6 +588,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
       const uint32_t row = ti * BM + r, cbeg = tj * BN + c0;
       const bool row_ok = row < g.m;
       const int ea = row_ok ? g.exp_a[b * g.exp_a_mstride + row] : 0;
+      if (TRAIL && row_ok && cbeg < g.n) {   // the old C values, read at the end of the tile
+        const double* cp = g.c + b * g.c_mstride + (uint64_t)row * g.ldc + cbeg;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cp));
+        if (cbeg + EPI_COLS - 1 < g.n)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + EPI_COLS - 1));
+      }
       // Level l as the integer bits(acc_l + 1.5 2^23) - 0x4B400000 (exact:
       // |acc_l| <= 2^22), folded as the levels become final:
       // T = sum_l acc_l 128^(7-l) = t_hi 2^28 + t_lo with

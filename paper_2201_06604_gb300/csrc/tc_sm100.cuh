@@ -151,6 +151,23 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+// The same with both descriptors given as their low words and a shared high
+// word (the K-major SW128 descriptors above differ only in the start-address
+// and leading-offset fields, both in the low word, and no address offset
+// inside shared memory carries out of the 14-bit start field): one 32-bit
+// add per operand instead of a 64-bit one.
+__device__ __forceinline__ void mma_bf16_lo(uint32_t tmem_d, uint32_t alo, uint32_t blo,
+                                            uint32_t hi, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+      "setp.ne.b32 p, %5, 0;\n\t"
+      "mov.b64 da, {%1, %3};\n\t"
+      "mov.b64 db, {%2, %3};\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(tmem_d),
+      "r"(alo), "r"(blo), "r"(hi), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrives on the mbarrier once every tcgen05 operation this thread issued
 // before it has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
