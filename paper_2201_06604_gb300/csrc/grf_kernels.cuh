@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "matern.cuh"
+#include "ozaki_round.cuh"
 #include "tc_sm100.cuh"
 #include "transforms_df.cuh"
 
@@ -316,34 +317,6 @@ __device__ __forceinline__ void lower_tile(uint32_t x, uint32_t& ti, uint32_t& t
   while ((uint64_t)t * (t + 1) > x) --t;
   ti = t;
   tj = x - t * (t + 1);
-}
-
-// 128-bit two's-complement value T = hi 2^64 + lo times 2^E, rounded to
-// nearest-even fp64 (0 for T = 0 and below the normal range).
-__device__ __forceinline__ double scaled_i128_to_f64(uint64_t hi, uint64_t lo, int E) {
-  const uint64_t sgn = hi & 0x8000000000000000ull;
-  // magnitude (two's-complement negation when negative), without branches
-  const uint64_t flip = (uint64_t)((int64_t)hi >> 63);
-  lo ^= flip;
-  hi ^= flip;
-  const uint64_t lo1 = lo - flip;             // + 1 when negative
-  hi += (flip & (lo1 == 0));
-  lo = lo1;
-  const bool h = hi != 0;
-  const uint64_t w = h ? hi : lo;
-  if (w == 0) return 0.0;
-  const int lzw = __clzll((long long)w);
-  // the leading 64 bits and what lies below them
-  const uint64_t top = h ? (hi << lzw) | (lzw ? lo >> (64 - lzw) : 0) : lo << lzw;
-  const uint64_t low = h ? lo << lzw : 0;
-  const int eb = 127 - (h ? lzw : 64 + lzw) + E + 1023;   // biased exponent of the result
-  if (eb <= 0) return 0.0;
-  uint64_t mant = top >> 11;                  // 53 bits with the leading one
-  const uint64_t rem = top & 0x7FF;
-  const bool up = rem > 0x400 || (rem == 0x400 && (low != 0 || (mant & 1)));
-  mant += up;
-  const uint64_t bits = ((uint64_t)(eb - 1) << 52) + mant;   // a rounding carry steps the exponent
-  return __longlong_as_double((long long)(bits | sgn));
 }
 
 // 32-byte global accesses of four doubles (address 32-byte aligned).
@@ -651,13 +624,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int c = kc + e;
-          uint64_t hi = (uint64_t)(th[c] >> 36);
-          uint64_t lo = (uint64_t)th[c] << 28;
-          const uint64_t lo2 = lo + (uint64_t)tl[c];
-          hi += (uint64_t)(tl[c] >> 63) + (lo2 < lo);
-          lo = lo2;
           const uint32_t col = cbeg + (uint32_t)c;
-          v[e] = scaled_i128_to_f64(hi, lo, ebase + (col < g.n ? eb[col] : 0));
+          v[e] = ozaki_round(th[c], tl[c], ebase + (col < g.n ? eb[col] : 0));
         }
         const uint32_t colc = cbeg + (uint32_t)kc;
         if (vec) {

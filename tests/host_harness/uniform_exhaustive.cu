@@ -11,6 +11,9 @@
 //   mode "step31" n seed: prints n outputs of g31::step from a state.
 //   mode "matern": prints e^x K_nu(x) and the Matern correlation of
 //     matern.cuh on a grid of orders and arguments ("nu x kscaled corr").
+//   mode "ozround": reads lines "th tl E" (decimal) and prints the bits of
+//     ozaki_round(th, tl, E) as 16 hex digits, one a line (the rounding of the
+//     GRF product kernels' exact level sum).
 //   mode "tables": prints the double-float transform tables the library
 //     uploads (host_jump.cpp, linked in), for M = m1 + 1 (table 0) and
 //     M = 2^32 (table 1), one float4 entry a line as hex floats.
@@ -22,6 +25,7 @@
 #include "../../paper_2201_06604_gb300/csrc/mrg31k3p_core.cuh"
 #include "../../paper_2201_06604_gb300/csrc/host_jump.h"
 #include "../../paper_2201_06604_gb300/csrc/matern.cuh"
+#include "../../paper_2201_06604_gb300/csrc/ozaki_round.cuh"
 #include <cmath>
 
 static int check_uniform(unsigned lo, unsigned hi) {
@@ -94,8 +98,21 @@ static int print_matern() {
   return 0;
 }
 
+static int ozround() {
+  long long th, tl;
+  int E;
+  while (std::scanf("%lld %lld %d", &th, &tl, &E) == 3) {
+    const double d = mrg::grf::ozaki_round(th, tl, E);
+    uint64_t b;
+    std::memcpy(&b, &d, 8);
+    std::printf("%016llx\n", (unsigned long long)b);
+  }
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 2 && !std::strcmp(argv[1], "tables")) return print_tables();
+  if (argc >= 2 && !std::strcmp(argv[1], "ozround")) return ozround();
   if (argc >= 2 && !std::strcmp(argv[1], "matern")) return print_matern();
   if (argc >= 2 && !std::strcmp(argv[1], "uniform31")) return check_uniform31();
   if (argc >= 9 && !std::strcmp(argv[1], "step31")) {
@@ -123,6 +140,6 @@ int main(int argc, char** argv) {
     std::printf("%u %u %u %u %u %u\n", c.a0, c.a1, c.a2, c.b0, c.b1, c.b2);
     return 0;
   }
-  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5 | tables | matern\n");
+  std::fprintf(stderr, "usage: uniform [lo hi] | step n s0..s5 | uniform31 | step31 n s0..s5 | tables | matern | ozround\n");
   return 2;
 }

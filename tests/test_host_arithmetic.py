@@ -10,6 +10,10 @@ own header and checked on the CPU (no GPU needed):
   sin and cos of the bucket angles in each of their eight copies,
   ln(C_k / (M 2^s)) for all shifts), as float pairs, against 50-digit values
   from mpmath;
+* the GRF products' final rounding (ozaki_round.cuh): the exact level sum
+  T = th 2^28 + tl times 2^E rounded once to fp64, against exact rational
+  rounding, on level sums drawn at every magnitude, exact ties, the int64
+  threshold and the flush below the normal range;
 * the device Matern correlation's Bessel function (matern.cuh, compiled for
   the host) against scipy's exponentially scaled K and the Matern
   correlation against the GRF oracle.
@@ -39,6 +43,7 @@ def harness():
             os.path.getmtime(SRC), os.path.getmtime(HOST_JUMP),
             os.path.getmtime(os.path.join(csrc, "host_jump.h")),
             os.path.getmtime(os.path.join(csrc, "matern.cuh")),
+            os.path.getmtime(os.path.join(csrc, "ozaki_round.cuh")),
             os.path.getmtime(os.path.join(csrc, "mrg32k3a_core.cuh")),
             os.path.getmtime(os.path.join(csrc, "mrg31k3p_core.cuh"))):
         subprocess.run(["nvcc", "-O2", "-std=c++17", "-Xcompiler", "-fopenmp",
@@ -155,3 +160,69 @@ def test_matern_bessel_k_against_scipy_and_oracle(harness):
     want = np.array([grf.matern(np.array([xi * 1.0]), n, np.sqrt(8 * n), 1.0)[0]
                      for n, xi in zip(nu[pos], x[pos])])      # phi = sqrt(8 nu): |d| = x
     assert np.allclose(corr[pos], want, rtol=2e-13, atol=1e-300)
+
+
+def _ozaki_cases(rng):
+    """(th, tl, E) triples as the product kernels form them, and edge cases."""
+    cases = []
+    bound = [(l + 1) << 19 for l in range(8)]          # |acc_l| <= (l + 1) 2^19
+    for _ in range(60000):
+        shrink = int(rng.integers(0, 40))
+        acc = [int(rng.integers(-b, b + 1)) >> min(shrink, 19 + l) for l, b in enumerate(bound)]
+        if rng.random() < 0.05:                       # leading levels zero: small sums
+            z = int(rng.integers(1, 8))
+            acc[:z] = [0] * z
+        p = [acc[2 * i] * 128 + acc[2 * i + 1] for i in range(4)]
+        th, tl = p[0] * 16384 + p[1], p[2] * 16384 + p[3]
+        cases.append((th, tl, int(rng.integers(-1080, 60))))
+    # exact ties and their neighbours at every rounding position, both signs
+    for s in range(1, 16):
+        for m in (1 << 52, (1 << 52) + 1, (1 << 53) - 1, (1 << 53) - 2, int(rng.integers(1 << 52, 1 << 53))):
+            for d in (-1, 0, 1):
+                for sign in (1, -1):
+                    T = sign * ((m << s) + (1 << (s - 1)) + d)
+                    th, tl = T >> 28, T & ((1 << 28) - 1)
+                    j = int(rng.integers(-4096, 4097))     # another split of the same T
+                    cases.append((th - j, tl + (j << 28), int(rng.integers(-900, 0))))
+                    cases.append((th, tl, -60))
+    # around |T| = 2^62, where T stops fitting an int64 (T = 64 Th + Tl, |Th| = 2^56)
+    for sign in (1, -1):
+        for d in range(-130, 131):
+            T = sign * ((1 << 62) + d)
+            cases.append((T >> 28, T & ((1 << 28) - 1), -62))
+    # the largest sums, zero, and results that fall below the normal range
+    big = sum(b << (7 * (7 - l)) for l, b in enumerate(bound))
+    for T in (big, -big, 0, 1, -1, 12345):
+        for E in (-1200, -1136, -1075, -1074, -1023, -1022, -1021, -66, 0):
+            cases.append((T >> 28, T & ((1 << 28) - 1), E))
+    return cases
+
+
+def _round_exact(T, E):
+    """T 2^E rounded to nearest-even fp64, +0 below the normal range."""
+    import math
+    import struct
+    if T == 0:
+        return 0
+    r = float(T)                                      # exact round-half-even of an integer
+    m, e = math.frexp(r)                              # r = m 2^e, 0.5 <= |m| < 1
+    biased = e - 1 + 1023 + E                         # exponent field of r 2^E
+    if biased <= 0:
+        return 0
+    if biased >= 0x7FF:
+        return struct.unpack("<Q", struct.pack("<d", math.copysign(math.inf, r)))[0]
+    return struct.unpack("<Q", struct.pack("<d", math.ldexp(r, E)))[0]
+
+
+def test_ozaki_round_against_exact_rounding(harness):
+    rng = np.random.default_rng(2201)
+    cases = _ozaki_cases(rng)
+    for th, tl, E in cases:
+        assert abs(tl) < 1 << 62 and abs(th * (1 << 28) + tl) < 1 << 69
+    inp = "\n".join(f"{th} {tl} {E}" for th, tl, E in cases) + "\n"
+    r = subprocess.run([harness, "ozround"], input=inp, capture_output=True, text=True, timeout=120,
+                       check=True)
+    got = [int(x, 16) for x in r.stdout.split()]
+    assert len(got) == len(cases)
+    bad = [(c, g) for c, g in zip(cases, got) if g != _round_exact(c[0] * (1 << 28) + c[1], c[2])]
+    assert not bad, bad[:5]
