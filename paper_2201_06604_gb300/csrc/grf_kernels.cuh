@@ -749,26 +749,29 @@ __device__ __forceinline__ void st_df(dfs& x, df v) {
 }
 
 // The lower triangle (strict: below the diagonal only) of a kb x kb fp64
-// block times 2^-sc into a shared double-float array of row pitch DG; eight
-// loads in flight per thread before the first conversion.
+// block times 2^-sc into a shared double-float array of row pitch DG.
 template <int NTH>
 __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint64_t lda, int kb,
                                               int sc, dfs* dst, bool strict) {
-  constexpr int U = 8;
-  const int n2 = kb * kb;
-  for (int base = (int)threadIdx.x; base < n2; base += U * NTH) {
-    double v[U];
+  // warp w takes rows w, w + NTH / 32, ..; its lanes run along the row
+  // (coalesced loads, no index division), four loads in flight per lane
+  constexpr int NW = NTH / 32;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  for (int i = warp; i < kb; i += NW) {
+    const int len = strict ? i : i + 1;
+    const double* row = A + (uint64_t)i * lda;
+    for (int j0 = 0; j0 < len; j0 += 128) {
+      double v[4];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * NTH;
-      const int i = idx / kb, j = idx - i * kb;
-      v[u] = idx < n2 && (strict ? j < i : j <= i) ? A[(uint64_t)i * lda + j] : 0.0;
-    }
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * 32 + lane;
+        v[u] = j < len ? row[j] : 0.0;
+      }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * NTH;
-      const int i = idx / kb, j = idx - i * kb;
-      if (idx < n2 && (strict ? j < i : j <= i)) st_df(dst[i * DG + j], df_of_scaled(v[u], sc));
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * 32 + lane;
+        if (j < len) st_df(dst[i * DG + j], df_of_scaled(v[u], sc));
+      }
     }
   }
 }
