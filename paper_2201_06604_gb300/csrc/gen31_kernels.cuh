@@ -95,6 +95,21 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
   } else if constexpr (DIST == MRG_UNIFORM) {
 #pragma unroll
     for (int e = 0; e < UE; ++e) w[e] = g31::uniform_bits32(g31::step(s));
+  } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F64 && UE % 4 == 0) {
+    // two pairs per packed fp32x2 evaluation (bit-identical to the scalar one)
+#pragma unroll
+    for (int p = 0; p < UE / 4; ++p) {
+      const uint32_t z1a = 2u * g31::step(s);
+      const uint32_t z2a = 2u * g31::step(s);
+      const uint32_t z1b = 2u * g31::step(s);
+      const uint32_t z2b = 2u * g31::step(s);
+      uint64_t xa, ya, xb, yb;
+      box_muller_f64_x2<UM2p32>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
+      put_f64(w + 8 * p, xa);
+      put_f64(w + 8 * p + 2, ya);
+      put_f64(w + 8 * p + 4, xb);
+      put_f64(w + 8 * p + 6, yb);
+    }
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
