@@ -29,6 +29,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "matern.cuh"
 #include "ozaki_round.cuh"
 #include "tc_sm100.cuh"
@@ -951,19 +953,30 @@ __global__ void __launch_bounds__(INV_COLS * 32) ldl_inverse_kernel(const double
   df x[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) x[t] = lane + 32 * t == c ? df{1.0f, 0.0f} : df{0.0f, 0.0f};
-  for (int m = c; m < (int)kb - 1; ++m) {
-    // x_m, broadcast from the lane that holds it
-    const int tm = m >> 5, lm = m & 31;
-    df xm;
+  // Step m: x_i -= L_im x_m for i > m.  Only x_{m+1} gates the next step, so
+  // it is updated first and broadcast at once, and the other rows' updates
+  // (rows i > m + 1 only) fill the shuffle's latency; rows i <= m are
+  // final.  The same operations as plain row order, so the same bits.
+  df xm{1.0f, 0.0f};                        // x_c
+  const int last = (int)kb - 1;
+  auto step = [&](auto tcv, int m) {
+    constexpr int tc = decltype(tcv)::value;       // x_{m+1} is x[tc] of lane (m + 1) mod 32
+    const int ic = lane + 32 * tc;
+    if (ic > m && ic < (int)kb) x[tc] = df_fnms(x[tc], ld_df(sLf[ic * DG + m]), xm);
+    const int l1 = (m + 1) & 31;
+    const df xn{__shfl_sync(0xffffffffu, x[tc].hi, l1), __shfl_sync(0xffffffffu, x[tc].lo, l1)};
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (t == tm) xm = df{__shfl_sync(0xffffffffu, x[t].hi, lm), __shfl_sync(0xffffffffu, x[t].lo, lm)};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = tc + 1; t < 4; ++t) {
       const int i = lane + 32 * t;
-      if (i > m && i < (int)kb) x[t] = df_fnms(x[t], ld_df(sLf[i * DG + m]), xm);
+      if (i < (int)kb) x[t] = df_fnms(x[t], ld_df(sLf[i * DG + m]), xm);
     }
-  }
+    xm = xn;
+  };
+  // the segments of m in which x_{m+1} sits in x[0], x[1], x[2], x[3]
+  for (int m = c; m < min(last, 31); ++m) step(std::integral_constant<int, 0>{}, m);
+  for (int m = max(c, 31); m < min(last, 63); ++m) step(std::integral_constant<int, 1>{}, m);
+  for (int m = max(c, 63); m < min(last, 95); ++m) step(std::integral_constant<int, 2>{}, m);
+  for (int m = max(c, 95); m < last; ++m) step(std::integral_constant<int, 3>{}, m);
   // B[n][c] = x_n / d_n (x_n = 0 above the diagonal, n < c)
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
