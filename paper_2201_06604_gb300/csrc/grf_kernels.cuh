@@ -786,7 +786,7 @@ __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint
 // step, and a step costs two barriers.  Double-float arithmetic on the FP32
 // pipes (GB300's FP64 pipe retires under one DFMA per cycle per SM).
 constexpr int DIAG_THREADS = 1024;
-constexpr int DIAG_P = 3;   // pivots per pass of the diagonal block's LDL^T (measured: 2: 108 us, 3: 106, 4: 114)
+constexpr int DIAG_P = 4;   // pivots per pass of the diagonal block's LDL^T (measured: 3: 88 us, 4: 82, 6: 97)
 
 // P pivots j .. j + P - 1 of the diagonal block's LDL^T in one pass, with
 // the operations of one pivot at a time in the same order (so the same
@@ -803,46 +803,53 @@ __device__ __forceinline__ void diag_pass(dfs* __restrict__ sm, dfs* __restrict_
                                           const uint16_t* __restrict__ s_pair, int* s_bad, int kb,
                                           int j, int tid) {
   constexpr int NT = DIAG_THREADS;
+  static_assert(NT >= NB, "one thread per row below the pivot block");
+  // only thread 0 and the threads with a row below the block need the
+  // pivot block (a prefix of the threads: whole warps drop out)
+  const bool active = tid == 0 || j + P + tid < kb;
   df Bk[P][P];                       // the pivot block, lower part
-#pragma unroll
-  for (int r = 0; r < P; ++r)
-#pragma unroll
-    for (int c = 0; c <= r; ++c) Bk[r][c] = ld_df(sm[(j + r) * DG + j + c]);
   df rc[P], Wb[P][P], Lb[P][P];
-  int bad = 0;
+  if (active) {
 #pragma unroll
-  for (int c = 0; c < P; ++c) {
-    const bool pos = Bk[c][c].hi > 0x1p-100f;
-    if (!pos && !bad) bad = 1 + c;
-    rc[c] = pos ? df_recip(Bk[c][c]) : df{0.0f, 0.0f};
+    for (int r = 0; r < P; ++r)
 #pragma unroll
-    for (int r = c + 1; r < P; ++r) {
-      Wb[r][c] = Bk[r][c];
-      Lb[r][c] = df_mul(Bk[r][c], rc[c]);
-    }
-#pragma unroll
-    for (int k = c + 1; k < P; ++k)
-#pragma unroll
-      for (int r = k; r < P; ++r) Bk[r][k] = df_fnms(Bk[r][k], Lb[r][c], Wb[k][c]);
-  }
-  if (tid == 0) {
-#pragma unroll
-    for (int c = 0; c < P; ++c) st_df(s_d[j + c], Bk[c][c]);
-    if (bad && !*s_bad) *s_bad = j + bad;
-  }
-  for (int i = j + P + tid; i < kb; i += NT) {
-    df x[P];
-#pragma unroll
-    for (int c = 0; c < P; ++c) x[c] = ld_df(sm[i * DG + j + c]);
+      for (int c = 0; c <= r; ++c) Bk[r][c] = ld_df(sm[(j + r) * DG + j + c]);
+    int bad = 0;
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-      const df w = x[c];
-      const df l = df_mul(w, rc[c]);
-      st_df(s_w[c * NB + i], w);
-      st_df(s_l[c * NB + i], l);
-      st_df(sm[i * DG + j + c], l);
+      const bool pos = Bk[c][c].hi > 0x1p-100f;
+      if (!pos && !bad) bad = 1 + c;
+      rc[c] = pos ? df_recip(Bk[c][c]) : df{0.0f, 0.0f};
 #pragma unroll
-      for (int k = c + 1; k < P; ++k) x[k] = df_fnms(x[k], l, Wb[k][c]);
+      for (int r = c + 1; r < P; ++r) {
+        Wb[r][c] = Bk[r][c];
+        Lb[r][c] = df_mul(Bk[r][c], rc[c]);
+      }
+#pragma unroll
+      for (int k = c + 1; k < P; ++k)
+#pragma unroll
+        for (int r = k; r < P; ++r) Bk[r][k] = df_fnms(Bk[r][k], Lb[r][c], Wb[k][c]);
+    }
+    if (tid == 0) {
+#pragma unroll
+      for (int c = 0; c < P; ++c) st_df(s_d[j + c], Bk[c][c]);
+      if (bad && !*s_bad) *s_bad = j + bad;
+    }
+    const int i = j + P + tid;
+    if (i < kb) {
+      df x[P];
+#pragma unroll
+      for (int c = 0; c < P; ++c) x[c] = ld_df(sm[i * DG + j + c]);
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        const df w = x[c];
+        const df l = df_mul(w, rc[c]);
+        st_df(s_w[c * NB + i], w);
+        st_df(s_l[c * NB + i], l);
+        st_df(sm[i * DG + j + c], l);
+#pragma unroll
+        for (int k = c + 1; k < P; ++k) x[k] = df_fnms(x[k], l, Wb[k][c]);
+      }
     }
   }
   __syncthreads();
