@@ -38,8 +38,8 @@ DTYPE_NOTE = ("exact 32-bit integer recurrence; uniforms formed in integers; nor
 # and the recurrence is integer multiply-add work), so beside the HBM
 # roofline the bench reports issue slots: 4 warp-instructions per cycle per SM.
 INSTR_PER_OUTPUT = {("raw", "u32"): 27.4, ("uniform", "f64"): 43.0, ("uniform", "f32"): 37.5,
-                    ("normal", "f64"): 117.5, ("normal", "f32"): 91.2,
-                    ("exponential", "f32"): 64.7, ("exponential", "f64"): 107.9}
+                    ("normal", "f64"): 117.5, ("normal", "f32"): 86.2,
+                    ("exponential", "f32"): 60.8, ("exponential", "f64"): 107.9}
 
 
 def env_rank():

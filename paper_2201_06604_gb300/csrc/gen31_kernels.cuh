@@ -110,6 +110,20 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
       put_f64(w + 8 * p + 4, xb);
       put_f64(w + 8 * p + 6, yb);
     }
+  } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F32 && UE % 4 == 0) {
+#pragma unroll
+    for (int p = 0; p < UE / 4; ++p) {
+      const uint32_t z1a = 2u * g31::step(s);
+      const uint32_t z2a = 2u * g31::step(s);
+      const uint32_t z1b = 2u * g31::step(s);
+      const uint32_t z2b = 2u * g31::step(s);
+      float xa, ya, xb, yb;
+      box_muller_f32_x2<UM2p32>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
+      w[4 * p] = __float_as_uint(xa);
+      w[4 * p + 1] = __float_as_uint(ya);
+      w[4 * p + 2] = __float_as_uint(xb);
+      w[4 * p + 3] = __float_as_uint(yb);
+    }
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
@@ -126,6 +140,16 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
         w[2 * p] = __float_as_uint(x);
         w[2 * p + 1] = __float_as_uint(y);
       }
+    }
+  } else if constexpr (DT == MRG_F32 && UE % 2 == 0) {   // exponential, two draws per packed evaluation
+#pragma unroll
+    for (int e = 0; e < UE; e += 2) {
+      const uint32_t za = 2u * g31::step(s);
+      const uint32_t zb = 2u * g31::step(s);
+      float ea, eb;
+      exp_f32_x2<UM2p32>(za, zb, tab, c.ir_hi, c.ir_lo, ea, eb);
+      w[e] = __float_as_uint(ea);
+      w[e + 1] = __float_as_uint(eb);
     }
   } else {  // exponential: -ln(u) / rate
 #pragma unroll

@@ -5,9 +5,9 @@
 //   jump_kernel      x <- A^k x for every stream (skip, substreams, advance)
 //   generate_kernel  the recurrence in registers + transform + 32-byte stores
 //   fused_kernel     no-store consumer: quarter-circle count and normal sum
-//   transform_kernel the transforms of caller-provided raw draws (fp64
-//                    normals into a 32-byte aligned output:
-//                    transform_normal_f64_x2_kernel, two pairs per thread)
+//   transform_kernel the transforms of caller-provided raw draws (normals
+//                    and fp32 exponentials into an output aligned to four
+//                    outputs: transform_x2_kernel, four draws per thread)
 //   fill_kernel      write-only stream (the write ceiling generate is held to)
 //   matrix_kernel    the paper's work-item matrix layout (matrix_kernels.cuh)
 //   fisher_kernel    Monte Carlo Fisher's exact test (fisher_kernels.cuh)
@@ -222,6 +222,20 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
       put_f64(w + 8 * p + 4, xb);
       put_f64(w + 8 * p + 6, yb);
     }
+  } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F32 && UE % 4 == 0) {
+#pragma unroll
+    for (int p = 0; p < UE / 4; ++p) {
+      const uint32_t z1a = step_fast(s, c.k1, c.k2);
+      const uint32_t z2a = step_fast(s, c.k1, c.k2);
+      const uint32_t z1b = step_fast(s, c.k1, c.k2);
+      const uint32_t z2b = step_fast(s, c.k1, c.k2);
+      float xa, ya, xb, yb;
+      box_muller_f32_x2<UM32k3a>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
+      w[4 * p] = __float_as_uint(xa);
+      w[4 * p + 1] = __float_as_uint(ya);
+      w[4 * p + 2] = __float_as_uint(xb);
+      w[4 * p + 3] = __float_as_uint(yb);
+    }
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
@@ -238,6 +252,16 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
         w[2 * p] = __float_as_uint(x);
         w[2 * p + 1] = __float_as_uint(y);
       }
+    }
+  } else if constexpr (DT == MRG_F32 && UE % 2 == 0) {   // exponential, two draws per packed evaluation
+#pragma unroll
+    for (int e = 0; e < UE; e += 2) {
+      const uint32_t za = step_fast(s, c.k1, c.k2);
+      const uint32_t zb = step_fast(s, c.k1, c.k2);
+      float ea, eb;
+      exp_f32_x2<UM32k3a>(za, zb, tab, c.ir_hi, c.ir_lo, ea, eb);
+      w[e] = __float_as_uint(ea);
+      w[e + 1] = __float_as_uint(eb);
     }
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
@@ -453,36 +477,71 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
   }
 }
 
-// fp64 normals into a 32-byte aligned output: each thread transforms four
-// draws (two pairs) with the packed evaluation and stores 32 bytes; a last
+// Normals and fp32 exponentials into an output aligned to four outputs
+// (32 bytes for fp64, 16 for fp32): each thread transforms four draws with
+// the packed two-at-a-time evaluation and stores them in one vector; a last
 // unit of fewer than four draws takes the scalar one (bit-identical results
 // either way; the launcher picks this kernel by the output's alignment, so
 // both evaluations are reachable through the same entry point).
-__global__ void __launch_bounds__(256) transform_normal_f64_x2_kernel(const uint32_t* __restrict__ z,
-                                                                     uint64_t n, char* out) {
+template <int DIST, int DT>
+__global__ void __launch_bounds__(256) transform_x2_kernel(const uint32_t* __restrict__ z, uint64_t n,
+                                                           char* out, Consts c) {
+  static_assert(DIST == MRG_NORMAL || (DIST == MRG_EXPONENTIAL && DT == MRG_F32), "packed forms");
   __shared__ float4 s_tab[TAB_ENTRIES];
   load_ttab(s_tab);
+  constexpr int ES = DT == MRG_F64 ? 8 : 4;
   const uint64_t units = (n + 3) / 4;
   const uint64_t step_all = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += step_all) {
     const uint64_t i0 = 4 * u;
-    uint64_t* d = reinterpret_cast<uint64_t*>(out) + i0;
+    char* d = out + i0 * ES;
     if (i0 + 4 <= n) {
-      uint32_t w[8];
-      uint64_t xa, ya, xb, yb;
-      box_muller_f64_x2<UM32k3a>(z[i0], z[i0 + 1], z[i0 + 2], z[i0 + 3], s_tab, xa, ya, xb, yb);
-      put_f64(w, xa);
-      put_f64(w + 2, ya);
-      put_f64(w + 4, xb);
-      put_f64(w + 6, yb);
-      store_vec<32>(reinterpret_cast<char*>(d), w);
-    } else {
-      for (uint64_t i = i0; i < n; i += 2) {
-        uint64_t x, y;
-        box_muller_f64(z[i], i + 1 < n ? z[i + 1] : 1u, s_tab, x, y);
-        d[i - i0] = x;
-        if (i + 1 < n) d[i + 1 - i0] = y;
+      uint32_t w[4 * ES / 4];
+      if constexpr (DIST == MRG_NORMAL && DT == MRG_F64) {
+        uint64_t xa, ya, xb, yb;
+        box_muller_f64_x2<UM32k3a>(z[i0], z[i0 + 1], z[i0 + 2], z[i0 + 3], s_tab, xa, ya, xb, yb);
+        put_f64(w, xa);
+        put_f64(w + 2, ya);
+        put_f64(w + 4, xb);
+        put_f64(w + 6, yb);
+      } else if constexpr (DIST == MRG_NORMAL) {
+        float xa, ya, xb, yb;
+        box_muller_f32_x2<UM32k3a>(z[i0], z[i0 + 1], z[i0 + 2], z[i0 + 3], s_tab, xa, ya, xb, yb);
+        w[0] = __float_as_uint(xa);
+        w[1] = __float_as_uint(ya);
+        w[2] = __float_as_uint(xb);
+        w[3] = __float_as_uint(yb);
+      } else {
+        float e0, e1, e2, e3;
+        exp_f32_x2<UM32k3a>(z[i0], z[i0 + 1], s_tab, c.ir_hi, c.ir_lo, e0, e1);
+        exp_f32_x2<UM32k3a>(z[i0 + 2], z[i0 + 3], s_tab, c.ir_hi, c.ir_lo, e2, e3);
+        w[0] = __float_as_uint(e0);
+        w[1] = __float_as_uint(e1);
+        w[2] = __float_as_uint(e2);
+        w[3] = __float_as_uint(e3);
       }
+      store_vec<4 * ES>(d, w);
+    } else if constexpr (DIST == MRG_NORMAL) {
+      for (uint64_t i = i0; i < n; i += 2) {
+        const uint32_t z2 = i + 1 < n ? z[i + 1] : 1u;
+        uint32_t w[4];
+        if constexpr (DT == MRG_F64) {
+          uint64_t x, y;
+          box_muller_f64(z[i], z2, s_tab, x, y);
+          put_f64(w, x);
+          put_f64(w + 2, y);
+        } else {
+          float x, y;
+          box_muller_f32(z[i], z2, s_tab, x, y);
+          w[0] = __float_as_uint(x);
+          w[1] = __float_as_uint(y);
+        }
+        store_vec<ES>(out + i * ES, w);
+        if (i + 1 < n) store_vec<ES>(out + (i + 1) * ES, w + ES / 4);
+      }
+    } else {
+      for (uint64_t i = i0; i < n; ++i)
+        reinterpret_cast<float*>(out)[i] = exp_f32(z[i], s_tab, c.ir_hi, c.ir_lo);
     }
   }
 }
@@ -915,7 +974,9 @@ cudaError_t preload_kernels() {
   load_fn(jump31_kernel, bad);
   load_fn(jump_kernel, bad);
   load_fn(fused_kernel, bad);
-  load_fn(transform_normal_f64_x2_kernel, bad);
+  load_fn(transform_x2_kernel<MRG_NORMAL, MRG_F64>, bad);
+  load_fn(transform_x2_kernel<MRG_NORMAL, MRG_F32>, bad);
+  load_fn(transform_x2_kernel<MRG_EXPONENTIAL, MRG_F32>, bad);
   load_fn(batch_kernel, bad);
   load_fn(serve_kernel, bad);
   return bad ? cudaErrorInvalidDeviceFunction : cudaSuccess;
@@ -949,8 +1010,18 @@ cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype,
     c.ir_lo = (float)(ir - (double)c.ir_hi);
   }
   char* o = reinterpret_cast<char*>(out);
-  if (dist == MRG_NORMAL && dtype == MRG_F64 && (reinterpret_cast<uintptr_t>(out) & 31) == 0) {
-    transform_normal_f64_x2_kernel<<<grid_for((n + 3) / 4, 256, 8), 256, 0, st>>>(z, n, o);
+  const uintptr_t al = reinterpret_cast<uintptr_t>(out);
+  const unsigned grid4 = grid_for((n + 3) / 4, 256, 8);
+  if (dist == MRG_NORMAL && dtype == MRG_F64 && (al & 31) == 0) {
+    transform_x2_kernel<MRG_NORMAL, MRG_F64><<<grid4, 256, 0, st>>>(z, n, o, c);
+    return after_launch();
+  }
+  if (dist == MRG_NORMAL && dtype == MRG_F32 && (al & 15) == 0) {
+    transform_x2_kernel<MRG_NORMAL, MRG_F32><<<grid4, 256, 0, st>>>(z, n, o, c);
+    return after_launch();
+  }
+  if (dist == MRG_EXPONENTIAL && dtype == MRG_F32 && (al & 15) == 0) {
+    transform_x2_kernel<MRG_EXPONENTIAL, MRG_F32><<<grid4, 256, 0, st>>>(z, n, o, c);
     return after_launch();
   }
   const uint64_t units = dist == MRG_NORMAL ? (n + 1) / 2 : n;

@@ -204,10 +204,12 @@ __device__ __forceinline__ df ln_u_lite_raw_m(uint32_t z, const float4* __restri
   poly = __fmaf_rn(rh, poly, -0.25f);
   poly = __fmaf_rn(rh, poly, 1.0f / 3.0f);
   poly = __fmaf_rn(rh, poly, -0.5f);
-  const float tail = __fmul_rn(__fmul_rn(rh, rh), poly);
+  // re + the tail r^2 poly, rounded once (an FMA: the packed evaluation's
+  // compiler would fuse a separate product into the add anyway)
+  const float rt = __fmaf_rn(__fmul_rn(rh, rh), poly, re);
   const float2 L = log_ck_shift(tab, s, k);
   const df u = fast_two_sum(L.x, rh);        // |ln(C_k / (M 2^s))| >= |r|, or both 0
-  const float lo = __fadd_rn(u.lo, __fadd_rn(L.y, __fadd_rn(re, tail)));
+  const float lo = __fadd_rn(u.lo, __fadd_rn(L.y, rt));
   return df{u.hi, lo};  // not renormalised: in the top bucket |lo| reaches 2^-9 |hi|
 }
 

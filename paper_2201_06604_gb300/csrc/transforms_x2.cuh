@@ -1,6 +1,7 @@
-// transforms_x2.cuh -- the double-float Box-Muller transform of two pairs at
-// once with packed fp32x2 instructions (add/sub/mul/fma .rn.f32x2: two IEEE
-// fp32 operations in one instruction).
+// transforms_x2.cuh -- the double-float transforms of two draws (Box-Muller:
+// two pairs) at once with packed fp32x2 instructions (add/sub/mul/fma
+// .rn.f32x2: two IEEE fp32 operations in one instruction): fp64 normals,
+// the radius R of fp32 normals, fp32 exponentials.
 //
 // The transform kernels are bound by instruction issue, not by the FP32
 // pipes (about half busy): a packed instruction carries two fp32 operations
@@ -228,6 +229,80 @@ __device__ __forceinline__ void box_muller_f64_x2(uint32_t z1a, uint32_t z2a, ui
   ya = df_abs_to_f64_bits(df{yha, yla}, ssa);
   xb = df_abs_to_f64_bits(df{xhb, xlb}, scb);
   yb = df_abs_to_f64_bits(df{yhb, ylb}, ssb);
+}
+
+// ---- fp32 outputs ------------------------------------------------------------
+
+// ln(z / M) of two draws to ~2^-34 relative, not renormalised
+// (ln_u_lite_raw_m on each).
+template <class UM>
+__device__ __forceinline__ df2 ln_u_lite_raw_m2(uint32_t za, uint32_t zb,
+                                                const float4* __restrict__ tab) {
+  uint32_t sa, sb;
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(sa) : "r"(za));
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(sb) : "r"(zb));
+  const uint32_t zna = za << sa, znb = zb << sb;
+  const uint32_t ka = (zna >> 24) & 127u, kb = (znb >> 24) & 127u;
+  const uint32_t cka = ka == 127u ? UM::TOP_CK : 0x80800000u + (ka << 24);
+  const uint32_t ckb = kb == 127u ? UM::TOP_CK : 0x80800000u + (kb << 24);
+  const float2 Ta = log_inv_ck(tab, ka), Tb = log_inv_ck(tab, kb);
+  const f2 dfl = pk((float)(int32_t)(zna - cka), (float)(int32_t)(znb - ckb));
+  const f2 Tx = pk(Ta.x, Tb.x), Ty = pk(Ta.y, Tb.y);
+  const f2 rh = mul2(Tx, dfl);
+  const f2 re = fma2(Ty, dfl, fma2(Tx, dfl, neg2(rh)));    // r = rh + re
+  f2 poly = fma2(rh, bc(-1.0f / 6.0f), bc(0.2f));
+  poly = fma2(rh, poly, bc(-0.25f));
+  poly = fma2(rh, poly, bc(1.0f / 3.0f));
+  poly = fma2(rh, poly, bc(-0.5f));
+  const f2 rt = fma2(mul2(rh, rh), poly, re);
+  const float2 La = log_ck_shift(tab, sa, ka), Lb = log_ck_shift(tab, sb, kb);
+  const df2 u = fast_two_sum2(pk(La.x, Lb.x), rh);
+  return df2{u.hi, add2(u.lo, add2(pk(La.y, Lb.y), rt))};
+}
+
+// RN32 of a b for two df a and b (df_mul_to_f32 on each).
+__device__ __forceinline__ f2 df_mul_to_f32_2(df2 a, df2 b) {
+  return fma2(a.hi, b.hi, fma2(a.hi, b.lo, mul2(a.lo, b.hi)));
+}
+
+__device__ __forceinline__ float with_sign(float v, uint32_t sgn) {
+  return __uint_as_float(__float_as_uint(v) ^ sgn);
+}
+
+// Two Box-Muller pairs (z1a, z2a) and (z1b, z2b) to fp32, identical to
+// box_muller_f32_m on each pair.  Only R = sqrt(-2 ln u1) is packed; sin and
+// cos stay one pair at a time.  A packed instruction occupies both FP32
+// sub-pipes, and the heavy one also runs the recurrence's IMADs and the
+// moves that pair operands: with sin/cos packed too, that pipe became the
+// limit (measured per 2^30 outputs: all packed 3.17 ms, sin/cos only 3.18,
+// none 3.10-3.13, the log and square root only 2.99).
+template <class UM>
+__device__ __forceinline__ void box_muller_f32_x2(uint32_t z1a, uint32_t z2a, uint32_t z1b,
+                                                  uint32_t z2b, const float4* __restrict__ tab,
+                                                  float& xa, float& ya, float& xb, float& yb) {
+  const df2 lr = ln_u_lite_raw_m2<UM>(z1a, z1b, tab);
+  const df2 l = fast_two_sum2(lr.hi, lr.lo);                 // ln_u_lite_m
+  f2 nRh;
+  const df2 R = df_sqrt_m2l2(l, nRh);
+  float rha, rhb, rla, rlb;
+  upk(R.hi, rha, rhb);
+  upk(R.lo, rla, rlb);
+  df sn, cs;
+  uint32_t ss, sc;
+  sincos_turn_lite_m<UM>(z2a, tab, sn, cs, ss, sc);
+  xa = with_sign(df_mul_to_f32(df{rha, rla}, cs.hi, cs.lo), sc);
+  ya = with_sign(df_mul_to_f32(df{rha, rla}, sn.hi, sn.lo), ss);
+  sincos_turn_lite_m<UM>(z2b, tab, sn, cs, ss, sc);
+  xb = with_sign(df_mul_to_f32(df{rhb, rlb}, cs.hi, cs.lo), sc);
+  yb = with_sign(df_mul_to_f32(df{rhb, rlb}, sn.hi, sn.lo), ss);
+}
+
+// -ln(u) / rate of two draws to fp32, identical to exp_f32_m on each.
+template <class UM>
+__device__ __forceinline__ void exp_f32_x2(uint32_t za, uint32_t zb, const float4* __restrict__ tab,
+                                           float ir_hi, float ir_lo, float& ea, float& eb) {
+  const df2 l = ln_u_lite_raw_m2<UM>(za, zb, tab);
+  upk(df_mul_to_f32_2(df2{bc(ir_hi), bc(ir_lo)}, l), ea, eb);
 }
 
 }  // namespace mrg

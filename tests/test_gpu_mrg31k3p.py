@@ -153,17 +153,21 @@ def test_materialised_full_size_sampled(M, dist, dtype):
     del out
 
 
+@pytest.mark.parametrize("dist,dt", [("normal", torch.float64), ("normal", torch.float32),
+                                     ("exponential", torch.float32)])
 @pytest.mark.parametrize("ns,n", [(300, 4096), (33, 1002)])
-def test_normal_f64_packed_equals_scalar(M, ns, n):
-    # 32-byte aligned rows take the packed two-pair evaluation, a pitch that
-    # breaks the alignment the one-pair one: same streams, same bits
+def test_packed_equals_scalar(M, ns, n, dist, dt):
+    # rows aligned for 16- or 32-byte stores take the packed two-at-a-time
+    # evaluation, a pitch of one element more the one-at-a-time one: same
+    # streams, same bits
     a = M.create_streams(ns, seed=SEED, generator="mrg31k3p")
     b = M.create_streams(ns, seed=SEED, generator="mrg31k3p")
-    got_a = M.generate(a, n, "normal", torch.float64)
-    big = torch.zeros((ns, n + 1), dtype=torch.float64, device="cuda")
-    got_b = M.generate(b, n, "normal", torch.float64, out=big[:, 1:])
+    got_a = M.generate(a, n, dist, dt, rate=0.6)
+    big = torch.zeros((ns, n + 1), dtype=dt, device="cuda")
+    got_b = M.generate(b, n, dist, dt, rate=0.6, out=big[:, 1:])
     torch.cuda.synchronize()
-    x = got_a[:ns, :n].cpu().numpy().view(np.uint64)
-    y = got_b[:ns, :n].cpu().numpy().view(np.uint64)
+    iv = np.uint64 if dt == torch.float64 else np.uint32
+    x = got_a[:ns, :n].cpu().numpy().view(iv)
+    y = got_b[:ns, :n].cpu().numpy().view(iv)
     assert np.array_equal(x, y), np.argwhere(x != y)[:5]
     assert np.array_equal(states(M, a), states(M, b))

@@ -335,20 +335,24 @@ def test_unaddressable_extent_is_rejected(M):
     assert rc == M.ERANGE
 
 
+@pytest.mark.parametrize("dist,dt", [("normal", torch.float64), ("normal", torch.float32),
+                                     ("exponential", torch.float32)])
 @pytest.mark.parametrize("ns,n", [(300, 4096), (33, 1002), (1, 9)])
-def test_normal_f64_packed_equals_scalar(M, ns, n):
-    # fp64 normals into 32-byte aligned rows are evaluated two pairs at a time
-    # with packed fp32x2 instructions; a row pitch that breaks the alignment
-    # selects the one-pair evaluation.  Same streams, same bits.
+def test_packed_equals_scalar(M, ns, n, dist, dt):
+    # normals and fp32 exponentials into rows aligned for 16- or 32-byte
+    # stores are evaluated two draws (two pairs) at a time with packed fp32x2
+    # instructions; a row pitch of one element more selects the one-at-a-time
+    # evaluation.  Same streams, same bits.
     a = M.create_streams(ns, seed=SEED)
     b = M.create_streams(ns, seed=SEED)
     M.skip(a, 999)
     M.skip(b, 999)
-    got_a = M.generate(a, n, "normal", torch.float64)
-    big = torch.zeros((ns, n + 1), dtype=torch.float64, device="cuda")
-    got_b = M.generate(b, n, "normal", torch.float64, out=big[:, 1:])
+    got_a = M.generate(a, n, dist, dt, rate=1.7)
+    big = torch.zeros((ns, n + 1), dtype=dt, device="cuda")
+    got_b = M.generate(b, n, dist, dt, rate=1.7, out=big[:, 1:])
     torch.cuda.synchronize()
-    x = got_a[:ns, :n].cpu().numpy().view(np.uint64)
-    y = got_b[:ns, :n].cpu().numpy().view(np.uint64)
+    iv = np.uint64 if dt == torch.float64 else np.uint32
+    x = got_a[:ns, :n].cpu().numpy().view(iv)
+    y = got_b[:ns, :n].cpu().numpy().view(iv)
     assert np.array_equal(x, y), np.argwhere(x != y)[:5]
     assert np.array_equal(host_states(M, a), host_states(M, b))

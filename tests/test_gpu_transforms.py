@@ -138,22 +138,29 @@ def test_odd_normal_count_and_zero_crossings(mrg):
     assert np.abs(got - ref).max() <= 1e-12
 
 
-def test_normal_f64_packed_and_scalar_evaluations_identical(mrg):
-    # A 32-byte aligned fp64 output takes the packed two-pair evaluation, a
-    # misaligned one the scalar one-pair evaluation: bit-identical outputs on
-    # random draws and on every reduction boundary (the accuracy tests above
-    # check the aligned path against the oracle).
+PACKED = [("normal", torch.float64), ("normal", torch.float32), ("exponential", torch.float32)]
+
+
+@pytest.mark.parametrize("dist,dt", PACKED)
+def test_packed_and_scalar_evaluations_identical(mrg, dist, dt):
+    # An output aligned to four elements (32 bytes for fp64, 16 for fp32)
+    # takes the packed two-at-a-time evaluation, a misaligned one the scalar
+    # evaluation: bit-identical outputs on random draws and on every
+    # reduction boundary (the accuracy tests above check the aligned path
+    # against the oracle).
     z = all_inputs(n_random=1 << 20)
     zt = torch.from_numpy(z.view(np.int32)).cuda()
     n = z.size
-    aligned = mrg.transform(zt, "normal", torch.float64)
-    assert aligned.data_ptr() % 32 == 0
-    big = torch.full((n + 5,), -7.0, dtype=torch.float64, device="cuda")
+    al = 8 * dt.itemsize if dt == torch.float64 else 4 * dt.itemsize
+    aligned = mrg.transform(zt, dist, dt, rate=2.5)
+    assert aligned.data_ptr() % al == 0
+    big = torch.full((n + 5,), -7.0, dtype=dt, device="cuda")
     shifted = big[1:n + 1]
-    assert shifted.data_ptr() % 32 != 0
-    mrg.transform(zt, "normal", torch.float64, out=shifted)
-    a = aligned.cpu().numpy().view(np.uint64)
-    b = shifted.cpu().numpy().view(np.uint64)
+    assert shifted.data_ptr() % al != 0
+    mrg.transform(zt, dist, dt, rate=2.5, out=shifted)
+    iv = np.uint64 if dt == torch.float64 else np.uint32
+    a = aligned.cpu().numpy().view(iv)
+    b = shifted.cpu().numpy().view(iv)
     assert np.array_equal(a, b), np.argwhere(a != b)[:5]
     assert big[0].item() == -7.0 and (big[n + 1:] == -7.0).all()
 
@@ -169,4 +176,22 @@ def test_normal_f64_packed_tails(mrg, n):
     zz = np.concatenate([z, np.ones(n % 2, dtype=np.uint32)])
     ref = O.box_muller_of(zz)[:n]
     assert np.abs(got.cpu().numpy() - ref).max() <= 1e-12
+    assert (big[n:] == -7.0).all()
+
+
+@pytest.mark.parametrize("dist", ["normal", "exponential"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 1001, 4099])
+def test_f32_packed_tails(mrg, dist, n):
+    # the same for fp32 outputs: a 16-byte aligned output whose count ends
+    # inside a unit of four draws equals the misaligned (scalar) evaluation
+    z = all_inputs(n_random=4096, seed=n)[:n]
+    zt = torch.from_numpy(z.view(np.int32)).cuda()
+    big = torch.full((n + 8,), -7.0, dtype=torch.float32, device="cuda")
+    got = mrg.transform(zt, dist, torch.float32, rate=0.3, out=big[:n])
+    assert big.data_ptr() % 16 == 0
+    ref = mrg.transform(zt, dist, torch.float32, rate=0.3,
+                        out=torch.empty(n + 1, dtype=torch.float32, device="cuda")[1:])
+    a = got.cpu().numpy().view(np.uint32)
+    b = ref.cpu().numpy().view(np.uint32)
+    assert np.array_equal(a, b), np.argwhere(a != b)[:5]
     assert (big[n:] == -7.0).all()
