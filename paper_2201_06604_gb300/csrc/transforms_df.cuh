@@ -451,11 +451,11 @@ __device__ __forceinline__ void box_muller_f32_m(uint32_t z1, uint32_t z2,
 // the ~2^-34 log and the lite sin/cos (absolute error ~2^-38), signed,
 // added error-free, times R with the exact leading product.  Absolute
 // error <= ~2^-34 per pair (R <= 6.7), whether or not cos and sin cancel.
+// box_muller_sum_lite_rest_m is the part after R, given R (the fused
+// consumer computes R of two pairs at once); box_muller_sum_lite_m the whole.
 template <class UM>
-__device__ __forceinline__ df box_muller_sum_lite_m(uint32_t z1, uint32_t z2,
-                                                    const float4* __restrict__ tab) {
-  const df l = ln_u_lite_m<UM>(z1, tab);
-  const df R = df_sqrt_raw(df{-2.0f * l.hi, -2.0f * l.lo});
+__device__ __forceinline__ df box_muller_sum_lite_rest_m(df R, uint32_t z2,
+                                                         const float4* __restrict__ tab) {
   df sn, cs;
   uint32_t sgn_s, sgn_c;
   sincos_turn_lite_m<UM>(z2, tab, sn, cs, sgn_s, sgn_c);
@@ -466,6 +466,13 @@ __device__ __forceinline__ df box_muller_sum_lite_m(uint32_t z1, uint32_t z2,
   const df t = two_sum(ch, sh);
   const float tl = __fadd_rn(t.lo, __fadd_rn(cl, sl));
   return df_mul_split(R, df{t.hi, tl});
+}
+
+template <class UM>
+__device__ __forceinline__ df box_muller_sum_lite_m(uint32_t z1, uint32_t z2,
+                                                    const float4* __restrict__ tab) {
+  const df l = ln_u_lite_m<UM>(z1, tab);
+  return box_muller_sum_lite_rest_m<UM>(df_sqrt_raw(df{-2.0f * l.hi, -2.0f * l.lo}), z2, tab);
 }
 
 // -ln(u) / rate for fp32 outputs: the ~2^-34 log times -1/rate (a float

@@ -297,6 +297,23 @@ __device__ __forceinline__ void box_muller_f32_x2(uint32_t z1a, uint32_t z2a, ui
   yb = with_sign(df_mul_to_f32(df{rhb, rlb}, sn.hi, sn.lo), ss);
 }
 
+// X + Y of two Box-Muller pairs as float pairs (box_muller_sum_lite_m on
+// each), with R of both packed as for the fp32 normals.
+template <class UM>
+__device__ __forceinline__ void box_muller_sum_lite_x2(uint32_t z1a, uint32_t z2a, uint32_t z1b,
+                                                       uint32_t z2b, const float4* __restrict__ tab,
+                                                       df& va, df& vb) {
+  const df2 lr = ln_u_lite_raw_m2<UM>(z1a, z1b, tab);
+  const df2 l = fast_two_sum2(lr.hi, lr.lo);
+  f2 nRh;
+  const df2 R = df_sqrt_m2l2(l, nRh);
+  float rha, rhb, rla, rlb;
+  upk(R.hi, rha, rhb);
+  upk(R.lo, rla, rlb);
+  va = box_muller_sum_lite_rest_m<UM>(df{rha, rla}, z2a, tab);
+  vb = box_muller_sum_lite_rest_m<UM>(df{rhb, rlb}, z2b, tab);
+}
+
 // -ln(u) / rate of two draws to fp32, identical to exp_f32_m on each.
 template <class UM>
 __device__ __forceinline__ void exp_f32_x2(uint32_t za, uint32_t zb, const float4* __restrict__ tab,
