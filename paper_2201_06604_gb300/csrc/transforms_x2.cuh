@@ -8,10 +8,12 @@
 // through one issue slot.  Every function below performs, element by
 // element, the fp32 operations of its scalar counterpart in
 // transforms_df.cuh with the same operands and the same rounding, so the
-// outputs are bit-identical to the scalar path's (which the batch, serving
-// and transform kernels use); only the integer parts (reductions, table
-// indices, the conversion to double bits) and the MUFU reciprocal square
-// root stay per element.
+// outputs are bit-identical to the scalar path's (which rows too narrowly
+// aligned for 16-byte stores, the last draws of a transform, an odd last
+// pair of the fused consumer and the matrix-layout kernel take; generate,
+// batched and served requests use the packed forms); only the integer
+// parts (reductions, table indices, the conversion to double bits) and the
+// MUFU reciprocal square root stay per element.
 //
 // Two rules keep that identity:
 //   * A scalar FMA negates an operand for free; a packed one cannot.  So
