@@ -755,24 +755,33 @@ __device__ __forceinline__ void st_df(dfs& x, df v) {
 template <int NTH>
 __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint64_t lda, int kb,
                                               int sc, dfs* dst, bool strict) {
-  // warp w takes rows w, w + NTH / 32, ..; its lanes run along the row
-  // (coalesced loads, no index division), four loads in flight per lane
+  // warp w takes rows w, w + NW, w + 2 NW, w + 3 NW (then the next four);
+  // its lanes run along the row (coalesced loads, no index division); the
+  // four rows' loads (up to 16 per lane, kb <= 128) are all in flight
+  // before the first conversion
   constexpr int NW = NTH / 32;
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-  for (int i = warp; i < kb; i += NW) {
-    const int len = strict ? i : i + 1;
-    const double* row = A + (uint64_t)i * lda;
-    for (int j0 = 0; j0 < len; j0 += 128) {
-      double v[4];
+  for (int i0 = warp; i0 < kb; i0 += 4 * NW) {
+    double v[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r * NW;
+      const int len = i < kb ? (strict ? i : i + 1) : 0;
+      const double* row = A + (uint64_t)i * lda;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u * 32 + lane;
-        v[u] = j < len ? row[j] : 0.0;
+        const int j = u * 32 + lane;
+        v[r][u] = j < len ? row[j] : 0.0;
       }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r * NW;
+      const int len = i < kb ? (strict ? i : i + 1) : 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u * 32 + lane;
-        if (j < len) st_df(dst[i * DG + j], df_of_scaled(v[u], sc));
+        const int j = u * 32 + lane;
+        if (j < len) st_df(dst[i * DG + j], df_of_scaled(v[r][u], sc));
       }
     }
   }
@@ -915,11 +924,13 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) ldl_diag_kernel(DiagArgs g) {
   int j = 0;
   for (; j + DIAG_P <= kb; j += DIAG_P) diag_pass<DIAG_P>(sm, s_w, s_l, s_d, s_pair, &s_bad, kb, j, tid);
   for (; j < kb; ++j) diag_pass<1>(sm, s_w, s_l, s_d, s_pair, &s_bad, kb, j, tid);
-  // outputs: L (strict lower part) and D into the matrix, D into d[]
-  for (int idx = tid; idx < kb * kb; idx += NT) {
-    const int i = idx / kb, j = idx - (idx / kb) * kb;
-    if (j < i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(ld_df(sm[i * DG + j]), 0);
-    else if (j == i) A[(uint64_t)i * g.lda + j] = f64_of_scaled(ld_df(s_d[i]), sc);
+  // outputs: L (strict lower part) and D into the matrix, one row per warp
+  // at a time with the lanes along it (the lower triangle only, no index
+  // division), and D into d[]
+  for (int i = warp; i < kb; i += NT / 32) {
+    double* row = A + (uint64_t)i * g.lda;
+    for (int j = lane; j <= i; j += 32)
+      row[j] = j < i ? f64_of_scaled(ld_df(sm[i * DG + j]), 0) : f64_of_scaled(ld_df(s_d[i]), sc);
   }
   for (int j = tid; j < kb; j += NT) g.d[b * g.d_mstride + g.k0 + j] = f64_of_scaled(ld_df(s_d[j]), sc);
   if (tid == 0 && s_bad) atomicCAS(&g.info[b], 0, (int)g.k0 + s_bad);
