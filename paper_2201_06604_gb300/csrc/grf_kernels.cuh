@@ -755,16 +755,17 @@ __device__ __forceinline__ void st_df(dfs& x, df v) {
 template <int NTH>
 __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint64_t lda, int kb,
                                               int sc, dfs* dst, bool strict) {
-  // warp w takes rows w, w + NW, w + 2 NW, w + 3 NW (then the next four);
-  // its lanes run along the row (coalesced loads, no index division); the
-  // four rows' loads (up to 16 per lane, kb <= 128) are all in flight
-  // before the first conversion
+  // warp w takes rows w, w + NW, .., w + (RW - 1) NW, then the next RW;
+  // its lanes run along the row (coalesced loads, no index division); a
+  // batch's loads (4 RW per lane, kb <= 128) are all in flight before the
+  // first conversion
   constexpr int NW = NTH / 32;
+  constexpr int RW = NW >= 32 ? 4 : 8;      // rows per batch (registers allow 8 in small blocks)
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-  for (int i0 = warp; i0 < kb; i0 += 4 * NW) {
-    double v[4][4];
+  for (int i0 = warp; i0 < kb; i0 += RW * NW) {
+    double v[RW][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RW; ++r) {
       const int i = i0 + r * NW;
       const int len = i < kb ? (strict ? i : i + 1) : 0;
       const double* row = A + (uint64_t)i * lda;
@@ -775,7 +776,7 @@ __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint
       }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RW; ++r) {
       const int i = i0 + r * NW;
       const int len = i < kb ? (strict ? i : i + 1) : 0;
 #pragma unroll
@@ -943,9 +944,9 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) ldl_diag_kernel(DiagArgs g) {
 // outer-product order (x = e_c; for m = c, c+1, ..: x_i -= L[i][m] x_m for
 // i > m -- backward stable per column), lanes over the rows, double-float
 // arithmetic, L from the matrix (fp64, written by ldl_diag_kernel).  Grid:
-// (columns / 8, matrices), 8 warps per CTA.  Writes B (fp64, 128 x 128,
+// (columns / INV_COLS, matrices), INV_COLS warps per CTA.  Writes B (fp64, 128 x 128,
 // zero outside kb x kb) to bx.
-constexpr int INV_COLS = 8;   // columns (warps) per CTA
+constexpr int INV_COLS = 8;   // columns (warps) per CTA (measured: 4 per CTA, one per SM sub-partition, was slower)
 
 __global__ void __launch_bounds__(INV_COLS * 32) ldl_inverse_kernel(const double* __restrict__ a,
                                                                     uint64_t lda, uint64_t a_mstride,
