@@ -468,7 +468,12 @@ int mrg_grf_simulate(const double* l, const double* d, uint64_t n, uint64_t lda,
   scale_sqrt_d_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, n, z, y, n, nsim, batch);
   if ((rc = after(cudaSuccess, "scale_sqrt_d_kernel"))) return rc;
   const dim3 grid((unsigned)((n + 7) / 8), batch);
-  lower_times_y_kernel<<<grid, 256, 0, st>>>(l, lda, n * lda, y, u, n, nsim, batch);
+  if (nsim <= 2)
+    lower_times_y_kernel<2><<<grid, 256, 0, st>>>(l, lda, n * lda, y, u, n, nsim, batch);
+  else if (nsim <= 4)
+    lower_times_y_kernel<4><<<grid, 256, 0, st>>>(l, lda, n * lda, y, u, n, nsim, batch);
+  else
+    lower_times_y_kernel<8><<<grid, 256, 0, st>>>(l, lda, n * lda, y, u, n, nsim, batch);
   return after(cudaSuccess, "lower_times_y_kernel");
 }
 

@@ -1069,7 +1069,8 @@ __global__ void __launch_bounds__(256) equil_apply_kernel(double* __restrict__ a
 // Step 4: U = L D^(1/2) Z for nsim columns of standard normals per matrix.
 // z and u are [batch][nsim][n] (one simulation contiguous); y = D^(1/2) z is
 // formed first, then one warp per row i accumulates sum_{j <= i} L_ij y_j
-// for every simulation (L_ii = 1) in fp64.
+// for every simulation (L_ii = 1) in fp64, four partial sums per lane and
+// simulation.
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) scale_sqrt_d_kernel(const double* __restrict__ d,
@@ -1085,13 +1086,18 @@ __global__ void __launch_bounds__(256) scale_sqrt_d_kernel(const double* __restr
   y[t] = sqrt(d[b * d_mstride + j]) * z[t];
 }
 
-constexpr int SIM_MAX = 8;   // simulations handled per pass of a row
-
+// SP simulations per pass of a row; four independent accumulators per
+// simulation and lane, so that four loads of the row (and their y) are in
+// flight and four FMA chains interleave (the FP64 pipe, 1.6 DFMA per cycle
+// per SM, allows ~0.25 ms for four 5580 x 5580 factors and two simulations;
+// one chain per lane left the kernel waiting on its loads at 1.1 ms).
+template <int SP>
 __global__ void __launch_bounds__(256) lower_times_y_kernel(const double* __restrict__ l,
                                                             uint64_t ldl, uint64_t l_mstride,
                                                             const double* __restrict__ y,
                                                             double* __restrict__ u, uint64_t n,
                                                             uint32_t nsim, uint32_t batch) {
+  constexpr int U = 4;
   const uint64_t row = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t b = blockIdx.y;
@@ -1099,25 +1105,41 @@ __global__ void __launch_bounds__(256) lower_times_y_kernel(const double* __rest
   const double* lr = l + b * l_mstride + row * ldl;
   const double* yb = y + (uint64_t)b * nsim * n;
   double* ub = u + (uint64_t)b * nsim * n;
-  for (uint32_t s0 = 0; s0 < nsim; s0 += SIM_MAX) {
-    double acc[SIM_MAX];
+  const uint64_t len = row + 1;                 // L_row,row = 1 (unit diagonal)
+  for (uint32_t s0 = 0; s0 < nsim; s0 += SP) {
+    double acc[SP][U];
 #pragma unroll
-    for (int s = 0; s < SIM_MAX; ++s) acc[s] = 0.0;
-    for (uint64_t j = lane; j <= row; j += 32) {
+    for (int s = 0; s < SP; ++s)
+#pragma unroll
+      for (int k = 0; k < U; ++k) acc[s][k] = 0.0;
+    uint64_t j0 = 0;
+    for (; j0 + 32 * U <= len; j0 += 32 * U) {
+      double lv[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint64_t j = j0 + 32 * k + lane;
+        lv[k] = j == row ? 1.0 : lr[j];
+      }
+#pragma unroll
+      for (int s = 0; s < SP; ++s)
+        if (s0 + s < nsim) {
+          const double* ys = yb + (uint64_t)(s0 + s) * n + j0 + lane;
+#pragma unroll
+          for (int k = 0; k < U; ++k) acc[s][k] = fma(lv[k], ys[32 * k], acc[s][k]);
+        }
+    }
+    for (uint64_t j = j0 + lane; j < len; j += 32) {
       const double lij = j == row ? 1.0 : lr[j];
 #pragma unroll
-      for (int s = 0; s < SIM_MAX; ++s)
-        if (s0 + s < nsim) acc[s] = fma(lij, yb[(uint64_t)(s0 + s) * n + j], acc[s]);
+      for (int s = 0; s < SP; ++s)
+        if (s0 + s < nsim) acc[s][0] = fma(lij, yb[(uint64_t)(s0 + s) * n + j], acc[s][0]);
     }
 #pragma unroll
-    for (int s = 0; s < SIM_MAX; ++s) {
+    for (int s = 0; s < SP; ++s) {
+      double v = (acc[s][0] + acc[s][1]) + (acc[s][2] + acc[s][3]);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int s = 0; s < SIM_MAX; ++s)
-        if (s0 + s < nsim) ub[(uint64_t)(s0 + s) * n + row] = acc[s];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && s0 + s < nsim) ub[(uint64_t)(s0 + s) * n + row] = v;
     }
   }
 }
