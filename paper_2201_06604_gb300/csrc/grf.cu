@@ -200,13 +200,15 @@ int mrg_grf_matern_raster(const mrg_matern_params* params, uint32_t batch, uint3
   const MaternParams* dprm = static_cast<const MaternParams*>(scratch);
   double* table = reinterpret_cast<double*>(static_cast<char*>(scratch) + 4096);
   const uint64_t per_t = (2ull * nrow - 1) * (2ull * ncol - 1);
-  const uint64_t nt = per_t * batch;
+  const uint64_t nt = (per_t / 2 + 1) * batch;      // one thread per mirrored pair of offsets
   matern_offsets_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(dprm, batch, nrow, ncol, cell,
                                                                        table);
   rc = after(cudaSuccess, "matern_offsets_kernel");
   if (rc) return rc;
-  const int grid = mrg::sm_count() * 8;
-  matern_fill_kernel<<<grid, 256, 0, st>>>(table, batch, nrow, ncol, cov, ld, n * ld);
+  const uint64_t items = (uint64_t)batch * n * ((n + 1023) / 1024);
+  const int grid = (int)std::min<uint64_t>(items, (uint64_t)mrg::sm_count() * 32);
+  const int vec = reinterpret_cast<uintptr_t>(cov) % 32 == 0 && ld % 4 == 0;
+  matern_fill_kernel<<<grid, 256, 0, st>>>(table, batch, nrow, ncol, cov, ld, n * ld, vec);
   return after(cudaSuccess, "matern_fill_kernel");
 }
 

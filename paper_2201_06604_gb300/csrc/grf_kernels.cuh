@@ -51,6 +51,18 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // bound of every device wait (2 s)
 // Error flags a kernel records (bitwise or) in the caller's status word.
 constexpr int ERR_TIMEOUT = 1;
 
+// 32-byte global accesses of four doubles (address 32-byte aligned).
+__device__ __forceinline__ void ld_v4f64(const double* p, double* v) {
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p));
+}
+__device__ __forceinline__ void st_v4f64(double* p, const double* v) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+               "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Step 1: Matern covariance (Sec. 5).  Sigma_ij = var * corr(x), x =
 // sqrt(8 kappa) |d_ij| / phi, d_ij = diag(1, omega) R(theta) (x_i - x_j).
@@ -73,48 +85,71 @@ __device__ __forceinline__ double matern_cov_at(const MaternParams& p, double dx
 // column k mod ncol, row k div ncol): the covariance depends only on the
 // offset (dr, dc) between two cells, so it is evaluated once per offset,
 // dr in (-nrow, nrow), dc in (-ncol, ncol), table[(dr + nrow - 1) (2 ncol - 1)
-// + dc + ncol - 1].  One thread per (matrix, offset).
+// + dc + ncol - 1].  The offsets (dr, dc) and (-dr, -dc) have the same
+// covariance and mirror indices o and per - 1 - o around the centre
+// c = (per - 1) / 2 (per is odd), so one thread per (matrix, o >= c)
+// evaluates it once and writes both entries (the evaluation is bound by the
+// FP64 pipe).
 __global__ void __launch_bounds__(256) matern_offsets_kernel(const MaternParams* __restrict__ prm,
                                                              uint32_t batch, uint32_t nrow,
                                                              uint32_t ncol, double cell,
                                                              double* __restrict__ table) {
   const uint64_t per = (uint64_t)(2 * nrow - 1) * (2 * ncol - 1);
+  const uint64_t half = per / 2 + 1;                 // o = c .. per - 1
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= per * batch) return;
-  const uint32_t b = (uint32_t)(t / per);
-  const uint64_t o = t - (uint64_t)b * per;
+  if (t >= half * batch) return;
+  const uint32_t b = (uint32_t)(t / half);
+  const uint64_t o = per / 2 + (t - (uint64_t)b * half);
   const int dr = (int)(o / (2 * ncol - 1)) - (int)(nrow - 1);
   const int dc = (int)(o % (2 * ncol - 1)) - (int)(ncol - 1);
-  table[t] = matern_cov_at(prm[b], dc * cell, dr * cell);
+  const double v = matern_cov_at(prm[b], dc * cell, dr * cell);
+  table[(uint64_t)b * per + o] = v;
+  table[(uint64_t)b * per + (per - 1 - o)] = v;
 }
 
 // Fills the n x n matrices (n = nrow ncol, leading dimension ld) from the
-// offset tables: 32-byte rows of four entries per thread.
+// offset tables.  A block item is a run of 1024 columns of one row of one
+// matrix (its matrix, row and run derived once per block, by a grid-stride
+// loop over the items); each thread takes four consecutive columns, walking
+// their (row, column) cells by increments, and writes them with one 32-byte
+// store when `vec` (cov, ld and the matrix stride allow it) or one by one.
+// 32-bit index arithmetic inside a row: n <= 2^20.
 __global__ void __launch_bounds__(256) matern_fill_kernel(const double* __restrict__ table,
                                                           uint32_t batch, uint32_t nrow,
                                                           uint32_t ncol, double* __restrict__ cov,
-                                                          uint64_t ld, uint64_t mstride) {
-  const uint64_t n = (uint64_t)nrow * ncol;
-  const uint64_t q = (n + 3) / 4;                    // groups of four columns per row
-  const uint64_t per = n * q;
-  const uint64_t per_t = (uint64_t)(2 * nrow - 1) * (2 * ncol - 1);
-  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per * batch; t += step) {
-    const uint32_t b = (uint32_t)(t / per);
-    const uint64_t rem = t - (uint64_t)b * per;
-    const uint64_t i = rem / q;
-    const uint64_t j0 = (rem - i * q) * 4;
-    const uint32_t ri = (uint32_t)(i / ncol), ci = (uint32_t)(i % ncol);
-    const double* tb = table + (uint64_t)b * per_t;
-    double* row = cov + (uint64_t)b * mstride + i * ld;
+                                                          uint64_t ld, uint64_t mstride, int vec) {
+  const uint32_t n = nrow * ncol;
+  const uint32_t bpr = (n + 1023) / 1024;            // items per row
+  const uint64_t items = (uint64_t)batch * n * bpr;
+  const uint32_t tw = 2 * ncol - 1;                  // table row width
+  const uint64_t per_t = (uint64_t)(2 * nrow - 1) * tw;
+  for (uint64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const uint32_t b = (uint32_t)(it / ((uint64_t)n * bpr));
+    const uint64_t rem = it - (uint64_t)b * n * bpr;
+    const uint32_t i = (uint32_t)(rem / bpr);
+    const uint32_t x = (uint32_t)(rem - (uint64_t)i * bpr);
+    const uint32_t j0 = x * 1024 + 4 * threadIdx.x;
+    if (j0 >= n) continue;
+    const uint32_t ri = i / ncol, ci = i - (i / ncol) * ncol;
+    uint32_t rj = j0 / ncol, cj = j0 - (j0 / ncol) * ncol;
+    // entry (dr, dc) at (dr + nrow - 1) tw + dc + ncol - 1, dr = ri - rj, dc = ci - cj
+    const double* tb = table + (uint64_t)b * per_t + (uint64_t)(ri + nrow - 1) * tw + (ci + ncol - 1);
+    double v[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const uint64_t j = j0 + e;
-      if (j < n) {
-        const uint32_t rj = (uint32_t)(j / ncol), cj = (uint32_t)(j % ncol);
-        const int dr = (int)ri - (int)rj, dc = (int)ci - (int)cj;
-        row[j] = tb[(uint64_t)(dr + (int)nrow - 1) * (2 * ncol - 1) + (dc + (int)ncol - 1)];
+      v[e] = j0 + e < n ? tb[-(int64_t)rj * tw - (int64_t)cj] : 0.0;
+      if (++cj == ncol) {
+        cj = 0;
+        ++rj;
       }
+    }
+    double* row = cov + (uint64_t)b * mstride + (uint64_t)i * ld + j0;
+    if (vec && j0 + 4 <= n) {
+      st_v4f64(row, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (j0 + e < n) row[e] = v[e];
     }
   }
 }
@@ -319,18 +354,6 @@ __device__ __forceinline__ void lower_tile(uint32_t x, uint32_t& ti, uint32_t& t
   while ((uint64_t)t * (t + 1) > x) --t;
   ti = t;
   tj = x - t * (t + 1);
-}
-
-// 32-byte global accesses of four doubles (address 32-byte aligned).
-__device__ __forceinline__ void ld_v4f64(const double* p, double* v) {
-  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
-               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
-               : "l"(p));
-}
-__device__ __forceinline__ void st_v4f64(double* p, const double* v) {
-  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
-               "d"(v[2]), "d"(v[3])
-               : "memory");
 }
 
 // Warps 0-15 drain TMEM (warp w reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31,

@@ -50,6 +50,21 @@ def test_raster_covariance_matches_oracle(R):
     assert np.array_equal(got, np.transpose(got, (0, 2, 1)))          # symmetric exactly
 
 
+@pytest.mark.parametrize("nrow,ncol,pad", [(4, 1, 0), (2, 3, 0), (5, 8, 0), (6, 10, 4), (12, 25, 3),
+                                            (1, 7, 1), (33, 2, 0)])
+def test_raster_covariance_layouts(R, nrow, ncol, pad):
+    # one-column rasters, rows that wrap inside a thread's four columns, the
+    # 32-byte store path (n and ld multiples of 4) and padded leading
+    # dimensions (the padding stays untouched)
+    n = nrow * ncol
+    out = torch.full((len(PARAMS), n, n + pad), -7.0, dtype=torch.float64, device="cuda")
+    R.matern_raster(PARAMS, nrow, ncol, CELL, out=out[:, :, :n])
+    got = out.cpu().numpy()
+    ref = oracle_cov(nrow, ncol, CELL, PARAMS)
+    np.testing.assert_allclose(got[:, :, :n], ref, rtol=1e-12, atol=1e-300)
+    assert (got[:, :, n:] == -7.0).all()
+
+
 def test_points_covariance_matches_oracle(R):
     rng = np.random.default_rng(5)
     pts = rng.uniform(0, 60e3, size=(70, 2))
