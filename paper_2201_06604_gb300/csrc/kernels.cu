@@ -197,24 +197,29 @@ __device__ __forceinline__ void put_f64(uint32_t* w, uint64_t b) {
 template <int DIST, int DT, int UE>
 __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
                                        const float4* __restrict__ tab) {
+  // the step's negations on the ALU pipe where that measured faster (all
+  // but the fp32 normals, whose ALU pipe is the busier; fp64 exponentials,
+  // not measured, keep the IMAD form)
+  constexpr bool AN = DIST == MRG_RAW || DIST == MRG_UNIFORM || (DIST == MRG_NORMAL && DT == MRG_F64) ||
+                      (DIST == MRG_EXPONENTIAL && DT == MRG_F32);
   if constexpr (DIST == MRG_RAW) {
 #pragma unroll
-    for (int e = 0; e < UE; ++e) w[e] = step_fast(s, c.k1, c.k2);
+    for (int e = 0; e < UE; ++e) w[e] = step_fast<AN>(s, c.k1, c.k2);
   } else if constexpr (DIST == MRG_UNIFORM && DT == MRG_F64) {
 #pragma unroll
-    for (int e = 0; e < UE; ++e) put_f64(w + 2 * e, uniform_bits64_fast(step_fast(s, c.k1, c.k2)));
+    for (int e = 0; e < UE; ++e) put_f64(w + 2 * e, uniform_bits64_fast(step_fast<AN>(s, c.k1, c.k2)));
   } else if constexpr (DIST == MRG_UNIFORM) {
 #pragma unroll
     for (int e = 0; e < UE; ++e)
-      w[e] = uniform_bits32(step_fast(s, c.k1, c.k2));
+      w[e] = uniform_bits32(step_fast<AN>(s, c.k1, c.k2));
   } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F64 && UE % 4 == 0) {
     // two pairs per packed fp32x2 evaluation (bit-identical to the scalar one)
 #pragma unroll
     for (int p = 0; p < UE / 4; ++p) {
-      const uint32_t z1a = step_fast(s, c.k1, c.k2);
-      const uint32_t z2a = step_fast(s, c.k1, c.k2);
-      const uint32_t z1b = step_fast(s, c.k1, c.k2);
-      const uint32_t z2b = step_fast(s, c.k1, c.k2);
+      const uint32_t z1a = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z2a = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z1b = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z2b = step_fast<AN>(s, c.k1, c.k2);
       uint64_t xa, ya, xb, yb;
       box_muller_f64_x2<UM32k3a>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
       put_f64(w + 8 * p, xa);
@@ -225,10 +230,10 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else if constexpr (DIST == MRG_NORMAL && DT == MRG_F32 && UE % 4 == 0) {
 #pragma unroll
     for (int p = 0; p < UE / 4; ++p) {
-      const uint32_t z1a = step_fast(s, c.k1, c.k2);
-      const uint32_t z2a = step_fast(s, c.k1, c.k2);
-      const uint32_t z1b = step_fast(s, c.k1, c.k2);
-      const uint32_t z2b = step_fast(s, c.k1, c.k2);
+      const uint32_t z1a = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z2a = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z1b = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z2b = step_fast<AN>(s, c.k1, c.k2);
       float xa, ya, xb, yb;
       box_muller_f32_x2<UM32k3a>(z1a, z2a, z1b, z2b, tab, xa, ya, xb, yb);
       w[4 * p] = __float_as_uint(xa);
@@ -239,8 +244,8 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else if constexpr (DIST == MRG_NORMAL) {
 #pragma unroll
     for (int p = 0; p < UE / 2; ++p) {
-      const uint32_t z1 = step_fast(s, c.k1, c.k2);
-      const uint32_t z2 = step_fast(s, c.k1, c.k2);
+      const uint32_t z1 = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t z2 = step_fast<AN>(s, c.k1, c.k2);
       if constexpr (DT == MRG_F64) {
         uint64_t x, y;
         box_muller_f64(z1, z2, tab, x, y);
@@ -256,8 +261,8 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else if constexpr (DT == MRG_F32 && UE % 2 == 0) {   // exponential, two draws per packed evaluation
 #pragma unroll
     for (int e = 0; e < UE; e += 2) {
-      const uint32_t za = step_fast(s, c.k1, c.k2);
-      const uint32_t zb = step_fast(s, c.k1, c.k2);
+      const uint32_t za = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t zb = step_fast<AN>(s, c.k1, c.k2);
       float ea, eb;
       exp_f32_x2<UM32k3a>(za, zb, tab, c.ir_hi, c.ir_lo, ea, eb);
       w[e] = __float_as_uint(ea);
@@ -266,7 +271,7 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
     for (int e = 0; e < UE; ++e) {
-      const uint32_t z = step_fast(s, c.k1, c.k2);
+      const uint32_t z = step_fast<AN>(s, c.k1, c.k2);
       if constexpr (DT == MRG_F64)
         put_f64(w + 2 * e, df_to_f64_bits(df_mul(ln_u_df(z, tab), df{c.ir_hi, c.ir_lo})));
       else

@@ -227,26 +227,38 @@ MRG_HD uint32_t uniform_bits32(uint32_t z) {
 // (the portable versions above are the specification; the host harness and
 // the GPU tests check that both agree bit for bit).
 // ---------------------------------------------------------------------------
+// NEG_ALU: the two negations 2^32 - x of a step as ALU subtractions instead
+// of IMADs (the multiply-add form the step used first).  Which pipe has room
+// depends on the output: measured per 2^30 outputs, the ALU form took the
+// fp32 uniforms 1.544 -> 1.503 ms, the fp32 exponentials 2.243 -> 2.216 and
+// the fp64 uniforms and normals 0.3-0.6 % less, and the fp32 normals 2.972
+// -> 3.010 (their ALU pipe is the busier one), so each caller chooses.
+template <bool NEG_ALU = false>
 __device__ __forceinline__ uint32_t step_fast(TState& s, uint64_t k1, uint64_t k2) {
 #ifndef __CUDA_ARCH__
   return step(s);  // host compilation pass only; never executed on the host
 #else
-  uint32_t p1, p2, z;
+  uint32_t p1, p2, z, na2, nb2;
+  if constexpr (NEG_ALU) {
+    asm("sub.u32 %0, 0, %1;" : "=r"(na2) : "r"(s.a2));
+    asm("sub.u32 %0, 0, %1;" : "=r"(nb2) : "r"(s.b2));
+  } else {
+    asm("mad.lo.u32 %0, %1, 0xFFFFFFFF, 0;" : "=r"(na2) : "r"(s.a2));
+    asm("mad.lo.u32 %0, %1, 0xFFFFFFFF, 0;" : "=r"(nb2) : "r"(s.b2));
+  }
   // component 1: t = 810728 (2^32 - a2) + K1 + 1403580 a1 ; one fold, carry adds 209
-  asm("{\n\t.reg .u32 n, lo, hi, vl;\n\t.reg .u64 t;\n\t.reg .pred c;\n\t"
-      "mad.lo.u32 n, %1, 0xFFFFFFFF, 0;\n\t"
-      "mad.wide.u32 t, n, 810728, %3;\n\t"
+  asm("{\n\t.reg .u32 lo, hi, vl;\n\t.reg .u64 t;\n\t.reg .pred c;\n\t"
+      "mad.wide.u32 t, %1, 810728, %3;\n\t"
       "mad.wide.u32 t, %2, 1403580, t;\n\t"
       "mov.b64 {lo, hi}, t;\n\t"
       "mad.lo.u32 vl, hi, 209, lo;\n\t"
       "setp.lt.u32 c, vl, lo;\n\t"
       "@c add.u32 vl, vl, 209;\n\t"
       "mov.u32 %0, vl;\n\t}"
-      : "=r"(p1) : "r"(s.a2), "r"(s.a1), "l"(k1));
+      : "=r"(p1) : "r"(na2), "r"(s.a1), "l"(k1));
   // component 2: t = 1370589 (2^32 - b2) + K2 + 527612 b0 ; two folds
-  asm("{\n\t.reg .u32 n, lo, hi, vl, vh, wl;\n\t.reg .u64 t, v;\n\t.reg .pred c;\n\t"
-      "mad.lo.u32 n, %1, 0xFFFFFFFF, 0;\n\t"
-      "mad.wide.u32 t, n, 1370589, %3;\n\t"
+  asm("{\n\t.reg .u32 lo, hi, vl, vh, wl;\n\t.reg .u64 t, v;\n\t.reg .pred c;\n\t"
+      "mad.wide.u32 t, %1, 1370589, %3;\n\t"
       "mad.wide.u32 t, %2, 527612, t;\n\t"
       "mov.b64 {lo, hi}, t;\n\t"
       "mad.wide.u32 v, hi, 22853, t;\n\t"       // hi*22853 + lo + hi*2^32
@@ -256,7 +268,7 @@ __device__ __forceinline__ uint32_t step_fast(TState& s, uint64_t k1, uint64_t k
       "setp.lt.u32 c, wl, vl;\n\t"
       "@c add.u32 wl, wl, 22853;\n\t"
       "mov.u32 %0, wl;\n\t}"
-      : "=r"(p2) : "r"(s.b2), "r"(s.b0), "l"(k2));
+      : "=r"(p2) : "r"(nb2), "r"(s.b0), "l"(k2));
   s.a2 = s.a1; s.a1 = s.a0; s.a0 = p1;
   s.b2 = s.b1; s.b1 = s.b0; s.b0 = p2;
   // z: h = p1 + (22643 - p2) carries exactly when D >= 1, i.e. when h < p1;
