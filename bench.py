@@ -32,14 +32,16 @@ DTYPE_NOTE = ("exact 32-bit integer recurrence; uniforms formed in integers; nor
               "exponentials in double-float (fp32 pairs); fp64 and fp32 outputs")
 
 # Warp-level instructions issued per output by generate_kernel, measured with
-# ncu (smsp__inst_executed.sum x 32 / outputs) on 16384 streams x 4096 draws
-# (profiles/generate_issue_mix_16384x4096.txt).  These kernels are bound by
-# instruction issue or by the IMAD (fmaheavy) pipe (the FP64 pipe is not used
-# and the recurrence is integer multiply-add work), so beside the HBM
-# roofline the bench reports issue slots: 4 warp-instructions per cycle per SM.
-INSTR_PER_OUTPUT = {("raw", "u32"): 27.4, ("uniform", "f64"): 43.0, ("uniform", "f32"): 37.5,
-                    ("normal", "f64"): 117.5, ("normal", "f32"): 86.2,
-                    ("exponential", "f32"): 60.8, ("exponential", "f64"): 107.9}
+# ncu (smsp__inst_executed.sum x 32 / outputs) on 65536 streams x 2048 draws
+# (profiles/generate_pipe_balance_65536x2048.txt; fp64 exponentials, which
+# the bench step does not time, from profiles/generate_issue_mix_16384x4096.txt).
+# These kernels are bound by instruction issue or by the IMAD (fmaheavy) pipe
+# (the FP64 pipe is not used and the recurrence is integer multiply-add work),
+# so beside the HBM roofline the bench reports issue slots: 4
+# warp-instructions per cycle per SM.
+INSTR_PER_OUTPUT = {("raw", "u32"): 28.1, ("uniform", "f64"): 43.8, ("uniform", "f32"): 38.2,
+                    ("normal", "f64"): 115.1, ("normal", "f32"): 83.7,
+                    ("exponential", "f32"): 58.0, ("exponential", "f64"): 107.9}
 
 
 def env_rank():
@@ -179,9 +181,9 @@ def run_reference(args):
 # DRAM bytes (read + write) per output of generate_kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 65536 streams x 4096 draws
 # (profiles/generate_dram_traffic_65536x4096.txt).
-TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.824, ("uniform", "f32"): 3.814,
-                      ("normal", "f64"): 7.829, ("normal", "f32"): 3.817,
-                      ("exponential", "f32"): 3.813}
+TRAFFIC_PER_OUTPUT = {("uniform", "f64"): 7.829, ("uniform", "f32"): 3.809,
+                      ("normal", "f64"): 7.822, ("normal", "f32"): 3.813,
+                      ("exponential", "f32"): 3.812}
 
 
 def roofline(dom, hbm, peak_kind, issue_peak, total_out, sm_count):

@@ -227,12 +227,14 @@ MRG_HD uint32_t uniform_bits32(uint32_t z) {
 // (the portable versions above are the specification; the host harness and
 // the GPU tests check that both agree bit for bit).
 // ---------------------------------------------------------------------------
-// NEG_ALU: the two negations 2^32 - x of a step as ALU subtractions instead
-// of IMADs (the multiply-add form the step used first).  Which pipe has room
-// depends on the output: measured per 2^30 outputs, the ALU form took the
-// fp32 uniforms 1.544 -> 1.503 ms, the fp32 exponentials 2.243 -> 2.216 and
-// the fp64 uniforms and normals 0.3-0.6 % less, and the fp32 normals 2.972
-// -> 3.010 (their ALU pipe is the busier one), so each caller chooses.
+// NEG_ALU: the two negations 2^32 - x of a step written as subtractions from
+// zero instead of multiply-adds by 2^32 - 1 (the form the step used first).
+// The per-draw instruction and pipe counts of the two forms barely differ
+// (ncu), but ptxas schedules the surrounding code differently, and the
+// times do differ: per 2^30 outputs the subtraction form took the fp32
+// uniforms 1.544 -> 1.503 ms and the fp32 exponentials 2.243 -> 2.216, the
+// fp64 uniforms about 1 % less, and the fp32 normals 2.972 -> 3.010, so
+// each caller chooses.
 template <bool NEG_ALU = false>
 __device__ __forceinline__ uint32_t step_fast(TState& s, uint64_t k1, uint64_t k2) {
 #ifndef __CUDA_ARCH__
