@@ -819,7 +819,7 @@ __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint
 // step, and a step costs two barriers.  Double-float arithmetic on the FP32
 // pipes (GB300's FP64 pipe retires under one DFMA per cycle per SM).
 constexpr int DIAG_THREADS = 1024;
-constexpr int DIAG_P = 4;   // pivots per pass of the diagonal block's LDL^T (measured: 3: 88 us, 4: 82, 6: 97)
+constexpr int DIAG_P = 4;   // pivots per pass of the diagonal block's LDL^T (measured: 3: 88 us, 4: 82, 6: 97; 5 spills)
 
 // P pivots j .. j + P - 1 of the diagonal block's LDL^T in one pass, with
 // the operations of one pivot at a time in the same order (so the same

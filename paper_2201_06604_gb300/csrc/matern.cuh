@@ -1,6 +1,8 @@
 // matern.cuh -- the Matern correlation of Sec. 5 in double precision, for
 // host and device code (the covariance step of the Gaussian-random-field
-// application, Algorithm 2 step 1; no kernel uses it yet).
+// application, Algorithm 2 step 1: matern_offsets_kernel and
+// matern_points_kernel in grf_kernels.cuh; the host test harness checks it
+// against scipy and the oracle).
 //
 // Modified Bessel function of the second kind, scaled: from the integral
 // representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt,
