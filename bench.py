@@ -33,15 +33,15 @@ DTYPE_NOTE = ("exact 32-bit integer recurrence; uniforms formed in integers; nor
 
 # Warp-level instructions issued per output by generate_kernel, measured with
 # ncu (smsp__inst_executed.sum x 32 / outputs) on 65536 streams x 2048 draws
-# (profiles/generate_pipe_balance_65536x2048.txt; fp64 exponentials, which
-# the bench step does not time, from profiles/generate_issue_mix_16384x4096.txt).
+# (profiles/generate_pipe_balance_65536x2048.txt, fp64 exponentials from a
+# capture of their own at the same size, listed there).
 # These kernels are bound by instruction issue or by the IMAD (fmaheavy) pipe
 # (the FP64 pipe is not used and the recurrence is integer multiply-add work),
 # so beside the HBM roofline the bench reports issue slots: 4
 # warp-instructions per cycle per SM.
 INSTR_PER_OUTPUT = {("raw", "u32"): 28.1, ("uniform", "f64"): 43.8, ("uniform", "f32"): 38.2,
                     ("normal", "f64"): 115.1, ("normal", "f32"): 83.7,
-                    ("exponential", "f32"): 58.0, ("exponential", "f64"): 107.9}
+                    ("exponential", "f32"): 58.0, ("exponential", "f64"): 93.9}
 
 
 def env_rank():

@@ -141,6 +141,16 @@ __device__ __forceinline__ void produce31(State& s, uint32_t* w, const Consts& c
         w[2 * p + 1] = __float_as_uint(y);
       }
     }
+  } else if constexpr (DT == MRG_F64 && UE % 2 == 0) {   // exponential, two draws per packed evaluation
+#pragma unroll
+    for (int e = 0; e < UE; e += 2) {
+      const uint32_t za = 2u * g31::step(s);
+      const uint32_t zb = 2u * g31::step(s);
+      uint64_t ea, eb;
+      exp_f64_x2<UM2p32>(za, zb, tab, c.ir_hi, c.ir_lo, ea, eb);
+      put_f64(w + 2 * e, ea);
+      put_f64(w + 2 * e + 2, eb);
+    }
   } else if constexpr (DT == MRG_F32 && UE % 2 == 0) {   // exponential, two draws per packed evaluation
 #pragma unroll
     for (int e = 0; e < UE; e += 2) {

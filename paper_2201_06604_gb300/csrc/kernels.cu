@@ -6,7 +6,7 @@
 //   generate_kernel  the recurrence in registers + transform + 32-byte stores
 //   fused_kernel     no-store consumer: quarter-circle count and normal sum
 //   transform_kernel the transforms of caller-provided raw draws (normals
-//                    and fp32 exponentials into an output aligned to four
+//                    and exponentials into an output aligned to four
 //                    outputs: transform_x2_kernel, four draws per thread)
 //   fill_kernel      write-only stream (the write ceiling generate is held to)
 //   matrix_kernel    the paper's work-item matrix layout (matrix_kernels.cuh)
@@ -268,6 +268,16 @@ __device__ __forceinline__ void produce(TState& s, uint32_t* w, const Consts& c,
       w[e] = __float_as_uint(ea);
       w[e + 1] = __float_as_uint(eb);
     }
+  } else if constexpr (DT == MRG_F64 && UE % 2 == 0) {   // the same for fp64 (3.80 -> 3.66 ms per 2^30)
+#pragma unroll
+    for (int e = 0; e < UE; e += 2) {
+      const uint32_t za = step_fast<AN>(s, c.k1, c.k2);
+      const uint32_t zb = step_fast<AN>(s, c.k1, c.k2);
+      uint64_t ea, eb;
+      exp_f64_x2<UM32k3a>(za, zb, tab, c.ir_hi, c.ir_lo, ea, eb);
+      put_f64(w + 2 * e, ea);
+      put_f64(w + 2 * e + 2, eb);
+    }
   } else {  // exponential: -ln(u) / rate
 #pragma unroll
     for (int e = 0; e < UE; ++e) {
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
   }
 }
 
-// Normals and fp32 exponentials into an output aligned to four outputs
+// Normals and exponentials into an output aligned to four outputs
 // (32 bytes for fp64, 16 for fp32): each thread transforms four draws with
 // the packed two-at-a-time evaluation and stores them in one vector; a last
 // unit of fewer than four draws takes the scalar one (bit-identical results
@@ -510,7 +520,7 @@ __global__ void __launch_bounds__(256) transform_kernel(const uint32_t* __restri
 template <int DIST, int DT>
 __global__ void __launch_bounds__(256) transform_x2_kernel(const uint32_t* __restrict__ z, uint64_t n,
                                                            char* out, Consts c) {
-  static_assert(DIST == MRG_NORMAL || (DIST == MRG_EXPONENTIAL && DT == MRG_F32), "packed forms");
+  static_assert(DIST == MRG_NORMAL || DIST == MRG_EXPONENTIAL, "packed forms");
   __shared__ float4 s_tab[TAB_ENTRIES];
   load_ttab(s_tab);
   constexpr int ES = DT == MRG_F64 ? 8 : 4;
@@ -535,6 +545,14 @@ __global__ void __launch_bounds__(256) transform_x2_kernel(const uint32_t* __res
         w[1] = __float_as_uint(ya);
         w[2] = __float_as_uint(xb);
         w[3] = __float_as_uint(yb);
+      } else if constexpr (DT == MRG_F64) {
+        uint64_t e0, e1, e2, e3;
+        exp_f64_x2<UM32k3a>(z[i0], z[i0 + 1], s_tab, c.ir_hi, c.ir_lo, e0, e1);
+        exp_f64_x2<UM32k3a>(z[i0 + 2], z[i0 + 3], s_tab, c.ir_hi, c.ir_lo, e2, e3);
+        put_f64(w, e0);
+        put_f64(w + 2, e1);
+        put_f64(w + 4, e2);
+        put_f64(w + 6, e3);
       } else {
         float e0, e1, e2, e3;
         exp_f32_x2<UM32k3a>(z[i0], z[i0 + 1], s_tab, c.ir_hi, c.ir_lo, e0, e1);
@@ -563,6 +581,10 @@ __global__ void __launch_bounds__(256) transform_x2_kernel(const uint32_t* __res
         store_vec<ES>(out + i * ES, w);
         if (i + 1 < n) store_vec<ES>(out + (i + 1) * ES, w + ES / 4);
       }
+    } else if constexpr (DT == MRG_F64) {
+      for (uint64_t i = i0; i < n; ++i)
+        reinterpret_cast<uint64_t*>(out)[i] =
+            df_to_f64_bits(df_mul(ln_u_df(z[i], s_tab), df{c.ir_hi, c.ir_lo}));
     } else {
       for (uint64_t i = i0; i < n; ++i)
         reinterpret_cast<float*>(out)[i] = exp_f32(z[i], s_tab, c.ir_hi, c.ir_lo);
@@ -1001,6 +1023,7 @@ cudaError_t preload_kernels() {
   load_fn(transform_x2_kernel<MRG_NORMAL, MRG_F64>, bad);
   load_fn(transform_x2_kernel<MRG_NORMAL, MRG_F32>, bad);
   load_fn(transform_x2_kernel<MRG_EXPONENTIAL, MRG_F32>, bad);
+  load_fn(transform_x2_kernel<MRG_EXPONENTIAL, MRG_F64>, bad);
   load_fn(batch_kernel, bad);
   load_fn(serve_kernel, bad);
   return bad ? cudaErrorInvalidDeviceFunction : cudaSuccess;
@@ -1046,6 +1069,10 @@ cudaError_t launch_transform(const uint32_t* z, uint64_t n, int dist, int dtype,
   }
   if (dist == MRG_EXPONENTIAL && dtype == MRG_F32 && (al & 15) == 0) {
     transform_x2_kernel<MRG_EXPONENTIAL, MRG_F32><<<grid4, 256, 0, st>>>(z, n, o, c);
+    return after_launch();
+  }
+  if (dist == MRG_EXPONENTIAL && dtype == MRG_F64 && (al & 31) == 0) {
+    transform_x2_kernel<MRG_EXPONENTIAL, MRG_F64><<<grid4, 256, 0, st>>>(z, n, o, c);
     return after_launch();
   }
   const uint64_t units = dist == MRG_NORMAL ? (n + 1) / 2 : n;

@@ -1,7 +1,7 @@
 // transforms_x2.cuh -- the double-float transforms of two draws (Box-Muller:
 // two pairs) at once with packed fp32x2 instructions (add/sub/mul/fma
 // .rn.f32x2: two IEEE fp32 operations in one instruction): fp64 normals,
-// the radius R of fp32 normals, fp32 exponentials.
+// the radius R of fp32 normals, fp32 and fp64 exponentials.
 //
 // The transform kernels are bound by instruction issue, not by the FP32
 // pipes (about half busy): a packed instruction carries two fp32 operations
@@ -314,6 +314,23 @@ __device__ __forceinline__ void box_muller_sum_lite_x2(uint32_t z1a, uint32_t z2
   upk(R.lo, rla, rlb);
   va = box_muller_sum_lite_rest_m<UM>(df{rha, rla}, z2a, tab);
   vb = box_muller_sum_lite_rest_m<UM>(df{rhb, rlb}, z2b, tab);
+}
+
+// -ln(u) / rate of two draws to fp64 bits, identical to
+// df_to_f64_bits(df_mul(ln_u_df_m(z), {ir_hi, ir_lo})) on each: the log of
+// both draws packed, the product by -1/rate packed (df_mul_nx2 is df_mul
+// given the negated leading part of its first operand), the conversion to
+// double bits per element.
+template <class UM>
+__device__ __forceinline__ void exp_f64_x2(uint32_t za, uint32_t zb, const float4* __restrict__ tab,
+                                           float ir_hi, float ir_lo, uint64_t& ea, uint64_t& eb) {
+  const df2 l = ln_u_df_m2<UM>(za, zb, tab);
+  const df2 p = df_mul_nx2(l, neg2(l.hi), df2{bc(ir_hi), bc(ir_lo)});
+  float ha, hb, la, lb;
+  upk(p.hi, ha, hb);
+  upk(p.lo, la, lb);
+  ea = df_to_f64_bits(df{ha, la});
+  eb = df_to_f64_bits(df{hb, lb});
 }
 
 // -ln(u) / rate of two draws to fp32, identical to exp_f32_m on each.

@@ -154,7 +154,7 @@ def test_materialised_full_size_sampled(M, dist, dtype):
 
 
 @pytest.mark.parametrize("dist,dt", [("normal", torch.float64), ("normal", torch.float32),
-                                     ("exponential", torch.float32)])
+                                     ("exponential", torch.float32), ("exponential", torch.float64)])
 @pytest.mark.parametrize("ns,n", [(300, 4096), (33, 1002)])
 def test_packed_equals_scalar(M, ns, n, dist, dt):
     # rows aligned for 16- or 32-byte stores take the packed two-at-a-time

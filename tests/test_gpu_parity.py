@@ -336,10 +336,10 @@ def test_unaddressable_extent_is_rejected(M):
 
 
 @pytest.mark.parametrize("dist,dt", [("normal", torch.float64), ("normal", torch.float32),
-                                     ("exponential", torch.float32)])
+                                     ("exponential", torch.float32), ("exponential", torch.float64)])
 @pytest.mark.parametrize("ns,n", [(300, 4096), (33, 1002), (1, 9)])
 def test_packed_equals_scalar(M, ns, n, dist, dt):
-    # normals and fp32 exponentials into rows aligned for 16- or 32-byte
+    # normals and exponentials into rows aligned for 16- or 32-byte
     # stores are evaluated two draws (two pairs) at a time with packed fp32x2
     # instructions; a row pitch of one element more selects the one-at-a-time
     # evaluation.  Same streams, same bits.

@@ -138,7 +138,8 @@ def test_odd_normal_count_and_zero_crossings(mrg):
     assert np.abs(got - ref).max() <= 1e-12
 
 
-PACKED = [("normal", torch.float64), ("normal", torch.float32), ("exponential", torch.float32)]
+PACKED = [("normal", torch.float64), ("normal", torch.float32), ("exponential", torch.float32),
+          ("exponential", torch.float64)]
 
 
 @pytest.mark.parametrize("dist,dt", PACKED)
