@@ -233,8 +233,9 @@ MRG_HD uint32_t uniform_bits32(uint32_t z) {
 // (ncu), but ptxas schedules the surrounding code differently, and the
 // times do differ: per 2^30 outputs the subtraction form took the fp32
 // uniforms 1.544 -> 1.503 ms and the fp32 exponentials 2.243 -> 2.216, the
-// fp64 uniforms about 1 % less, and the fp32 normals 2.972 -> 3.010, so
-// each caller chooses.
+// fp64 uniforms about 1 % less, the fp64 exponentials 3.65 -> 3.59, and the
+// fp32 normals 2.972 -> 3.010 and the fused consumer 13.85 -> 13.89 (2^32
+// draws), so each caller chooses.
 template <bool NEG_ALU = false>
 __device__ __forceinline__ uint32_t step_fast(TState& s, uint64_t k1, uint64_t k2) {
 #ifndef __CUDA_ARCH__
