@@ -682,14 +682,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) ozaki_gemm_kernel(GemmArgs g)
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal block: LDL^T of a kb x kb block (kb <= 128) and the inverse X of
-// its unit lower factor, by one CTA of 512 threads per matrix, in
+// Diagonal block: LDL^T of a kb x kb block (kb <= 128) by one CTA of
+// DIAG_THREADS per matrix (ldl_diag_kernel), then the inverse X of its unit
+// lower factor by columns on many CTAs (ldl_inverse_kernel), in
 // double-float arithmetic (fp32 pairs; GB300's FP64 rate is a small fraction
 // of its FP32 rate) on the block scaled by a power of two (its largest
 // diagonal entry brought near 1, so that fp32's exponent range holds it).
 // Writes L (strict lower part of the block, unit diagonal implied), D (on the
-// block's diagonal and into d[]), and the B-role operand of the panel
-// product, row n of B = row n of X divided by d_n (so that L_ik = A_ik B^T).
+// block's diagonal and into d[]), and the panel product's B operand, row n
+// of B = row n of X divided by d_n (so that L_ik = A_ik B^T), which
+// slice_kernel then cuts into digit planes.
 // ---------------------------------------------------------------------------
 
 constexpr int DG = NB + 1;   // row pitch of the shared block, in float pairs (odd: fewer bank conflicts)
@@ -816,8 +818,9 @@ __device__ __forceinline__ void load_lower_df(const double* __restrict__ A, uint
 // trailing update a_il -= l_ij w_l (j < l <= i < kb, w = column j before
 // scaling), from a table of (i, l) pairs ordered by column l descending, so
 // that the pairs of step j are a prefix of it: every lane works on every
-// step, and a step costs two barriers.  Double-float arithmetic on the FP32
-// pipes (GB300's FP64 pipe retires under one DFMA per cycle per SM).
+// step.  DIAG_P steps form a pass, which costs two barriers.  Double-float
+// arithmetic on the FP32 pipes (GB300's FP64 pipe retires 1.6 DFMA per
+// cycle per SM, against 128 FP32 FMAs).
 constexpr int DIAG_THREADS = 1024;
 constexpr int DIAG_P = 4;   // pivots per pass of the diagonal block's LDL^T (measured: 3: 88 us, 4: 82, 6: 97; 5 spills)
 
