@@ -20,9 +20,10 @@
 // the recurrence in registers.  Segment q of the flattened index runs stream
 // q mod ns at segment q div ns, so the 32 lanes of a warp share the segment
 // offset whenever ns >= 32 and the jump's table reads are warp-uniform.
-// fp64 normals are transformed two pairs at a time with packed fp32x2
-// instructions (transforms_x2.cuh) when a unit holds two pairs (32-byte
-// stores), else one pair at a time; the results are bit-identical.
+// Normals and exponentials are transformed two draws (two Box-Muller pairs)
+// at a time with packed fp32x2 instructions (transforms_x2.cuh; for fp32
+// normals only the radius) when a unit holds enough outputs (16- or 32-byte
+// stores), else one at a time; the results are bit-identical.
 // Each lane's outputs are contiguous in its row, so a lane stores whole
 // 32-byte sectors with one 256-bit st.global per 32 bytes: the L2 receives
 // full-sector writes and nothing is staged in shared memory.  (Staged
