@@ -147,8 +147,11 @@ int mrg_generate_host(const mrg_streams *s, uint64_t n_per_stream, int dist, int
  * out[2k] = X, out[2k+1] = Y; an odd n computes the last X from (z[n-1], 1)) or
  * MRG_EXPONENTIAL with MRG_F32 / MRG_F64, same accuracy as mrg_generate.
  * Values of z outside [1, m1] give unspecified (but memory-safe) outputs.
- * Errors: MRG_EINVAL (NULL pointers with n > 0, bad dist/dtype or rate),
- * MRG_ECUDA. */
+ * The outputs are bit-identical to mrg_generate's for the same draws,
+ * whatever the alignment of out (an out aligned to four outputs takes the
+ * packed evaluation, bit-identical to the one-at-a-time one).
+ * Errors: MRG_EINVAL (NULL pointers with n > 0, bad dist/dtype or rate, out
+ * not aligned to its element size or z not to 4 bytes), MRG_ECUDA. */
 int mrg_transform(const uint32_t *z, uint64_t n, int dist, int dtype, double rate, void *out,
                   void *stream);
 
